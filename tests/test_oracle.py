@@ -1,0 +1,351 @@
+"""Pins for the CPU oracle: checks against what the paper and the mathematics
+fix, never against the oracle itself.  CPU only."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_11290_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def full_from_cores(cores):
+    """Contract TT cores [s_{m-1}, n_m, s_m] into the full tensor (numpy)."""
+    X = cores[0]
+    for G in cores[1:]:
+        X = np.tensordot(X, G, axes=([-1], [0]))
+    return X[0, ..., 0]
+
+
+def full_tensor(n, gen):
+    """The exact tensor, evaluated entry by entry by numpy expressions."""
+    grids = np.meshgrid(*[np.arange(v) for v in n], indexing="ij")
+    if gen["kind"] == "hilbert":
+        return 1.0 / (1.0 + sum(grids))
+    if gen["kind"] == "tt":
+        return full_from_cores([np.asarray(c) for c in gen["cores"]])
+    raise ValueError
+
+
+def matrix_as_tt(A):
+    """An n1 x n2 matrix as a d=2 TT that reproduces it exactly: G0 = I, G1 = A."""
+    n1, n2 = A.shape
+    G0 = np.eye(n1).reshape(1, n1, n1)
+    G1 = A.reshape(n1, n2, 1)
+    return {"kind": "tt", "ranks": [1, n1, 1], "cores": [G0, G1]}
+
+
+# --------------------------------------------------------------------------
+# Sampling generator: published SplitMix64 outputs (golden file).
+def test_splitmix64_published_outputs():
+    vals = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt"))
+            if l.strip() and not l.startswith("#")]
+    # index = floor(x * n / 2^64) with n = 2^31 is x >> 33
+    idx = oracle.sample_indices([2**31], len(vals), seed=0)[:, 0]
+    assert [int(v) for v in idx] == [v >> 33 for v in vals]
+    assert [W.splitmix64(0, k) for k in range(len(vals))] == vals
+
+
+def test_sample_indices_in_range_and_uniform():
+    n = [7, 64, 3]
+    s = oracle.sample_indices(n, 60000, seed=5)
+    assert s.min() == 0 and all(s[:, m].max() == n[m] - 1 for m in range(3))
+    counts = np.bincount(s[:, 0], minlength=7)
+    chi2 = ((counts - 60000 / 7) ** 2 / (60000 / 7)).sum()
+    assert chi2 < 30  # 6 dof; p ~ 4e-5
+
+
+# --------------------------------------------------------------------------
+# d = 2: the cross with an exhaustive screen is Gaussian elimination with
+# complete pivoting after the fixed first pivot (Sec. 2.3; eq. aca_approx_E).
+def lu_complete_pivoting(A, steps):
+    S = A.copy()
+    n1, n2 = A.shape
+    piv, vals = [(0, 0)], []
+    S = S - np.outer(S[:, 0], S[0, :]) / S[0, 0]
+    for _ in range(steps - 1):
+        mag = np.abs(S)
+        m = mag.max()
+        cand = np.argwhere(mag == m)
+        lin = cand[:, 0] + n1 * cand[:, 1]          # column-major linear index
+        i, j = cand[np.argmin(lin)]
+        vals.append(m)
+        piv.append((int(i), int(j)))
+        S = S - np.outer(S[:, j], S[i, :]) / S[i, j]
+    return piv, vals
+
+
+@pytest.mark.parametrize("shape,seed", [((8, 8), 0), ((13, 29), 1), ((40, 17), 2), ((1, 9), 3)])
+def test_d2_matches_complete_pivoting_lu(shape, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal(shape)
+    A[0, 0] = 2.0
+    steps = min(shape)
+    o = oracle.Oracle(list(shape), matrix_as_tt(A), steps)
+    assert o.init() == 0
+    got_vals = []
+    for _ in range(steps - 1):
+        rc, s = o.screen()
+        assert rc == 0
+        got_vals.append(s["best"][0])
+        assert o.apply([1], s["row"], s["col"]) == 0
+    I, J = o.pivots(0)
+    piv, vals = lu_complete_pivoting(A, steps)
+    assert [(int(a), int(b)) for a, b in zip(I[:, 0], J[:, 0])] == piv
+    np.testing.assert_allclose(got_vals, vals, rtol=1e-10, atol=1e-13)
+
+
+def test_tie_goes_to_lowest_column_major_index():
+    # after the pivot (0,0) the residual has |E| = 1 at (2,1) and (1,3):
+    # column-major lin 2+4*1=6 < 1+4*3=13, row-major would pick (1,3)
+    A = np.zeros((4, 4))
+    A[0, 0] = 1.0
+    A[2, 1] = 1.0
+    A[1, 3] = -1.0
+    o = oracle.Oracle([4, 4], matrix_as_tt(A), 3)
+    o.init()
+    rc, s = o.screen()
+    assert s["best"][0] == 1.0
+    assert (s["row"][0], s["col"][0]) == (2, 1)
+    assert s["lin"][0] == 6
+
+
+# --------------------------------------------------------------------------
+# Fig. 1 (Sec. 3.1.1): on the 100 x 100 Hilbert matrix the iterative formula
+# reaches machine precision while C P^{-1} R degrades beyond rank ~12.
+def test_fig1_iterative_vs_direct_hilbert_matrix():
+    n = 100
+    i = np.arange(n)
+    H = 1.0 / (1 + i[:, None] + i[None, :])
+    o = oracle.Oracle([n, n], {"kind": "hilbert"}, 24)
+    o.init()
+    err_it, err_dir = {}, {}
+    for z in range(1, 23):
+        T, R = o.T(0), o.R(0)
+        err_it[z] = np.linalg.norm(H - T @ R) / np.linalg.norm(H)
+        I, J = o.pivots(0)
+        P = H[np.ix_(I[:, 0], J[:, 0])]
+        try:  # the direct method forms the inverse of the cross section
+            with np.errstate(all="ignore"):
+                D = H[:, J[:, 0]] @ np.linalg.inv(P) @ H[I[:, 0], :]
+            err_dir[z] = np.linalg.norm(H - D) / np.linalg.norm(H)
+        except np.linalg.LinAlgError:
+            err_dir[z] = np.inf
+        rc, s = o.screen()
+        o.apply([1], s["row"], s["col"])
+    assert min(err_it.values()) < 1e-15
+    assert err_it[20] < 1e-15
+    assert err_dir[20] > 1e4 * err_it[20]
+    # both agree while the pivot block is well conditioned
+    assert abs(err_dir[8] - err_it[8]) < 1e-3 * err_it[8]
+
+
+# --------------------------------------------------------------------------
+def test_separable_rank1_is_exact():
+    w = W.separable([7, 9, 5, 6])
+    o = oracle.Oracle(w["n"], w["gen"], 8)
+    rc, st = o.run(1e-12, nsamples=0)
+    assert rc == 0
+    assert list(o.ranks()) == [1, 1, 1]
+    X = full_tensor(w["n"], w["gen"])
+    Y = full_from_cores(o.cores())
+    assert np.abs(X - Y).max() <= 1e-15 * np.abs(X).max()
+
+
+def test_random_tt_known_ranks_recovered():
+    w = W.random_tt([12, 12, 12, 12], [1, 3, 4, 3, 1], seed=7)
+    o = oracle.Oracle(w["n"], w["gen"], 10)
+    rc, st = o.run(1e-12, nsamples=0)
+    assert rc == 0
+    assert list(o.ranks()) == [3, 4, 3]
+    X = full_tensor(w["n"], w["gen"])
+    Y = full_from_cores(o.cores())
+    assert np.linalg.norm(X - Y) / np.linalg.norm(X) <= 1e-12
+
+
+def _interp_points(o, m):
+    """Multi-indices (alpha in I_{<=m-1}, i_m, beta in J_{>m})."""
+    d = o.d
+    if m == 0:
+        lefts = [()]
+    else:
+        I, _ = o.pivots(m - 1)
+        lefts = [tuple(r) for r in I]
+    if m == d - 1:
+        rights = [()]
+    else:
+        _, J = o.pivots(m)
+        rights = [tuple(r) for r in J]
+    for a in lefts:
+        for i in range(int(o.n[m])):
+            for b in rights:
+                yield a + (i,) + b
+
+
+@pytest.mark.parametrize("case", ["hilbert", "tt"])
+def test_interpolation_and_nestedness(case):
+    if case == "hilbert":
+        w = W.hilbert(4, 10)
+        eps = 1e-9
+    else:
+        w = W.random_tt([6, 7, 8, 5], [1, 4, 6, 3, 1], seed=11)
+        eps = 1e-3
+    o = oracle.Oracle(w["n"], w["gen"], 6)
+    rc, _ = o.run(eps, nsamples=0)
+    assert rc in (0, oracle.NOT_CONVERGED)
+    X = full_tensor(w["n"], w["gen"])
+    Y = full_from_cores(o.cores())
+    tol = 1e-13 * np.abs(X).max()
+    # Sec. 3.2.1: the cross reproduces X exactly on (I_{<=k-1}, i_k, J_{>k})
+    for m in range(o.d):
+        for idx in _interp_points(o, m):
+            assert abs(Y[idx] - X[idx]) <= tol, (m, idx)
+    # eq. nestedpivots: I_{<=k} subset I_{<=k-1} x I_k, J_{>k} subset I_{k+1} x J_{>k+1}
+    for b in range(o.d - 1):
+        I, J = o.pivots(b)
+        if b > 0:
+            Ip, _ = o.pivots(b - 1)
+            prev = {tuple(r) for r in Ip}
+            assert all(tuple(r[:-1]) in prev for r in I)
+        if b < o.d - 2:
+            _, Jn = o.pivots(b + 1)
+            nxt = {tuple(r) for r in Jn}
+            assert all(tuple(r[1:]) in nxt for r in J)
+        assert len({tuple(r) for r in I}) == len(I)
+        assert len({tuple(r) for r in J}) == len(J)
+
+
+def test_factor_identities():
+    """T_k = C_k U_k with U_k = P_k^{-1} from the bordered Sherman-Morrison
+    update (Sec. 3.1.1-3.1.3), and T_k R_k = C_k P_k^{-1} R_k."""
+    w = W.hilbert(4, 9)
+    o = oracle.Oracle(w["n"], w["gen"], 5)
+    rc, _ = o.run(1e-6, nsamples=0)
+    X = full_tensor(w["n"], w["gen"])
+    for b in range(o.d - 1):
+        rows, cols = o.dims(b)
+        T, R, U = o.T(b), o.R(b), o.U(b)
+        I, J = o.pivots(b)
+        Il = o.pivots(b - 1)[0] if b > 0 else np.zeros((1, 0), np.int32)
+        Jr = o.pivots(b + 1)[1] if b < o.d - 2 else np.zeros((1, 0), np.int32)
+        n_b, n_b1 = int(o.n[b]), int(o.n[b + 1])
+        # superblock rows (alpha, i_b) and the pivot columns (j, beta) of J_{>k}
+        C = np.array([[X[tuple(Il[a // n_b]) + (a % n_b,) + tuple(Jrow)] for Jrow in J]
+                      for a in range(rows)])
+        P = np.array([[X[tuple(Irow) + tuple(Jrow)] for Jrow in J] for Irow in I])
+        Rx = np.array([[X[tuple(Irow) + (c % n_b1,) + tuple(Jr[c // n_b1])] for c in range(cols)]
+                       for Irow in I])
+        np.testing.assert_array_equal(R, Rx)
+        assert np.abs(U @ P - np.eye(len(I))).max() < 1e-9 * np.linalg.cond(P)
+        # rounding of C U grows with |C||U| (U = P^{-1} is ill conditioned)
+        np.testing.assert_allclose(T, C @ U, rtol=0, atol=1e-13 * (np.abs(C) @ np.abs(U)).max())
+        direct = C @ np.linalg.solve(P, Rx)
+        np.testing.assert_allclose(T @ R, direct, rtol=0, atol=1e-10 * np.abs(direct).max())
+
+
+def test_tt_eval_and_sampled_error_against_numpy():
+    w = W.hilbert(4, 11)
+    o = oracle.Oracle(w["n"], w["gen"], 4)
+    o.run(1e-4, nsamples=5000, seed=3)
+    X = full_tensor(w["n"], w["gen"])
+    Y = full_from_cores(o.cores())
+    S = oracle.sample_indices(w["n"], 5000, seed=3)
+    xs = X[tuple(S.T)]
+    ys = Y[tuple(S.T)]
+    ref = np.sqrt(((xs - ys) ** 2).sum() / (xs ** 2).sum())
+    assert abs(o.sampled_error(5000, seed=3) - ref) <= 1e-14
+    for idx in S[:50]:
+        assert abs(o.tt_eval(idx) - Y[tuple(idx)]) <= 1e-15
+    # exhaustive mode == full-tensor relative Frobenius error (eq. FrobeniusNorm)
+    full = np.linalg.norm(X - Y) / np.linalg.norm(X)
+    assert abs(o.sampled_error(0) - full) <= 1e-15
+
+
+def test_config0_end_to_end_and_svd_bound():
+    """3D Hilbert n=32, eps=1e-10: full-tensor error below eps; no TT with the
+    cross's ranks can beat the tail of the unfoldings' singular values."""
+    w = W.CONFIGS["hilbert3d_n32"]
+    o = oracle.Oracle(w["n"], w["gen"], w["max_rank"])
+    rc, st = o.run(w["eps"], nsamples=0)
+    assert rc == 0
+    X = full_tensor(w["n"], w["gen"])
+    Y = full_from_cores(o.cores())
+    err = np.linalg.norm(X - Y) / np.linalg.norm(X)
+    assert err <= w["eps"]
+    assert abs(err - st["err"]) <= 1e-15
+    r = o.ranks()
+    n = w["n"]
+    for b in range(2):
+        sv = np.linalg.svd(X.reshape(int(np.prod(n[:b + 1])), -1, order="F"), compute_uv=False)
+        tail = np.sqrt((sv[r[b]:] ** 2).sum()) / np.linalg.norm(X)
+        assert err >= tail * (1 - 1e-6)
+        # TT-SVD (delta-truncation at eps/sqrt(d-1)) needs about as many
+        delta = w["eps"] / np.sqrt(2)
+        k = int(np.searchsorted(-np.sqrt(np.cumsum((sv ** 2)[::-1])[::-1] / (X ** 2).sum()), -delta))
+        assert r[b] <= k + 6
+
+
+def test_thread_split_does_not_change_pivots():
+    """The global best pivot is the best of local bests (Sec. 3.2.1)."""
+    w = W.hilbert(4, 12)
+    piv = []
+    for nt in (1, 3, 8):
+        o = oracle.Oracle(w["n"], w["gen"], 8, nthreads=nt)
+        o.run(1e-9, nsamples=2000)
+        piv.append([o.pivot_coords(b) for b in range(3)])
+    for other in piv[1:]:
+        for (a, b), (c, d) in zip(piv[0], other):
+            np.testing.assert_array_equal(a, c)
+            np.testing.assert_array_equal(b, d)
+
+
+def test_zero_start_and_nonfinite():
+    w = W.random_tt([4, 5, 6], [1, 2, 2, 1], seed=3)
+    w["gen"]["cores"][0][:, 0, :] = 0.0
+    o = oracle.Oracle(w["n"], w["gen"], 3)
+    assert o.init() == oracle.ERR_ZERO_START
+    w = W.random_tt([4, 5, 6], [1, 2, 2, 1], seed=3)
+    w["gen"]["cores"][1][:, 3, :] = np.nan
+    o = oracle.Oracle(w["n"], w["gen"], 3)
+    rc, st = o.run(1e-6, nsamples=0)
+    assert rc == oracle.ERR_NONFINITE
+
+
+def test_table5_weak_range():
+    """Table 5: one-process TT-ACA reaches 1.40e-6 on the n=250 Hilbert tensor
+    with ranks (1,25,25,1); the exhaustive greedy search must be at least as
+    accurate, within the 10x slack of a different search."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table5_hilbert3d.txt"))
+            if l.strip() and not l.startswith("#")]
+    ttaca_err = {int(r[0]): float(r[4]) for r in rows}
+    w = W.hilbert(3, 250)
+    o = oracle.Oracle(w["n"], w["gen"], 25, nthreads=os.cpu_count() or 1)
+    rc, st = o.run(0.0, nsamples=10**5, seed=W.DEFAULT_SEED)
+    assert rc == 0 and list(o.ranks()) == [25, 25]
+    assert st["err"] <= 10 * ttaca_err[250]
+
+
+def test_maxwellian_moments():
+    """Velocity moments of the Maxwellian (Sec. 5.2 family): on a wide v-grid
+    the quadrature of f over v returns rho(x), rho u(x) and dv rho T(x)."""
+    n = 48
+    w = W.maxwellian(2, 2, [5, 6, n, n], a_rho=0.4, a_u=0.3, a_T=0.25, vmin=-9.0, vmax=9.0)
+    o = oracle.Oracle(w["n"], w["gen"], 2)
+    g = w["gen"]
+    v = g["vmin"] + (g["vmax"] - g["vmin"]) * np.arange(n) / (n - 1)
+    h = (g["vmax"] - g["vmin"]) / (n - 1)
+    for ix in [(0, 0), (1, 2), (4, 5), (3, 1)]:
+        x = [2 * np.pi * ix[0] / 5, 2 * np.pi * ix[1] / 6]
+        F = np.array([[o.entry(ix + (a, b)) for b in range(n)] for a in range(n)])
+        m0 = F.sum() * h * h
+        rho = 1 + g["a_rho"] * np.sin(x[0]) * np.sin(x[1])
+        T = 1 + g["a_T"] * np.cos(x[0] + x[1])
+        u = [g["a_u"] * np.cos(x[1]), g["a_u"] * np.cos(x[0])]
+        m1 = [(F * v[:, None]).sum() * h * h / m0, (F * v[None, :]).sum() * h * h / m0]
+        m2 = ((F * ((v[:, None] - m1[0]) ** 2 + (v[None, :] - m1[1]) ** 2)).sum() * h * h
+              / m0 / 2)
+        assert abs(m0 - rho) < 1e-10
+        assert abs(m1[0] - u[0]) < 1e-10 and abs(m1[1] - u[1]) < 1e-10
+        assert abs(m2 - T) < 1e-9
