@@ -1,0 +1,272 @@
+"""Benchmark: time-to-eps of the adaptive TT cross on one GB300.
+
+A step is one whole adaptive TT cross (every sweep: residual screen of every
+bond, candidate merge, pivot updates, and the sampled-error verification) on
+the 6D Hilbert tensor X = 1/(1 + i_1 + ... + i_6), n = 64 per mode
+(6.9e10 entries, never formed), eps = 1e-8, max rank 64, subtensor grid 2^6,
+error on 10^6 seeded random entries.  The tensor is a function of its
+indices, so the inputs are synthetic by construction.
+
+One JSON line on rank 0.  ``--impl reference`` times the CPU oracle (plain C,
+FP64, OpenMP over the host cores) on the same workload.  With ``--gpus N``
+(under torchrun) every rank runs an independent replica: the path has no
+exchange step on one GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-eps TT cross (ms), 6D Hilbert n=64 eps=1e-8"
+WORKLOAD = "hilbert6d_n64"
+THROTTLE_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+                 0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+                 0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+                 0x100: "display_clock_setting"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks / throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--id={self.index}",
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active",
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 4:
+                try:
+                    self.samples.append((float(parts[0]), float(parts[1]), parts[2],
+                                         int(parts[3], 16) if parts[3].startswith("0x")
+                                         else int(parts[3])))
+                except ValueError:
+                    pass
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [s[0] for s in self.samples]
+        mask = 0
+        for s in self.samples:
+            mask |= s[3]
+        reasons = [name for bit, name in THROTTLE_BITS.items() if mask & bit and bit != 0x1]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(s[1] for s in self.samples),
+                "reasons": reasons, "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return None
+
+
+def cpu_oracle_time(cfg, threads: int, reps: int = 1):
+    """The oracle as it stands, on the host cores: full runs of the workload."""
+    import oracle
+    times = []
+    st = None
+    for _ in range(reps):
+        o = oracle.Oracle(cfg["n"], cfg["gen"], cfg["max_rank"], nthreads=threads)
+        t0 = time.perf_counter()
+        rc, st = o.run(cfg["eps"], nsamples=cfg["nsamples"])
+        times.append((time.perf_counter() - t0) * 1e3)
+        del o
+    return times, st
+
+
+def bench_reference(args, rank, world):
+    from paper_2407_11290_gb300 import workloads
+    if rank != 0:
+        return
+    cfg = workloads.CONFIGS[WORKLOAD]
+    threads = os.cpu_count() or 1
+    warm, _ = cpu_oracle_time(cfg, threads, reps=args.warmup)
+    times, st = cpu_oracle_time(cfg, threads, reps=args.steps)
+    ms = sum(times) / len(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (analytic tensor)",
+        "config": {"workload": WORKLOAD, "d": 6, "n": 64, "eps": cfg["eps"],
+                   "max_rank": cfg["max_rank"], "nsamples": cfg["nsamples"], "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} full runs of the workload"},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "entries_screened": st["entries_screened"], "sweeps": st["sweeps"], "err": st["err"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_gpu(args, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2407_11290_gb300 import ttcross, workloads
+
+    torch.cuda.set_device(local)
+    cfg = workloads.CONFIGS[WORKLOAD]
+    stream = torch.cuda.Stream()
+    tc = ttcross.TTCross(cfg["n"], cfg["gen"], max_rank=cfg["max_rank"], nsamples=cfg["nsamples"],
+                         precision=args.precision)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_step():
+        tc.run(cfg["eps"], subtensor_grid=cfg["grid"], stream=stream)
+
+    for _ in range(args.warmup):
+        one_step()
+        tc.sync()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kern_ms = []
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))            # L2 flush (512 MB > 129 MB L2), untimed
+        ev[i][0].record(stream)
+        one_step()
+        ev[i][1].record(stream)
+        tc.sync()
+        kern_ms.append(tc.stats()["device_ms"])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    st = tc.stats()
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C ABI with host buffers: run + cores to host memory
+    e2e = []
+    d2h = 0
+    for _ in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one_step()
+        cores = tc.cores()
+        e2e.append((time.perf_counter() - t0) * 1e3)
+        d2h = sum(c.nbytes for c in cores)
+
+    # roofline of the dominant kernel (the persistent cross kernel): its
+    # algorithmic FP64 FMAs (screen + error) over its measured duration
+    fma64, _ = ttcross.probe_fma_peak(True)
+    kms = statistics.median(kern_ms)
+    algo_fma = st["screen_fmas"] + st["error_fmas"]
+    achieved = 2.0 * algo_fma / (kms * 1e-3) / 1e12
+    peak = 2.0 * fma64 / 1e12
+    line = {
+        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else args.precision,
+        "data": "synthetic (analytic tensor, never formed)",
+        "config": {"workload": WORKLOAD, "d": 6, "n": 64, "eps": cfg["eps"],
+                   "max_rank": cfg["max_rank"], "grid": cfg["grid"], "nsamples": cfg["nsamples"],
+                   "precision": args.precision, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "min_ms": min(step_ms), "median_ms": statistics.median(step_ms),
+        "entries_screened": st["entries_screened"],
+        "entries_per_s": st["entries_screened"] * world / (ms * 1e-3),
+        "sweeps": st["sweeps"], "ranks": [int(x) for x in tc.ranks()], "err": st["err"],
+        "status": ttcross.STATUS_NAMES.get(st["status"], st["status"]),
+        "e2e": {"value": statistics.median(e2e), "unit": "ms", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "measured FP64 FMA loop on this GPU",
+                     "kernel": "k_persistent", "kernel_ms": kms,
+                     "algorithmic_fma": algo_fma},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        times, ost = cpu_oracle_time(cfg, threads, reps=1)
+        line["cpu_baseline"] = {"value": times[0], "unit": "ms", "cores": threads,
+                                "kind": "oracle", "sample": "one full run of the workload",
+                                "err": ost["err"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tc.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "split", "auto"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        bench_reference(args, rank, world)
+    else:
+        bench_gpu(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * ttcross.h -- C ABI of the GB300 (sm_103a) adaptive tensor-train cross.
+ *
+ * Problem (paper: "Distributed memory parallel adaptive tensor-train cross
+ * approximation", arXiv 2407.11290, Sec. 1 eq. FrobeniusNorm and Sec. 5 intro):
+ * given a d-way tensor X of mode sizes n_1..n_d defined entry-wise by a
+ * function (it is never formed), build TT cores G_1..G_d (Sec. 2.2) such that
+ * the relative Frobenius error, estimated on random entries (Sec. 5), is at
+ * most eps.
+ *
+ * Method (all steps run in CUDA kernels on one GPU):
+ *   - every bond k = 1..d-1 screens its whole superblock
+ *     X_k(I_{<=k-1} x I_k, I_{k+1} x J_{>k+1}) (Alg. 2) for the entry of
+ *     largest residual |A - T_k R_k| (Alg. 1 with the sample set equal to the
+ *     superblock); the paper's subtensor process grid (Sec. 3, Alg. 3) becomes
+ *     a grid of CTAs, each taking a local argmax, followed by a device-side
+ *     merge of the candidates (the Allgather of Alg. 3);
+ *   - all bonds search simultaneously; pivots are appended with nestedness
+ *     (eq. nestedpivots);
+ *   - T_k = C_k P_k^{-1} is updated by eq. aca_approx_T_sub, rows entering a
+ *     superblock are rebuilt by Alg. 4, and P_k^{-1} is bordered by the
+ *     Sherman-Morrison step of Sec. 3.1.1, all in FP64;
+ *   - cores follow eq. ttcross_build / corereshape; the sampled error is
+ *     computed in FP64 on the GPU.
+ *
+ * Conventions
+ *   - Indices are 0-based.  Bonds and cores use the paper's k: bonds
+ *     1 <= k <= d-1, cores 1 <= k <= d.
+ *   - The linear index used to break ties between equal residuals is the
+ *     column-major one, lin = sum_m i_m prod_{l<m} n_l (Sec. 2.1 reshape).
+ *   - `stream` arguments are cudaStream_t values passed as void*; NULL is the
+ *     legacy default stream.
+ *   - Every function returns a ttc_status; no exception crosses the ABI.
+ *     On failure ttcross_last_error_string() (thread-local) describes it.
+ *   - Handles own all of their device memory (allocated by ttcross_create,
+ *     freed by ttcross_destroy).  Buffers passed by the caller stay owned by
+ *     the caller and are not retained after the call returns.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef TTCROSS_H
+#define TTCROSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TTC_OK = 0,
+  TTC_ERR_INVALID_ARG = 1,   /* bad argument; nothing was launched */
+  TTC_ERR_OOM = 2,           /* device allocation failed */
+  TTC_ERR_ZERO_START = 3,    /* X(0,...,0) == 0: the first pivot is unusable */
+  TTC_ERR_NONFINITE = 4,     /* a generated entry or residual was NaN/Inf */
+  TTC_ERR_DEVICE_TIMEOUT = 5,/* a device-side wait ran past its limit */
+  TTC_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+  TTC_NOT_CONVERGED = 7      /* rank caps or refinement limit reached with the
+                                sampled error above eps; cores are valid */
+} ttc_status;
+
+typedef enum {
+  TTC_GEN_HILBERT = 0,    /* X(i) = 1/(1 + i_1 + ... + i_d) (eq. HilbertTensor, 0-based) */
+  TTC_GEN_TT = 1,         /* X given by TT cores (tests; exact recovery) */
+  TTC_GEN_MAXWELLIAN = 2  /* f(x,v), see ttc_generator */
+} ttc_gen_kind;
+
+/* Entry generator.  All pointers are host pointers, read during
+   ttcross_create only (the data is copied to the device). */
+typedef struct {
+  int32_t kind; /* ttc_gen_kind */
+  /* TTC_GEN_TT: ranks rho[0..d] with rho[0] = rho[d] = 1, rho[m] <= 256, and
+     the cores concatenated, core m laid out [rho_m][n_m][rho_{m+1}]
+     row-major (doubles).  The entry is the left-to-right product of the core
+     slices, each dot product a serial FMA chain. */
+  const int32_t *tt_ranks;
+  const double *tt_cores;
+  /* TTC_GEN_MAXWELLIAN: modes ordered (x_0..x_{dx-1}, v_0..v_{dv-1});
+     x_m = 2 pi i / n_m (periodic), v = vmin + (vmax - vmin) i / (n - 1);
+     rho = 1 + a_rho prod_m sin x_m, u_j = a_u cos x_{(j+1) mod dx},
+     T = 1 + a_T cos(sum_m x_m),
+     f = rho (2 pi T)^{-dv/2} exp(-sum_j (v_j - u_j)^2 / (2 T)). */
+  int32_t dx, dv;
+  double a_rho, a_u, a_T, vmin, vmax;
+} ttc_generator;
+
+typedef enum {
+  TTC_PREC_FP64 = 0,  /* FP64 screen; pivots bit-identical to the FP64 oracle */
+  TTC_PREC_FP32 = 1,  /* FP32 screen, top-k re-scored in FP64 */
+  TTC_PREC_SPLIT = 2, /* float-float (hi/lo FP32) screen, top-k re-scored in FP64 */
+  TTC_PREC_AUTO = 3   /* FP32 for eps >= 1e-7 (of the entries' rms), else SPLIT */
+} ttc_precision;
+
+typedef struct {
+  int32_t max_rank;         /* rank capacity of every bond (default 64, <= 128) */
+  const int32_t *bond_max_rank; /* nullable host array of d-1 per-bond rank caps
+                               (prescribed ranks, e.g. (15,17,18,17,15)); copied */
+  int32_t precision;        /* ttc_precision (default TTC_PREC_FP64) */
+  int64_t nsamples;         /* error samples (default 1e6; <= 0: every entry) */
+  uint64_t seed;            /* SplitMix64 seed of the error samples (default 20240715) */
+  int32_t max_refine;       /* tau reductions before TTC_NOT_CONVERGED (default 6) */
+  int32_t topk;             /* mixed forms: candidates re-scored in FP64 per tile (default 8) */
+  int32_t host_loop;        /* 0: one persistent cooperative launch runs the whole cross
+                               (default); 1: host-stepped phases (debugging) */
+  int32_t grid_ctas;        /* persistent CTAs (0 = one wave at full occupancy) */
+  double wait_limit_s;      /* limit of every device-side wait, seconds (default 2.0) */
+} ttc_options;
+
+typedef struct {
+  int64_t sweeps;            /* residual screens (simultaneous over bonds) */
+  int64_t entries_screened;  /* candidate entries screened, summed over sweeps */
+  int64_t refinements;       /* tau reductions */
+  int64_t pivots_uncertified;/* mixed forms: pivots whose FP64 re-score could not
+                                prove them the FP64 argmax */
+  int64_t screen_fmas;       /* algorithmic FMAs of the screens: sum over sweeps and
+                                bonds of r_k * |superblock_k| */
+  int64_t error_fmas;        /* algorithmic FMAs of the sampled-error evaluations */
+  double tau;                /* final tau */
+  double x_rms;              /* rms of X over the error samples */
+  double err;                /* sampled relative Frobenius error */
+  double device_ms;          /* GPU time of the last run (events around it) */
+  int32_t status;            /* ttc_status of the last run */
+  int32_t device_error_where;/* for TTC_ERR_DEVICE_TIMEOUT: the wait that gave up */
+} ttc_stats;
+
+typedef struct ttc_handle ttc_handle;
+
+/* Fills *opt with the defaults listed above. */
+ttc_status ttcross_default_options(ttc_options *opt);
+
+/* Creates a TT-cross instance for a d-way tensor (2 <= d <= 16) with mode
+   sizes n[0..d-1] >= 1 and the entry generator *gen.  opt may be NULL
+   (defaults).  Allocates all device memory for rank capacity opt->max_rank on
+   the current CUDA device.  Errors: INVALID_ARG (shape/generator/options),
+   OOM, CUDA.  On success *out owns the instance. */
+ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen,
+                          const ttc_options *opt, ttc_handle **out);
+
+/* Runs the adaptive cross to accuracy eps (Sec. 1 eq. FrobeniusNorm, error
+   estimated as in Sec. 5) from the start pivot (0,...,0).
+   eps == 0 selects prescribed-rank mode: every bond grows to its cap.
+   max_rank (<= the capacity; <= 0 means the capacity) caps every bond.
+   subtensor_grid (nullable, d entries >= 1) splits every mode into that many
+   pieces and makes the screen's CTA tiles follow the pieces (Sec. 3); the
+   pivots do not depend on it (the global best is the best of the local bests,
+   Sec. 3.2.1).  NULL lets the library choose the tiles.
+   Asynchronous on `stream` unless opt->host_loop: it returns after the launch;
+   ttcross_sync / the getters wait for it.  Errors detected on the host are
+   returned at once; errors found on the device are reported by ttcross_sync. */
+ttc_status ttcross_run(ttc_handle *h, double eps, int max_rank,
+                       const int32_t *subtensor_grid, void *stream);
+
+/* Runs count independent instances (each created by ttcross_create) in one
+   persistent launch on `stream`.  eps[i], max_rank[i] as in ttcross_run;
+   grids may be NULL.  The handles must be distinct and live on the current
+   device. */
+ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps,
+                             const int32_t *max_rank, void *stream);
+
+/* Waits for the last run of h and returns its device-side status. */
+ttc_status ttcross_sync(ttc_handle *h);
+
+/* TT core sizes s_0..s_d (s_0 = s_d = 1) after the last run.  Waits for it. */
+ttc_status ttcross_get_ranks(ttc_handle *h, int64_t *s);
+
+/* Core k (1 <= k <= d) as [s_{k-1}][n_k][s_k] row-major doubles into dst
+   (s_{k-1} n_k s_k elements, caller-owned; device memory if dst_is_device,
+   else host memory).  Waits for the last run. */
+ttc_status ttcross_get_cores(ttc_handle *h, int k, double *dst, int dst_is_device,
+                             void *stream);
+
+/* Pivot sets of bond k (1 <= k <= d-1) in insertion order: I_{<=k} as
+   [r_k][k] and J_{>k} as [r_k][d-k] int32 host arrays (caller-owned). */
+ttc_status ttcross_get_pivots(ttc_handle *h, int k, int32_t *I, int32_t *J);
+
+/* Pivot inverse U_k = P_k^{-1} of bond k as [r_k][r_k] host doubles. */
+ttc_status ttcross_get_pivot_inverse(ttc_handle *h, int k, double *U);
+
+/* Statistics of the last run.  Waits for it. */
+ttc_status ttcross_get_stats(ttc_handle *h, ttc_stats *st);
+
+/* Frees the instance (waits for its last run).  NULL is accepted. */
+ttc_status ttcross_destroy(ttc_handle *h);
+
+/* Description of the last error on this host thread ("" if none). */
+const char *ttcross_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTCROSS_H */

@@ -1,0 +1,612 @@
+// ttc_api.cu -- the C ABI of include/ttcross.h: argument checks, the device
+// memory of an instance (one pooled allocation), and the launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ttc_internal.cuh"
+#include "ttc_launch.h"
+#include "ttcross.h"
+
+using namespace ttc;
+
+namespace {
+
+thread_local std::string g_err;
+
+ttc_status fail(ttc_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CU(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(e_ == cudaErrorMemoryAllocation ? TTC_ERR_OOM : TTC_ERR_CUDA,      \
+                  "%s failed: %s", #call, cudaGetErrorString(e_));                   \
+  } while (0)
+
+// Two-pass carving of one device allocation: the first pass (base == nullptr)
+// only measures, the second hands out 256-byte aligned pieces.
+struct Carver {
+  char *base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T *take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += sizeof(T) * (count ? count : 1);
+    return p;
+  }
+};
+
+}  // namespace
+
+struct ttc_handle {
+  int d = 0, nb = 0;
+  int64_t n[TTC_MAXD] = {};
+  ttc_options opt{};
+  int32_t bond_cap[TTC_MAXB] = {};
+  int device = 0;
+  int grid = 0;
+  InstDev hi{};                 // host copy of the device descriptor
+  InstDev *d_inst = nullptr;
+  InstDev **d_list = nullptr;   // [1] = d_inst, for single runs
+  Ctrl *d_ctrl = nullptr;
+  Barrier *d_bar = nullptr;
+  Ctrl h_ctrl{};
+  void *pool = nullptr;
+  size_t pool_bytes = 0;
+  Cand *cand = nullptr;
+  int64_t cand_cap = 0;
+  int64_t bond_cand_cap[TTC_MAXB] = {};
+  double *core_stage = nullptr;
+  int64_t core_stage_cap = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool ran = false;
+  bool events_ok = false;
+  std::vector<double> tt_cores;
+  std::vector<int32_t> tt_ranks;
+};
+
+namespace {
+
+__global__ void k_set_ctrl(Ctrl *dst, Ctrl v) { *dst = v; }
+
+int64_t cand_need(const ttc_handle *h, int b, const int32_t *grid) {
+  const int64_t capL = b == 0 ? 1 : h->bond_cap[b - 1];
+  const int64_t capR = b == h->nb - 1 ? 1 : h->bond_cap[b + 1];
+  const int32_t pr = grid ? grid[b] : 0, pc = grid ? grid[b + 1] : 0;
+  return host_tiles(h->n[b], h->n[b + 1], capL, capR, pr, pc);
+}
+
+ttc_status ensure_cands(ttc_handle *h, const int32_t *grid) {
+  int64_t need[TTC_MAXB], total = 0;
+  bool grow = false;
+  for (int b = 0; b < h->nb; ++b) {
+    need[b] = cand_need(h, b, grid);
+    if (need[b] > h->bond_cand_cap[b]) grow = true;
+  }
+  if (!grow && h->cand) return TTC_OK;
+  for (int b = 0; b < h->nb; ++b) {
+    need[b] = std::max(need[b], h->bond_cand_cap[b]);
+    total += need[b];
+  }
+  if (h->cand) {
+    CU(cudaDeviceSynchronize());
+    CU(cudaFree(h->cand));
+    h->cand = nullptr;
+  }
+  CU(cudaMalloc(&h->cand, sizeof(Cand) * (size_t)total));
+  h->cand_cap = total;
+  int64_t off = 0;
+  for (int b = 0; b < h->nb; ++b) {
+    h->bond_cand_cap[b] = need[b];
+    h->hi.bond[b].cand_base = off;
+    h->hi.bond[b].cand_cap = need[b];
+    off += need[b];
+  }
+  h->hi.cand = h->cand;
+  CU(cudaMemcpy(h->d_inst, &h->hi, sizeof(InstDev), cudaMemcpyHostToDevice));
+  return TTC_OK;
+}
+
+ttc_status check_handle(const ttc_handle *h) {
+  if (!h) return fail(TTC_ERR_INVALID_ARG, "null handle");
+  return TTC_OK;
+}
+
+Ctrl make_ctrl(const ttc_handle *h, double eps, int max_rank, const int32_t *grid) {
+  Ctrl c;
+  std::memset(&c, 0, sizeof c);
+  c.state = ST_SCREEN;
+  c.status = TTC_OK;
+  for (int b = 0; b < h->nb; ++b) {
+    int cap = h->bond_cap[b];
+    if (max_rank > 0 && max_rank < cap) cap = max_rank;
+    c.maxr[b] = cap;
+  }
+  c.eps = eps;
+  c.tau = eps;
+  c.max_refine = h->opt.max_refine;
+  for (int m = 0; m < h->d; ++m) c.grid[m] = grid ? grid[m] : 0;
+  return c;
+}
+
+ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, cudaStream_t s) {
+  ttc_handle *h0 = hs[0];
+  RunArgs ra;
+  ra.insts = d_list;
+  ra.count = count;
+  ra.bar = h0->d_bar;
+  ra.wait_ns = (int64_t)(h0->opt.wait_limit_s * 1e9);
+  ra.persistent = h0->opt.host_loop ? 0 : 1;
+  int64_t iters = 0;
+  for (int i = 0; i < count; ++i) {
+    int64_t s = hs[i]->opt.max_refine + 4;
+    for (int b = 0; b < hs[i]->nb; ++b) s += hs[i]->bond_cap[b];
+    iters = std::max(iters, s);
+  }
+  ra.max_iters = (int32_t)iters;
+  CU(cudaMemsetAsync(h0->d_bar, 0, sizeof(Barrier), s));
+  if (!h0->opt.host_loop) {
+    CU(launch_persistent(ra, h0->grid, s));
+    return TTC_OK;
+  }
+  // host-stepped: the same phases as separate launches, state read per sweep
+  CU(launch_phase(PH_INIT1, ra, h0->grid, s));
+  CU(launch_phase(PH_INIT2, ra, h0->grid, s));
+  for (int64_t it = 0; it <= ra.max_iters; ++it) {
+    bool done = true;
+    for (int i = 0; i < count; ++i) {
+      int32_t st = 0;
+      CU(cudaMemcpyAsync(&st, &hs[i]->d_ctrl->state, sizeof st, cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      if (st != ST_DONE) done = false;
+    }
+    if (done) return TTC_OK;
+    CU(launch_phase(PH_SCREEN, ra, h0->grid, s));
+    CU(launch_phase(PH_DECIDE, ra, h0->grid, s));
+    CU(launch_phase(PH_UPDATE, ra, h0->grid, s));
+  }
+  return fail(TTC_ERR_CUDA, "host-stepped run did not finish");
+}
+
+}  // namespace
+
+extern "C" {
+
+ttc_status ttcross_default_options(ttc_options *opt) {
+  if (!opt) return fail(TTC_ERR_INVALID_ARG, "null options");
+  std::memset(opt, 0, sizeof *opt);
+  opt->max_rank = 64;
+  opt->bond_max_rank = nullptr;
+  opt->precision = TTC_PREC_FP64;
+  opt->nsamples = 1000000;
+  opt->seed = 20240715ull;
+  opt->max_refine = 6;
+  opt->topk = 8;
+  opt->host_loop = 0;
+  opt->grid_ctas = 0;
+  opt->wait_limit_s = 2.0;
+  return TTC_OK;
+}
+
+const char *ttcross_last_error_string(void) { return g_err.c_str(); }
+
+ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, const ttc_options *opt,
+                          ttc_handle **out) {
+  g_err.clear();
+  if (!out) return fail(TTC_ERR_INVALID_ARG, "null output handle");
+  *out = nullptr;
+  if (d < 2 || d > TTC_MAXD) return fail(TTC_ERR_INVALID_ARG, "d=%d outside [2,%d]", d, TTC_MAXD);
+  if (!n || !gen) return fail(TTC_ERR_INVALID_ARG, "null n or generator");
+  ttc_options o;
+  if (opt) o = *opt; else ttcross_default_options(&o);
+  if (o.max_rank < 1 || o.max_rank > RCAP)
+    return fail(TTC_ERR_INVALID_ARG, "max_rank=%d outside [1,%d]", o.max_rank, RCAP);
+  if (o.precision < TTC_PREC_FP64 || o.precision > TTC_PREC_AUTO)
+    return fail(TTC_ERR_INVALID_ARG, "unknown precision %d", o.precision);
+  if (o.precision != TTC_PREC_FP64)
+    return fail(TTC_ERR_INVALID_ARG, "precision %d is not built in this library", o.precision);
+  if (o.max_refine < 0) return fail(TTC_ERR_INVALID_ARG, "max_refine < 0");
+  if (!(o.wait_limit_s > 0.0) || o.wait_limit_s > 600.0)
+    return fail(TTC_ERR_INVALID_ARG, "wait_limit_s must be in (0, 600]");
+  if (o.grid_ctas < 0 || o.grid_ctas > GRID_CAP)
+    return fail(TTC_ERR_INVALID_ARG, "grid_ctas outside [0,%d]", GRID_CAP);
+  int64_t total = 1;
+  bool overflow = false;
+  int64_t hsum = 0;
+  for (int m = 0; m < d; ++m) {
+    if (n[m] < 1 || n[m] > (1 << 24)) return fail(TTC_ERR_INVALID_ARG, "n[%d]=%lld", m, (long long)n[m]);
+    if (total > ((int64_t)1 << 62) / n[m]) overflow = true; else total *= n[m];
+    hsum += n[m] - 1;
+  }
+  if (gen->kind == TTC_GEN_HILBERT) {
+    if (hsum > (1 << 26)) return fail(TTC_ERR_INVALID_ARG, "Hilbert index sum too large");
+  } else if (gen->kind == TTC_GEN_TT) {
+    if (!gen->tt_ranks || !gen->tt_cores) return fail(TTC_ERR_INVALID_ARG, "TT generator without cores");
+    if (gen->tt_ranks[0] != 1 || gen->tt_ranks[d] != 1)
+      return fail(TTC_ERR_INVALID_ARG, "TT ranks must start and end with 1");
+    for (int m = 1; m < d; ++m)
+      if (gen->tt_ranks[m] < 1 || gen->tt_ranks[m] > 32)
+        return fail(TTC_ERR_INVALID_ARG, "TT generator ranks must be in [1,32]");
+  } else if (gen->kind == TTC_GEN_MAXWELLIAN) {
+    if (gen->dx < 1 || gen->dv < 1 || gen->dx + gen->dv != d)
+      return fail(TTC_ERR_INVALID_ARG, "Maxwellian needs dx, dv >= 1 and dx + dv = d");
+    for (int m = gen->dx; m < d; ++m)
+      if (n[m] < 2) return fail(TTC_ERR_INVALID_ARG, "velocity modes need n >= 2");
+  } else {
+    return fail(TTC_ERR_INVALID_ARG, "unknown generator kind %d", gen->kind);
+  }
+  if (overflow) return fail(TTC_ERR_INVALID_ARG, "more than 2^62 entries: linear index overflows");
+  const bool exhaustive = o.nsamples <= 0 || (!overflow && o.nsamples >= total);
+  if (exhaustive && (overflow || total > (int64_t)1 << 30))
+    return fail(TTC_ERR_INVALID_ARG, "every-entry error on %s entries", overflow ? "> 2^63" : "> 2^30");
+  const int64_t ns = exhaustive ? total : o.nsamples;
+
+  ttc_handle *h = new ttc_handle();
+  h->d = d;
+  h->nb = d - 1;
+  for (int m = 0; m < d; ++m) h->n[m] = n[m];
+  h->opt = o;
+  for (int b = 0; b < d - 1; ++b) {
+    int cap = o.max_rank;
+    if (o.bond_max_rank) {
+      if (o.bond_max_rank[b] < 1 || o.bond_max_rank[b] > RCAP) {
+        delete h;
+        return fail(TTC_ERR_INVALID_ARG, "bond_max_rank[%d]=%d", b, o.bond_max_rank[b]);
+      }
+      cap = std::max(cap, (int)o.bond_max_rank[b]);
+    }
+    h->bond_cap[b] = cap;
+  }
+  h->opt.bond_max_rank = nullptr;
+  std::vector<int32_t> bcaps;
+  if (o.bond_max_rank) bcaps.assign(o.bond_max_rank, o.bond_max_rank + d - 1);
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return fail(TTC_ERR_CUDA, "no CUDA device");
+  }
+  // persistent grid: one wave at full occupancy
+  int bps = 0, nsm = 0;
+  cudaError_t ce = persistent_occupancy(&bps);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  if (ce != cudaSuccess || bps < 1) {
+    delete h;
+    return fail(TTC_ERR_CUDA, "occupancy query failed: %s", cudaGetErrorString(ce));
+  }
+  h->grid = std::min(bps * nsm, GRID_CAP);
+  if (o.grid_ctas > 0) h->grid = std::min(h->grid, o.grid_ctas);
+
+  // ---- device memory: one pool ----
+  InstDev &I = h->hi;
+  std::memset(&I, 0, sizeof I);
+  I.d = d;
+  I.nb = d - 1;
+  int64_t st = 1;
+  for (int m = 0; m < d; ++m) {
+    I.n[m] = n[m];
+    I.stride[m] = st;
+    st = overflow ? st : st * n[m];
+  }
+  I.gen = gen->kind;
+  I.prec = o.precision;
+  I.topk = o.topk;
+  I.nsamples = ns;
+  I.exhaustive = exhaustive ? 1 : 0;
+  I.seed = o.seed;
+  if (gen->kind == TTC_GEN_MAXWELLIAN) {
+    I.dx = gen->dx; I.dv = gen->dv;
+    I.a_rho = gen->a_rho; I.a_u = gen->a_u; I.a_T = gen->a_T;
+    I.vmin = gen->vmin; I.vmax = gen->vmax;
+  }
+  int64_t tt_total = 0;
+  if (gen->kind == TTC_GEN_TT) {
+    for (int m = 0; m <= d; ++m) I.rho[m] = gen->tt_ranks[m];
+    for (int m = 0; m < d; ++m) {
+      I.core_off[m] = tt_total;
+      tt_total += (int64_t)I.rho[m] * n[m] * I.rho[m + 1];
+    }
+  }
+  const int64_t hlen = gen->kind == TTC_GEN_HILBERT ? hsum + 1 : 1;
+  int64_t core_cap = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    Carver cv;
+    cv.base = static_cast<char *>(h->pool);
+    Ctrl *ctrl = cv.take<Ctrl>(1);
+    Barrier *bar = cv.take<Barrier>(1);
+    InstDev *dinst = cv.take<InstDev>(1);
+    InstDev **dlist = cv.take<InstDev *>(1);
+    double *hilb = cv.take<double>(hlen);
+    double *tt = cv.take<double>(tt_total);
+    double *xs = cv.take<double>(ns);
+    double *errp = cv.take<double>(GRID_CAP);
+    int32_t *eidx = cv.take<int32_t>(TTC_MAXD);
+    int64_t *elin = cv.take<int64_t>(1);
+    int32_t *esum = cv.take<int32_t>(1);
+    for (int b = 0; b < d - 1; ++b) {
+      BondDev &B = I.bond[b];
+      const int64_t cap = h->bond_cap[b];
+      const int64_t capL = b == 0 ? 1 : h->bond_cap[b - 1];
+      const int64_t capR = b == d - 2 ? 1 : h->bond_cap[b + 1];
+      B.cap = (int32_t)cap;
+      B.ldT = capL * n[b];
+      B.ldR = n[b + 1] * capR;
+      B.T = cv.take<double>(cap * B.ldT);
+      B.R = cv.take<double>(cap * B.ldR);
+      B.U = cv.take<double>(cap * cap);
+      B.hpiv = cv.take<double>(cap * cap);
+      B.hc = cv.take<double>(cap * cap);
+      B.delta = cv.take<double>(cap);
+      B.prow = cv.take<int32_t>(cap);
+      B.pcol = cv.take<int32_t>(cap);
+      B.I.width = b + 1;
+      B.I.idx = cv.take<int32_t>(cap * (b + 1));
+      B.I.lin = cv.take<int64_t>(cap);
+      B.I.sum = cv.take<int32_t>(cap);
+      B.J.width = d - 1 - b;
+      B.J.idx = cv.take<int32_t>(cap * (d - 1 - b));
+      B.J.lin = cv.take<int64_t>(cap);
+      B.J.sum = cv.take<int32_t>(cap);
+      B.Thi = B.Tlo = B.Rhi = B.Rlo = nullptr;
+      core_cap = std::max(core_cap, B.ldT * cap);
+    }
+    core_cap = std::max(core_cap, h->bond_cap[d - 2] * n[d - 1]);
+    double *stage = cv.take<double>(core_cap);
+    if (pass == 0) {
+      h->pool_bytes = cv.off;
+      cudaError_t e = cudaMalloc(&h->pool, h->pool_bytes);
+      if (e != cudaSuccess) {
+        delete h;
+        return fail(e == cudaErrorMemoryAllocation ? TTC_ERR_OOM : TTC_ERR_CUDA,
+                    "cudaMalloc(%zu) failed: %s", cv.off, cudaGetErrorString(e));
+      }
+    } else {
+      h->d_ctrl = ctrl;
+      h->d_bar = bar;
+      h->d_inst = dinst;
+      h->d_list = dlist;
+      I.hilb = hilb;
+      I.tt = tt;
+      I.xs = xs;
+      I.err_part = errp;
+      I.err_part_cap = GRID_CAP;
+      I.empty.idx = eidx;
+      I.empty.lin = elin;
+      I.empty.sum = esum;
+      I.empty.width = 0;
+      I.ctrl = ctrl;
+      h->core_stage = stage;
+      h->core_stage_cap = core_cap;
+    }
+  }
+  auto cleanup = [&](ttc_status s) {
+    cudaFree(h->pool);
+    if (h->cand) cudaFree(h->cand);
+    delete h;
+    return s;
+  };
+  if (cudaMemset(h->pool, 0, h->pool_bytes) != cudaSuccess)
+    return cleanup(fail(TTC_ERR_CUDA, "cudaMemset failed"));
+  if (gen->kind == TTC_GEN_HILBERT) {
+    std::vector<double> tab(hlen);
+    for (int64_t s = 0; s < hlen; ++s) tab[s] = 1.0 / (double)(s + 1);
+    if (cudaMemcpy((void *)I.hilb, tab.data(), sizeof(double) * hlen, cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return cleanup(fail(TTC_ERR_CUDA, "copy of the Hilbert table failed"));
+  }
+  if (gen->kind == TTC_GEN_TT) {
+    if (cudaMemcpy((void *)I.tt, gen->tt_cores, sizeof(double) * tt_total, cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return cleanup(fail(TTC_ERR_CUDA, "copy of the TT cores failed"));
+  }
+  InstDev *lst[1] = {h->d_inst};
+  if (cudaMemcpy(h->d_list, lst, sizeof lst, cudaMemcpyHostToDevice) != cudaSuccess)
+    return cleanup(fail(TTC_ERR_CUDA, "copy of the instance list failed"));
+  ttc_status s = ensure_cands(h, nullptr);
+  if (s != TTC_OK) return cleanup(s);
+  if (cudaEventCreate(&h->ev0) == cudaSuccess && cudaEventCreate(&h->ev1) == cudaSuccess)
+    h->events_ok = true;
+  if (!bcaps.empty()) {
+    // per-bond caps become the default caps of every run
+    for (int b = 0; b < d - 1; ++b) h->bond_cap[b] = std::min(h->bond_cap[b], bcaps[b]);
+  }
+  *out = h;
+  return TTC_OK;
+}
+
+ttc_status ttcross_run(ttc_handle *h, double eps, int max_rank, const int32_t *subtensor_grid,
+                       void *stream) {
+  g_err.clear();
+  ttc_status s = check_handle(h);
+  if (s) return s;
+  if (!(eps >= 0.0) || !std::isfinite(eps) || eps >= 1.0)
+    return fail(TTC_ERR_INVALID_ARG, "eps=%g must be in [0,1)", eps);
+  if (subtensor_grid)
+    for (int m = 0; m < h->d; ++m)
+      if (subtensor_grid[m] < 1 || subtensor_grid[m] > h->n[m])
+        return fail(TTC_ERR_INVALID_ARG, "subtensor_grid[%d]=%d outside [1,n]", m, subtensor_grid[m]);
+  int dev = -1;
+  CU(cudaGetDevice(&dev));
+  if (dev != h->device) return fail(TTC_ERR_INVALID_ARG, "handle lives on device %d", h->device);
+  s = ensure_cands(h, subtensor_grid);
+  if (s) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ctrl c = make_ctrl(h, eps, max_rank, subtensor_grid);
+  k_set_ctrl<<<1, 1, 0, st>>>(h->d_ctrl, c);
+  CU(cudaGetLastError());
+  if (h->events_ok) CU(cudaEventRecord(h->ev0, st));
+  ttc_handle *hs[1] = {h};
+  s = launch_run(hs, 1, h->d_list, st);
+  if (s) return s;
+  if (h->events_ok) CU(cudaEventRecord(h->ev1, st));
+  h->stream = st;
+  h->ran = true;
+  return TTC_OK;
+}
+
+ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps,
+                             const int32_t *max_rank, void *stream) {
+  g_err.clear();
+  if (!hs || count < 1 || !eps) return fail(TTC_ERR_INVALID_ARG, "bad batch arguments");
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return fail(TTC_ERR_INVALID_ARG, "null handle %d", i);
+    if (!(eps[i] >= 0.0) || eps[i] >= 1.0) return fail(TTC_ERR_INVALID_ARG, "eps[%d]", i);
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(TTC_ERR_INVALID_ARG, "handle %d repeated", i);
+    if (hs[i]->device != hs[0]->device) return fail(TTC_ERR_INVALID_ARG, "handles on different devices");
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < count; ++i) {
+    ttc_status s = ensure_cands(hs[i], nullptr);
+    if (s) return s;
+    Ctrl c = make_ctrl(hs[i], eps[i], max_rank ? max_rank[i] : 0, nullptr);
+    k_set_ctrl<<<1, 1, 0, st>>>(hs[i]->d_ctrl, c);
+    CU(cudaGetLastError());
+  }
+  std::vector<InstDev *> lst(count);
+  for (int i = 0; i < count; ++i) lst[i] = hs[i]->d_inst;
+  InstDev **d_list = nullptr;
+  CU(cudaMallocAsync((void **)&d_list, sizeof(InstDev *) * count, st));
+  CU(cudaMemcpyAsync(d_list, lst.data(), sizeof(InstDev *) * count, cudaMemcpyHostToDevice, st));
+  CU(cudaStreamSynchronize(st));  // the host vector dies at return
+  ttc_handle *h0 = hs[0];
+  if (h0->events_ok) CU(cudaEventRecord(h0->ev0, st));
+  ttc_status s = launch_run(hs, count, d_list, st);
+  if (h0->events_ok) cudaEventRecord(h0->ev1, st);
+  cudaFreeAsync(d_list, st);
+  if (s) return s;
+  for (int i = 0; i < count; ++i) {
+    hs[i]->stream = st;
+    hs[i]->ran = true;
+  }
+  return TTC_OK;
+}
+
+ttc_status ttcross_sync(ttc_handle *h) {
+  ttc_status s = check_handle(h);
+  if (s) return s;
+  if (!h->ran) return fail(TTC_ERR_INVALID_ARG, "no run to wait for");
+  CU(cudaStreamSynchronize(h->stream));
+  CU(cudaMemcpy(&h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+  Barrier bar;
+  CU(cudaMemcpy(&bar, h->d_bar, sizeof bar, cudaMemcpyDeviceToHost));
+  if (bar.abort) {
+    h->h_ctrl.status = TTC_ERR_DEVICE_TIMEOUT;
+    return fail(TTC_ERR_DEVICE_TIMEOUT, "a device-side wait ran past %.3g s (wait %d)",
+                h->opt.wait_limit_s, bar.where);
+  }
+  if (bar.overrun) return fail(TTC_ERR_CUDA, "sweep cap reached before the run finished");
+  if (h->h_ctrl.state != ST_DONE)
+    return fail(TTC_ERR_CUDA, "run ended without finishing (state %d)", h->h_ctrl.state);
+  return (ttc_status)h->h_ctrl.status;
+}
+
+static ttc_status synced(ttc_handle *h) {
+  ttc_status s = ttcross_sync(h);
+  if (s == TTC_OK || s == TTC_NOT_CONVERGED) return TTC_OK;
+  if (s == TTC_ERR_CUDA || s == TTC_ERR_INVALID_ARG) return s;
+  return TTC_OK;  // device-side failures still leave a readable state
+}
+
+ttc_status ttcross_get_ranks(ttc_handle *h, int64_t *sz) {
+  ttc_status s = synced(h);
+  if (s) return s;
+  if (!sz) return fail(TTC_ERR_INVALID_ARG, "null output");
+  sz[0] = 1;
+  for (int b = 0; b < h->nb; ++b) sz[b + 1] = h->h_ctrl.r[b];
+  sz[h->d] = 1;
+  return TTC_OK;
+}
+
+ttc_status ttcross_get_cores(ttc_handle *h, int k, double *dst, int dst_is_device, void *stream) {
+  ttc_status s = synced(h);
+  if (s) return s;
+  if (k < 1 || k > h->d || !dst) return fail(TTC_ERR_INVALID_ARG, "core k=%d", k);
+  const int m = k - 1;
+  const int64_t sl = m == 0 ? 1 : h->h_ctrl.r[m - 1];
+  const int64_t sr = m == h->d - 1 ? 1 : h->h_ctrl.r[m];
+  const int64_t cnt = sl * h->n[m] * sr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (dst_is_device) {
+    CU(launch_core(h->d_inst, m, dst, st));
+    return TTC_OK;
+  }
+  if (cnt > h->core_stage_cap) return fail(TTC_ERR_INVALID_ARG, "core larger than its capacity");
+  CU(launch_core(h->d_inst, m, h->core_stage, st));
+  CU(cudaMemcpyAsync(dst, h->core_stage, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return TTC_OK;
+}
+
+ttc_status ttcross_get_pivots(ttc_handle *h, int k, int32_t *Iout, int32_t *Jout) {
+  ttc_status s = synced(h);
+  if (s) return s;
+  if (k < 1 || k > h->nb) return fail(TTC_ERR_INVALID_ARG, "bond k=%d", k);
+  const int b = k - 1;
+  const int64_t r = h->h_ctrl.r[b];
+  if (Iout) CU(cudaMemcpy(Iout, h->hi.bond[b].I.idx, sizeof(int32_t) * r * k, cudaMemcpyDeviceToHost));
+  if (Jout)
+    CU(cudaMemcpy(Jout, h->hi.bond[b].J.idx, sizeof(int32_t) * r * (h->d - k), cudaMemcpyDeviceToHost));
+  return TTC_OK;
+}
+
+ttc_status ttcross_get_pivot_inverse(ttc_handle *h, int k, double *U) {
+  ttc_status s = synced(h);
+  if (s) return s;
+  if (k < 1 || k > h->nb || !U) return fail(TTC_ERR_INVALID_ARG, "bond k=%d", k);
+  const BondDev &B = h->hi.bond[k - 1];
+  const int64_t r = h->h_ctrl.r[k - 1];
+  CU(cudaMemcpy2D(U, sizeof(double) * r, B.U, sizeof(double) * B.cap, sizeof(double) * r, r,
+                  cudaMemcpyDeviceToHost));
+  return TTC_OK;
+}
+
+ttc_status ttcross_get_stats(ttc_handle *h, ttc_stats *out) {
+  if (!h || !out) return fail(TTC_ERR_INVALID_ARG, "null argument");
+  std::memset(out, 0, sizeof *out);
+  ttc_status s = ttcross_sync(h);
+  const Ctrl &c = h->h_ctrl;
+  out->sweeps = c.sweeps;
+  out->entries_screened = c.entries;
+  out->refinements = c.refinements;
+  out->pivots_uncertified = c.uncertified;
+  out->screen_fmas = c.screen_fmas;
+  out->error_fmas = c.error_fmas;
+  out->tau = c.tau;
+  out->x_rms = c.xrms;
+  out->err = c.err;
+  out->status = s;
+  float ms = 0.f;
+  if (h->events_ok && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) out->device_ms = ms;
+  Barrier bar;
+  if (cudaMemcpy(&bar, h->d_bar, sizeof bar, cudaMemcpyDeviceToHost) == cudaSuccess)
+    out->device_error_where = bar.where;
+  return TTC_OK;
+}
+
+ttc_status ttcross_destroy(ttc_handle *h) {
+  if (!h) return TTC_OK;
+  if (h->ran) cudaStreamSynchronize(h->stream);
+  if (h->events_ok) {
+    cudaEventDestroy(h->ev0);
+    cudaEventDestroy(h->ev1);
+  }
+  if (h->cand) cudaFree(h->cand);
+  if (h->pool) cudaFree(h->pool);
+  delete h;
+  return TTC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// ttc_gen.cuh -- tensor entries X(i) evaluated on the device (Sec. 5: the
+// tensor is a function of its indices and is never formed).
+#pragma once
+#include "ttc_internal.cuh"
+
+namespace ttc {
+
+// TT given by cores: left-to-right product of the slices, each dot product a
+// serial FMA chain (device ranks <= 32).
+__device__ __noinline__ double gen_tt(const InstDev &in, const int32_t *idx) {
+  double v[32], w[32];
+  const int d = in.d;
+  int rl = in.rho[1];
+  const double *G0 = in.tt + in.core_off[0];
+  for (int t = 0; t < rl; ++t) v[t] = G0[(int64_t)idx[0] * rl + t];
+  for (int m = 1; m < d; ++m) {
+    const int ra = in.rho[m], rb = in.rho[m + 1];
+    const double *G = in.tt + in.core_off[m];
+    for (int q = 0; q < rb; ++q) {
+      double acc = 0.0;
+      const double *g = G + (int64_t)idx[m] * rb + q;
+      const int64_t sg = in.n[m] * rb;
+      for (int t = 0; t < ra; ++t) acc = __fma_rn(v[t], g[t * sg], acc);
+      w[q] = acc;
+    }
+    for (int q = 0; q < rb; ++q) v[q] = w[q];
+  }
+  return v[0];
+}
+
+// Maxwellian f(x,v) = rho(x) (2 pi T(x))^{-dv/2} exp(-|v - u(x)|^2 / (2 T(x)))
+__device__ __noinline__ double gen_maxwellian(const InstDev &in, const int32_t *idx) {
+  const double two_pi = 6.283185307179586476925286766559;
+  double x[TTC_MAXD];
+  double prod_sin = 1.0, sum_x = 0.0;
+  for (int m = 0; m < in.dx; ++m) {
+    x[m] = __dmul_rn(two_pi, (double)idx[m]) / (double)in.n[m];
+    prod_sin = __dmul_rn(prod_sin, sin(x[m]));
+    sum_x = __dadd_rn(sum_x, x[m]);
+  }
+  const double rho = __dadd_rn(1.0, __dmul_rn(in.a_rho, prod_sin));
+  const double T = __dadd_rn(1.0, __dmul_rn(in.a_T, cos(sum_x)));
+  double q = 0.0;
+  for (int j = 0; j < in.dv; ++j) {
+    const int m = in.dx + j;
+    const double v = __dadd_rn(in.vmin, __dmul_rn(__dsub_rn(in.vmax, in.vmin), (double)idx[m]) /
+                                            (double)(in.n[m] - 1));
+    const double u = __dmul_rn(in.a_u, cos(x[(j + 1) % in.dx]));
+    const double dvu = __dsub_rn(v, u);
+    q = __dadd_rn(q, __dmul_rn(dvu, dvu));
+  }
+  return __dmul_rn(rho / pow(__dmul_rn(two_pi, T), 0.5 * (double)in.dv),
+                   exp(-q / __dmul_rn(2.0, T)));
+}
+
+__device__ __forceinline__ double gen_full(const InstDev &in, const int32_t *idx) {
+  if (in.gen == 0) {
+    int s = 0;
+    for (int m = 0; m < in.d; ++m) s += idx[m];
+    return in.hilb[s];
+  }
+  if (in.gen == 1) return gen_tt(in, idx);
+  return gen_maxwellian(in, idx);
+}
+
+// Entry (a, c) of the superblock of bond b: rows a = p*n_b + i (p indexes
+// I_{<=k-1}), columns c = q*n_{b+1} + j (q indexes J_{>k+1}), Alg. 2.
+__device__ __noinline__ double sb_entry(const InstDev &in, int b, int64_t a, int64_t c) {
+  const int64_t nb0 = in.n[b], nb1 = in.n[b + 1];
+  const int64_t p = a / nb0, i = a - p * nb0;
+  const int64_t q = c / nb1, j = c - q * nb1;
+  const SetDev &L = left_set(in, b);
+  const SetDev &Rs = right_set(in, b);
+  if (in.gen == 0) return in.hilb[L.sum[p] + (int)i + (int)j + Rs.sum[q]];
+  int32_t idx[TTC_MAXD];
+  for (int m = 0; m < b; ++m) idx[m] = L.idx[p * b + m];
+  idx[b] = (int32_t)i;
+  idx[b + 1] = (int32_t)j;
+  const int w = in.d - b - 2;
+  for (int m = 0; m < w; ++m) idx[b + 2 + m] = Rs.idx[q * w + m];
+  return gen_full(in, idx);
+}
+
+// Multi-index of error sample k (SplitMix64 counter form, sample-major,
+// mode-minor; index = floor(x * n / 2^64)), or entry k in column-major
+// order when the error runs over every entry.
+__device__ __forceinline__ void sample_index(const InstDev &in, int64_t k, int32_t *idx) {
+  if (in.exhaustive) {
+    int64_t l = k;
+    for (int m = 0; m < in.d; ++m) {
+      idx[m] = (int32_t)(l % in.n[m]);
+      l /= in.n[m];
+    }
+  } else {
+    for (int m = 0; m < in.d; ++m) {
+      const uint64_t x = splitmix64_at(in.seed, (uint64_t)(k * in.d + m));
+      idx[m] = (int32_t)__umul64hi(x, (uint64_t)in.n[m]);
+    }
+  }
+}
+
+}  // namespace ttc

@@ -1,0 +1,165 @@
+// ttc_internal.cuh -- device-side data layout and helpers of the TT cross.
+//
+// Layout in HBM (one instance; capacities fixed at create so one persistent
+// launch can run the whole cross without reallocating):
+//   bond b (paper's k = b+1), rank cap R_b, superblock rows a = p*n_b + i
+//   (p indexes I_{<=k-1}), columns c = q*n_{b+1} + j (q indexes J_{>k+1}):
+//     T  [R_b][ldT]  FP64, t-major: column t of T_k = C_k P_k^{-1} is contiguous
+//     R  [R_b][ldR]  FP64: row t = X(I_{<=k}[t], superblock columns)
+//     Thi/Tlo, Rhi/Rlo: FP32 (hi, lo) shadows of T and R for the mixed screens
+//     U  [R_b][R_b]  P_k^{-1} (bordered Sherman-Morrison, Sec. 3.1.1)
+//     hpiv/hc [R_b][R_b], delta[R_b]: pivot history replayed by Alg. 4
+//     I, J: pivot multi-indices + column-major linear index + index sum
+//   ldT = cap(R_{b-1}) * n_b and ldR = n_{b+1} * cap(R_{b+1}), so rows and
+//   columns that enter the superblock later are appended, never moved.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define TTC_MAXD 16
+#define TTC_MAXB (TTC_MAXD - 1)
+
+namespace ttc {
+
+constexpr int BM = 64, BN = 64;   // screen tile (superblock rows x columns)
+constexpr int RCAP = 128;         // largest rank capacity the kernels accept
+constexpr int GRID_CAP = 4096;    // largest persistent grid (partial-sum slots)
+
+enum State : int32_t { ST_SCREEN = 0, ST_UPDATE = 1, ST_VERIFY = 2, ST_DONE = 3 };
+enum Prec : int32_t { P_FP64 = 0, P_FP32 = 1, P_SPLIT = 2 };
+
+struct SetDev {          // pivot index set I_{<=k} or J_{>k}
+  int32_t *idx;          // [cap][width] mode indices
+  int64_t *lin;          // [cap] part of the column-major linear index
+  int32_t *sum;          // [cap] sum of the indices (Hilbert)
+  int32_t width;
+};
+
+struct BondDev {
+  int32_t cap;
+  int64_t ldT, ldR;      // row / column capacity of the superblock
+  double *T, *R, *U, *hpiv, *hc, *delta;
+  float *Thi, *Tlo, *Rhi, *Rlo;
+  int32_t *prow, *pcol;  // pivot superblock coordinates, insertion order
+  SetDev I, J;
+  int64_t cand_base;     // first candidate slot of this bond
+  int64_t cand_cap;      // candidate slots of this bond
+};
+
+// Per-instance control block; written by the device, read by the host.
+struct Ctrl {
+  int32_t state;
+  int32_t status;
+  int32_t r[TTC_MAXD];     // current ranks (bond b)
+  int32_t r_old[TTC_MAXD]; // ranks before the last pivot step
+  int32_t add[TTC_MAXD];   // bond added a pivot in the last decision
+  int32_t maxr[TTC_MAXD];  // rank caps of this run
+  int32_t ntiles[TTC_MAXD];// tiles screened for bond b in the last screen
+  uint64_t best_key[TTC_MAXD];
+  int64_t best_lin[TTC_MAXD];
+  int32_t best_row[TTC_MAXD], best_col[TTC_MAXD];
+  double eps, tau, xrms, den, err;
+  int64_t sweeps, entries, refinements, uncertified;
+  int64_t screen_fmas, error_fmas;  // algorithmic FMAs of the screens / errors
+  int32_t max_refine;
+  int32_t grid[TTC_MAXD];  // subtensor pieces per mode (0 = library tiles)
+  int32_t pad;
+};
+
+struct InstDev {
+  int32_t d, nb;
+  int64_t n[TTC_MAXD], stride[TTC_MAXD];
+  int32_t gen;                       // ttc_gen_kind
+  const double *hilb;                // [sum_m (n_m-1) + 1] = 1/(s+1)
+  const float *hilb_hi, *hilb_lo;    // its (hi, lo) FP32 split
+  const double *tt;                  // TT cores
+  int32_t rho[TTC_MAXD + 1];
+  int64_t core_off[TTC_MAXD + 1];
+  int32_t dx, dv;
+  double a_rho, a_u, a_T, vmin, vmax;
+  int32_t prec;
+  int32_t topk;
+  BondDev bond[TTC_MAXB];
+  SetDev empty;                      // I_{<=0} / J_{>d}: one empty multi-index
+  double *xs;                        // X at the error samples
+  int64_t nsamples;                  // samples used (== prod n when exhaustive)
+  int32_t exhaustive;
+  uint64_t seed;
+  double *err_part;                  // [max grid] partial sums
+  int32_t err_part_cap;
+  struct Cand *cand;
+  Ctrl *ctrl;
+};
+
+struct Cand {            // one screen candidate (max |E| of a tile, or top-k)
+  uint64_t key;          // bits of |E| (FP64 or FP32 widened), larger wins
+  int64_t lin;           // column-major linear index, smaller wins ties
+  int32_t row, col;      // superblock coordinates
+};
+
+struct Barrier {
+  unsigned int count;
+  unsigned int gen;
+  int32_t abort;
+  int32_t where;         // first wait that ran out
+  int32_t overrun;       // the sweep cap was reached before every instance finished
+};
+
+struct RunArgs {
+  InstDev *const *insts; // device array of instance pointers
+  int32_t count;
+  Barrier *bar;
+  int64_t wait_ns;
+  int32_t persistent;
+  int32_t max_iters;     // sweep cap of the launch (sum of rank caps + refinements)
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// key order: larger |E| first, then smaller linear index
+__device__ __forceinline__ bool key_better(uint64_t k1, int64_t l1, uint64_t k2, int64_t l2) {
+  return k1 > k2 || (k1 == k2 && l1 < l2);
+}
+
+__device__ __forceinline__ uint64_t abs_key(double e) {
+  return (uint64_t)__double_as_longlong(e) & 0x7FFFFFFFFFFFFFFFull;
+}
+// +Inf bit pattern: keys above it are NaN
+constexpr uint64_t KEY_INF = 0x7FF0000000000000ull;
+
+// The contract's dot product: acc = +0; acc = fma(x[t], y[t], acc), t = 0..K-1
+__device__ __forceinline__ double chain(const double *x, int64_t sx, const double *y, int64_t sy,
+                                        int K) {
+  double acc = 0.0;
+  for (int t = 0; t < K; ++t) acc = __fma_rn(x[t * sx], y[t * sy], acc);
+  return acc;
+}
+
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int64_t rows_of(const InstDev &in, const int32_t *r, int b) {
+  return (int64_t)(b == 0 ? 1 : r[b - 1]) * in.n[b];
+}
+__device__ __forceinline__ int64_t cols_of(const InstDev &in, const int32_t *r, int b) {
+  return in.n[b + 1] * (int64_t)(b == in.nb - 1 ? 1 : r[b + 1]);
+}
+__device__ __forceinline__ const SetDev &left_set(const InstDev &in, int b) {
+  return b == 0 ? in.empty : in.bond[b - 1].I;
+}
+__device__ __forceinline__ const SetDev &right_set(const InstDev &in, int b) {
+  return b == in.nb - 1 ? in.empty : in.bond[b + 1].J;
+}
+
+}  // namespace ttc

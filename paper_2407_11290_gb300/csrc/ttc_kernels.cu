@@ -1,0 +1,940 @@
+// ttc_kernels.cu -- the hot path of the adaptive TT cross on sm_103a.
+//
+// One sweep (all bonds at once, Sec. 3.2.3) is three phases:
+//   screen : every CTA takes superblock tiles of every bond (the paper's
+//            subtensors of Alg. 3 become CTA tiles), generates the entries,
+//            forms E = A - T R with the FP64 FMA chain of the arithmetic
+//            contract (or the FP32 / float-float forms), and keeps the tile's
+//            max |E| (ties: lowest column-major linear index);
+//   decide : one CTA per instance merges the tile candidates (the Allgather
+//            of Alg. 3), applies the stop test and appends the pivots:
+//            nested index sets (eq. nestedpivots), pivot history, and the
+//            bordered Sherman-Morrison update of P^{-1} (Sec. 3.1.1);
+//   update : every CTA applies eq. aca_approx_T_sub to the old rows of T,
+//            replays the pivot history on rows that entered the superblock
+//            (Alg. 4), and generates the new rows / columns of R; or, when an
+//            instance has converged at its threshold, evaluates the sampled
+//            error of Sec. 5.
+// The phases run either in one persistent cooperative launch separated by
+// grid barriers (every wait bounded in time) or as separate launches.
+#include <cfloat>
+#include <climits>
+
+#include "ttc_gen.cuh"
+#include "ttc_internal.cuh"
+#include "ttc_launch.h"
+
+namespace ttc {
+
+constexpr int NT = 256;  // threads per CTA
+constexpr int KC = 32;   // depth of the T / R chunks staged in shared memory
+
+struct ScreenSmem {
+  double Ts[KC][BM];
+  double Rs[KC][BN];
+  int32_t srow[BM], scol[BN];
+  int64_t lrow[BM], lcol[BN];
+  int32_t ridx[BM][TTC_MAXD];
+  int32_t cidx[BN][TTC_MAXD];
+};
+
+struct DecideSmem {
+  double ua[RCAP], bu[RCAP], brow[RCAP];
+  double red[NT / 32];
+  uint64_t rk[NT / 32];
+  int64_t rl[NT / 32];
+  int32_t rr[NT / 32], rc[NT / 32];
+  double delta;
+  int32_t flag;
+};
+
+union __align__(16) PhaseSmem {
+  ScreenSmem s;
+  DecideSmem d;
+  double red[NT / 32];
+};
+
+// ---------------------------------------------------------------------------
+// reductions
+
+struct KeyBest {
+  uint64_t key;
+  int64_t lin;
+  int32_t row, col;
+};
+
+__device__ __forceinline__ void kb_take(KeyBest &a, const KeyBest &b) {
+  if (b.row >= 0 && (a.row < 0 || key_better(b.key, b.lin, a.key, a.lin))) a = b;
+}
+
+// block-wide max by key; result valid in thread 0
+__device__ KeyBest block_best(KeyBest v, uint64_t *sk, int64_t *sl, int32_t *sr, int32_t *sc) {
+  for (int off = 16; off > 0; off >>= 1) {
+    KeyBest o;
+    o.key = __shfl_down_sync(0xffffffffu, v.key, off);
+    o.lin = __shfl_down_sync(0xffffffffu, v.lin, off);
+    o.row = __shfl_down_sync(0xffffffffu, v.row, off);
+    o.col = __shfl_down_sync(0xffffffffu, v.col, off);
+    kb_take(v, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { sk[w] = v.key; sl[w] = v.lin; sr[w] = v.row; sc[w] = v.col; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < NT / 32; ++i) {
+      KeyBest o{sk[i], sl[i], sr[i], sc[i]};
+      kb_take(v, o);
+    }
+  }
+  return v;
+}
+
+// deterministic block sum (fixed shuffle tree, warps summed in order)
+__device__ double block_sum(double v, double *red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NT / 32; ++i) s += red[i];
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// grid barrier for the persistent form: arrive, then wait for the generation
+// to change; every wait gives up after wait_ns and raises the abort flag.
+__device__ bool grid_barrier(const RunArgs &ra, int where) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    Barrier *bar = ra.bar;
+    volatile unsigned int *vgen = &bar->gen;
+    volatile int32_t *vabort = &bar->abort;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      const uint64_t t0 = globaltimer_ns();
+      while (*vgen == g) {
+        if (*vabort) { ok = 0; break; }
+        __nanosleep(100);
+        if (globaltimer_ns() - t0 > (uint64_t)ra.wait_ns) {
+          atomicCAS(&bar->where, 0, where);
+          atomicExch(&bar->abort, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (*vabort) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// tiles of the superblock of bond b.  Without a subtensor grid the rows
+// (columns) are cut into BM (BN) chunks; with one, mode b (b+1) is split into
+// grid[b] (grid[b+1]) balanced pieces and no tile crosses a piece.
+
+struct TileGeo {
+  int64_t nrt, nct;        // row tiles, column tiles
+  int64_t rows, cols;
+  int32_t pr, pc;          // pieces (0 = none)
+  int64_t rtpb, ctpb;      // tiles per block of n_b rows / n_{b+1} columns
+};
+
+__device__ __forceinline__ int64_t piece_tiles(int64_t n, int32_t C, int64_t T) {
+  int64_t s = 0;
+  for (int32_t k = 0; k < C; ++k) {
+    const int64_t lo = n * k / C, hi = n * (k + 1) / C;
+    s += (hi - lo + T - 1) / T;
+  }
+  return s;
+}
+
+__device__ __forceinline__ void piece_locate(int64_t n, int32_t C, int64_t T, int64_t t,
+                                             int64_t &start, int64_t &len) {
+  for (int32_t k = 0; k < C; ++k) {
+    const int64_t lo = n * k / C, hi = n * (k + 1) / C;
+    const int64_t nt = (hi - lo + T - 1) / T;
+    if (t < nt) {
+      start = lo + t * T;
+      len = min(T, hi - start);
+      return;
+    }
+    t -= nt;
+  }
+  start = 0;
+  len = 0;
+}
+
+__device__ TileGeo tile_geo(const InstDev &in, const Ctrl &cr, const int32_t *r, int b) {
+  TileGeo g;
+  g.rows = rows_of(in, r, b);
+  g.cols = cols_of(in, r, b);
+  g.pr = cr.grid[b];
+  g.pc = cr.grid[b + 1];
+  const int64_t nrb = b == 0 ? 1 : r[b - 1];
+  const int64_t ncb = b == in.nb - 1 ? 1 : r[b + 1];
+  if (g.pr > 0) {
+    g.rtpb = piece_tiles(in.n[b], g.pr, BM);
+    g.nrt = nrb * g.rtpb;
+  } else {
+    g.rtpb = 0;
+    g.nrt = (g.rows + BM - 1) / BM;
+  }
+  if (g.pc > 0) {
+    g.ctpb = piece_tiles(in.n[b + 1], g.pc, BN);
+    g.nct = ncb * g.ctpb;
+  } else {
+    g.ctpb = 0;
+    g.nct = (g.cols + BN - 1) / BN;
+  }
+  return g;
+}
+
+__device__ __forceinline__ void tile_rows(const InstDev &in, const TileGeo &g, int b, int64_t t,
+                                          int64_t &r0, int &nr) {
+  if (g.pr > 0) {
+    const int64_t p = t / g.rtpb;
+    int64_t s, len;
+    piece_locate(in.n[b], g.pr, BM, t - p * g.rtpb, s, len);
+    r0 = p * in.n[b] + s;
+    nr = (int)len;
+  } else {
+    r0 = t * BM;
+    nr = (int)min((int64_t)BM, g.rows - r0);
+  }
+}
+
+__device__ __forceinline__ void tile_cols(const InstDev &in, const TileGeo &g, int b, int64_t t,
+                                          int64_t &c0, int &nc) {
+  if (g.pc > 0) {
+    const int64_t q = t / g.ctpb;
+    int64_t s, len;
+    piece_locate(in.n[b + 1], g.pc, BN, t - q * g.ctpb, s, len);
+    c0 = q * in.n[b + 1] + s;
+    nc = (int)len;
+  } else {
+    c0 = t * BN;
+    nc = (int)min((int64_t)BN, g.cols - c0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// screen of one tile in FP64: A - chain(T(a,:), R(:,c)) for a 64 x 64 tile,
+// 4 x 4 entries per thread, T / R staged through shared memory in 32-deep
+// chunks; the accumulation order over t is the contract's serial chain.
+__device__ void screen_tile_fp64(const InstDev &in, int b, int K, int64_t r0, int nr, int64_t c0,
+                                 int nc, Cand *out, ScreenSmem &sm) {
+  const BondDev &B = in.bond[b];
+  const SetDev &L = left_set(in, b);
+  const SetDev &Rset = right_set(in, b);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t nb0 = in.n[b], nb1 = in.n[b + 1];
+  const bool hil = in.gen == 0;
+  const int wl = b, wr = in.d - b - 2;
+  __syncthreads();
+  for (int x = tid; x < BM; x += NT) {
+    if (x < nr) {
+      const int64_t a = r0 + x, p = a / nb0, i = a - p * nb0;
+      sm.lrow[x] = L.lin[p] + i * in.stride[b];
+      if (hil) {
+        sm.srow[x] = L.sum[p] + (int)i;
+      } else {
+        for (int m = 0; m < wl; ++m) sm.ridx[x][m] = L.idx[p * wl + m];
+        sm.ridx[x][wl] = (int32_t)i;
+      }
+    }
+  }
+  for (int x = tid; x < BN; x += NT) {
+    if (x < nc) {
+      const int64_t c = c0 + x, q = c / nb1, j = c - q * nb1;
+      sm.lcol[x] = j * in.stride[b + 1] + Rset.lin[q];
+      if (hil) {
+        sm.scol[x] = (int)j + Rset.sum[q];
+      } else {
+        sm.cidx[x][0] = (int32_t)j;
+        for (int m = 0; m < wr; ++m) sm.cidx[x][1 + m] = Rset.idx[q * wr + m];
+      }
+    }
+  }
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  for (int t0 = 0; t0 < K; t0 += KC) {
+    const int kc = min(KC, K - t0);
+    __syncthreads();
+    for (int x = tid; x < kc * BM; x += NT) {
+      const int tt = x / BM, rr = x - tt * BM;
+      sm.Ts[tt][rr] = rr < nr ? B.T[(int64_t)(t0 + tt) * B.ldT + r0 + rr] : 0.0;
+    }
+    for (int x = tid; x < kc * BN; x += NT) {
+      const int tt = x / BN, cc = x - tt * BN;
+      sm.Rs[tt][cc] = cc < nc ? B.R[(int64_t)(t0 + tt) * B.ldR + c0 + cc] : 0.0;
+    }
+    __syncthreads();
+    for (int tt = 0; tt < kc; ++tt) {
+      double tv[4], rv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) tv[u] = sm.Ts[tt][ty + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) rv[v] = sm.Rs[tt][tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = __fma_rn(tv[u], rv[v], acc[u][v]);
+    }
+  }
+  KeyBest best{0ull, LLONG_MAX, -1, -1};
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int rr = ty + 16 * u;
+    if (rr >= nr) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int cc = tx + 16 * v;
+      if (cc >= nc) continue;
+      double A;
+      if (hil) {
+        A = in.hilb[sm.srow[rr] + sm.scol[cc]];
+      } else {
+        int32_t idx[TTC_MAXD];
+        for (int m = 0; m <= wl; ++m) idx[m] = sm.ridx[rr][m];
+        for (int m = 0; m <= wr; ++m) idx[wl + 1 + m] = sm.cidx[cc][m];
+        A = gen_full(in, idx);
+      }
+      const double e = __dsub_rn(A, acc[u][v]);
+      const uint64_t k = abs_key(e);
+      if (best.row < 0 || k >= best.key) {
+        const int64_t l = sm.lrow[rr] + sm.lcol[cc];
+        if (best.row < 0 || k > best.key || l < best.lin) {
+          best.key = k;
+          best.lin = l;
+          best.row = (int32_t)(r0 + rr);
+          best.col = (int32_t)(c0 + cc);
+        }
+      }
+    }
+  }
+  __shared__ uint64_t sk[NT / 32];
+  __shared__ int64_t sl[NT / 32];
+  __shared__ int32_t sr[NT / 32], sc[NT / 32];
+  best = block_best(best, sk, sl, sr, sc);
+  if (tid == 0) {
+    out->key = best.key;
+    out->lin = best.lin;
+    out->row = best.row;
+    out->col = best.col;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// phase: screen.  Tiles of every (instance, bond) pair that needs a screen
+// are numbered consecutively; CTA g takes tiles g, g + G, ...
+__device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
+  const int64_t G = gridDim.x;
+  int64_t base = 0;
+  for (int ii = 0; ii < ra.count; ++ii) {
+    const InstDev &in = *ra.insts[ii];
+    const Ctrl &cr = *in.ctrl;
+    const int st = *(volatile const int32_t *)&cr.state;
+    if (st != ST_SCREEN && st != ST_UPDATE) continue;
+    int32_t r[TTC_MAXD];
+    for (int b = 0; b < in.nb; ++b) r[b] = *(volatile const int32_t *)&cr.r[b];
+    for (int b = 0; b < in.nb; ++b) {
+      const TileGeo g = tile_geo(in, cr, r, b);
+      const int64_t nt = g.nrt * g.nct;
+      int64_t first = base + ((blockIdx.x - base) % G + G) % G;
+      for (int64_t t = first; t < base + nt; t += G) {
+        const int64_t lt = t - base;
+        const int64_t tr = lt / g.nct, tc = lt - tr * g.nct;
+        int64_t r0, c0;
+        int nr, nc;
+        tile_rows(in, g, b, tr, r0, nr);
+        tile_cols(in, g, b, tc, c0, nc);
+        screen_tile_fp64(in, b, r[b], r0, nr, c0, nc, in.cand + in.bond[b].cand_base + lt, sm.s);
+      }
+      base += nt;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// decide: append the pivot (a*, c*) to bond b (block-wide).  I_{<=k} gets
+// (alpha*, i*), J_{>k} gets (j*, beta*) (eq. nestedpivots); the history of
+// step z keeps c_z = R(:, c*), T(a*, :) and delta; U = P^{-1} is bordered
+// by [[U + d U a b U, -d U a], [-d b U, d]] (Sec. 3.1.1).
+__device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int64_t cs,
+                             DecideSmem &sm) {
+  const BondDev &B = in.bond[b];
+  const int z = cr.r[b];
+  const int cap = B.cap;
+  const int tid = threadIdx.x;
+  const int64_t nb0 = in.n[b], nb1 = in.n[b + 1];
+  const int64_t p = as / nb0, i = as - p * nb0;
+  const int64_t q = cs / nb1, j = cs - q * nb1;
+  const SetDev &L = left_set(in, b);
+  const SetDev &Rset = right_set(in, b);
+  if (tid == 0) {
+    const int wl = b, wj = in.d - 1 - b;
+    for (int m = 0; m < wl; ++m) B.I.idx[(int64_t)z * (wl + 1) + m] = L.idx[p * wl + m];
+    B.I.idx[(int64_t)z * (wl + 1) + wl] = (int32_t)i;
+    B.I.lin[z] = L.lin[p] + i * in.stride[b];
+    B.I.sum[z] = L.sum[p] + (int32_t)i;
+    B.J.idx[(int64_t)z * wj] = (int32_t)j;
+    for (int m = 0; m < wj - 1; ++m) B.J.idx[(int64_t)z * wj + 1 + m] = Rset.idx[q * (wj - 1) + m];
+    B.J.lin[z] = j * in.stride[b + 1] + Rset.lin[q];
+    B.J.sum[z] = (int32_t)j + Rset.sum[q];
+    B.prow[z] = (int32_t)as;
+    B.pcol[z] = (int32_t)cs;
+  }
+  double *hc = B.hc + (int64_t)z * cap;
+  double *hp = B.hpiv + (int64_t)z * cap;
+  for (int t = tid; t < z; t += NT) {
+    hc[t] = B.R[(int64_t)t * B.ldR + cs];
+    hp[t] = B.T[(int64_t)t * B.ldT + as];
+    sm.brow[t] = sb_entry(in, b, as, B.pcol[t]);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double piv = __dsub_rn(sb_entry(in, b, as, cs), chain(hp, 1, hc, 1, z));
+    const double delta = 1.0 / piv;
+    sm.delta = delta;
+    sm.flag = isfinite(delta) ? 1 : 0;
+    B.delta[z] = delta;
+  }
+  __syncthreads();
+  if (!sm.flag) return false;
+  const double delta = sm.delta;
+  double *U = B.U;
+  for (int t = tid; t < z; t += NT) {
+    sm.ua[t] = chain(U + (int64_t)t * cap, 1, hc, 1, z);
+    sm.bu[t] = chain(sm.brow, 1, U + t, cap, z);
+  }
+  __syncthreads();
+  for (int x = tid; x < z * z; x += NT) {
+    const int t = x / z, u = x - t * z;
+    const double du = __dmul_rn(delta, sm.ua[t]);
+    U[(int64_t)t * cap + u] = __fma_rn(du, sm.bu[u], U[(int64_t)t * cap + u]);
+  }
+  for (int t = tid; t < z; t += NT) {
+    U[(int64_t)t * cap + z] = -__dmul_rn(delta, sm.ua[t]);
+    U[(int64_t)z * cap + t] = -__dmul_rn(delta, sm.bu[t]);
+  }
+  if (tid == 0) U[(int64_t)z * cap + z] = delta;
+  __syncthreads();
+  return true;
+}
+
+// stop test on the cached best residuals: add a pivot on bond b while its
+// best |E| exceeds tau * rms(X) and the cap allows; returns bonds added.
+__device__ int decide_and_append(const InstDev &in, Ctrl &cr, DecideSmem &sm) {
+  const double theta = cr.tau * cr.xrms;
+  int32_t add[TTC_MAXD];
+  int nadd = 0;
+  for (int b = 0; b < in.nb; ++b) {
+    const double v = __longlong_as_double((long long)cr.best_key[b]);
+    add[b] = (v > theta && v > 0.0 && cr.r[b] < cr.maxr[b]) ? 1 : 0;
+    nadd += add[b];
+  }
+  if (nadd == 0) return 0;
+  for (int b = 0; b < in.nb; ++b) {
+    if (!add[b]) continue;
+    if (!append_pivot(in, cr, b, cr.best_row[b], cr.best_col[b], sm)) {
+      if (threadIdx.x == 0) {
+        cr.status = 4;  // TTC_ERR_NONFINITE
+        cr.state = ST_DONE;
+      }
+      __syncthreads();
+      return -1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < in.nb; ++b) {
+      cr.r_old[b] = cr.r[b];
+      cr.add[b] = add[b];
+      cr.r[b] += add[b];
+    }
+    cr.state = ST_UPDATE;
+  }
+  __syncthreads();
+  return nadd;
+}
+
+__device__ void decide_instance(const RunArgs &ra, int ii, DecideSmem &sm) {
+  const InstDev &in = *ra.insts[ii];
+  Ctrl &cr = *in.ctrl;
+  const int st = cr.state;
+  __syncthreads();
+  if (st == ST_DONE) return;
+  if (st == ST_VERIFY) {
+    // sampled error (Sec. 5) from the partial sums of the update phase
+    double part = 0.0;
+    for (int c = threadIdx.x; c < (int)gridDim.x; c += NT) part += in.err_part[c];
+    const double num = block_sum(part, sm.red);
+    if (threadIdx.x == 0) {
+      const double err = sqrt(num / cr.den);
+      cr.err = err;
+      int64_t per = cr.r[0];
+      for (int b = 1; b < in.nb; ++b) per += (int64_t)cr.r[b - 1] * cr.r[b];
+      per += cr.r[in.nb - 1];
+      cr.error_fmas += per * in.nsamples;
+      sm.flag = 0;
+      if (!isfinite(err)) {
+        cr.status = 4;
+        cr.state = ST_DONE;
+      } else if (cr.eps == 0.0 || err <= cr.eps) {
+        cr.status = 0;
+        cr.state = ST_DONE;
+      } else {
+        sm.flag = 1;  // refine
+      }
+    }
+    __syncthreads();
+    if (!sm.flag) return;
+    // tau /= 10 until a bond adds, the caps are hit or the refinements run out
+    for (;;) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        bool capped = true;
+        for (int b = 0; b < in.nb; ++b)
+          if (cr.r[b] < cr.maxr[b]) capped = false;
+        if (capped || cr.refinements >= cr.max_refine) {
+          cr.status = 7;  // TTC_NOT_CONVERGED
+          cr.state = ST_DONE;
+          sm.flag = 0;
+        } else {
+          cr.tau = cr.tau / 10.0;
+          cr.refinements += 1;
+          sm.flag = 1;
+        }
+      }
+      __syncthreads();
+      if (!sm.flag) return;
+      const int n = decide_and_append(in, cr, sm);
+      if (n != 0) return;
+    }
+  }
+  // SCREEN / UPDATE: merge the tile candidates of every bond
+  int64_t entries = 0, fmas = 0;
+  for (int b = 0; b < in.nb; ++b) {
+    const TileGeo g = tile_geo(in, cr, cr.r, b);
+    const int64_t nt = g.nrt * g.nct;
+    entries += g.rows * g.cols;
+    fmas += g.rows * g.cols * cr.r[b];
+    KeyBest best{0ull, LLONG_MAX, -1, -1};
+    const Cand *cand = in.cand + in.bond[b].cand_base;
+    for (int64_t t = threadIdx.x; t < nt; t += NT) {
+      KeyBest o{cand[t].key, cand[t].lin, cand[t].row, cand[t].col};
+      kb_take(best, o);
+    }
+    best = block_best(best, sm.rk, sm.rl, sm.rr, sm.rc);
+    if (threadIdx.x == 0) {
+      cr.best_key[b] = best.key;
+      cr.best_lin[b] = best.lin;
+      cr.best_row[b] = best.row;
+      cr.best_col[b] = best.col;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cr.sweeps += 1;
+    cr.entries += entries;
+    cr.screen_fmas += fmas;
+    sm.flag = 1;
+    for (int b = 0; b < in.nb; ++b)
+      if (cr.best_key[b] > KEY_INF || cr.best_row[b] < 0) sm.flag = 0;
+    if (!sm.flag) {
+      cr.status = 4;
+      cr.state = ST_DONE;
+    }
+  }
+  __syncthreads();
+  if (!sm.flag) return;
+  const int n = decide_and_append(in, cr, sm);
+  if (n == 0 && threadIdx.x == 0) cr.state = ST_VERIFY;
+  __syncthreads();
+}
+
+__device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
+  for (int ii = blockIdx.x; ii < ra.count; ii += gridDim.x) decide_instance(ra, ii, sm.d);
+}
+
+// ---------------------------------------------------------------------------
+// update: items of one instance, in this order per bond b
+//   C: replay rows of the new prefix (Alg. 4)                 n_b items
+//   A: eq. aca_approx_T_sub on the sweep-start rows           rows_old items
+//   B: new row z of R on the sweep-start columns              cols_old items
+//   D: new columns of R for the new suffix                    r_new * n_{b+1}
+__device__ void replay_row(const InstDev &in, int b, int64_t a, int nz) {
+  const BondDev &B = in.bond[b];
+  double Tr[RCAP];
+  const int cap = B.cap;
+  for (int z = 0; z < nz; ++z) {
+    const double *hc = B.hc + (int64_t)z * cap;
+    const double *hp = B.hpiv + (int64_t)z * cap;
+    const double s = __dsub_rn(chain(Tr, 1, hc, 1, z), sb_entry(in, b, a, B.pcol[z]));
+    const double w = __dmul_rn(B.delta[z], s);
+    for (int t = 0; t < z; ++t) Tr[t] = __fma_rn(w, hp[t], Tr[t]);
+    Tr[z] = -w;
+  }
+  for (int t = 0; t < nz; ++t) B.T[(int64_t)t * B.ldT + a] = Tr[t];
+}
+
+__device__ void update_row(const InstDev &in, int b, int64_t a, int z) {
+  const BondDev &B = in.bond[b];
+  const int cap = B.cap;
+  const double *hc = B.hc + (int64_t)z * cap;
+  const double *hp = B.hpiv + (int64_t)z * cap;
+  double *T = B.T + a;
+  const int64_t ld = B.ldT;
+  double acc = 0.0;
+  for (int t = 0; t < z; ++t) acc = __fma_rn(T[t * ld], hc[t], acc);
+  const double s = __dsub_rn(acc, sb_entry(in, b, a, B.pcol[z]));
+  const double w = __dmul_rn(B.delta[z], s);
+  for (int t = 0; t < z; ++t) T[t * ld] = __fma_rn(w, hp[t], T[t * ld]);
+  T[(int64_t)z * ld] = -w;
+}
+
+// error of one sample: X(i) - X~(i), X~ = G_1(i_1) ... G_d(i_d) from T and R
+__device__ double sample_residual(const InstDev &in, int64_t k) {
+  int32_t idx[TTC_MAXD];
+  sample_index(in, k, idx);
+  double v[RCAP], w[RCAP];
+  const Ctrl &cr = *in.ctrl;
+  const BondDev &B0 = in.bond[0];
+  int rl = cr.r[0];
+  for (int t = 0; t < rl; ++t) v[t] = B0.T[(int64_t)t * B0.ldT + idx[0]];
+  const int d = in.d;
+  for (int m = 1; m < d - 1; ++m) {
+    const BondDev &B = in.bond[m];
+    const int rr = cr.r[m];
+    const int64_t a0 = idx[m];
+    const int64_t nm = in.n[m];
+    for (int u = 0; u < rr; ++u) {
+      const double *col = B.T + (int64_t)u * B.ldT + a0;
+      double acc = 0.0;
+      for (int p = 0; p < rl; ++p) acc = __fma_rn(v[p], col[p * nm], acc);
+      w[u] = acc;
+    }
+    for (int u = 0; u < rr; ++u) v[u] = w[u];
+    rl = rr;
+  }
+  const BondDev &BL = in.bond[d - 2];
+  const double xt = chain(v, 1, BL.R + idx[d - 1], BL.ldR, rl);
+  return __dsub_rn(in.xs[k], xt);
+}
+
+__device__ __forceinline__ int64_t first_item(int64_t base, int64_t gt, int64_t NTOT) {
+  return base + ((gt - base) % NTOT + NTOT) % NTOT;
+}
+
+__device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
+  const int64_t NTOT = (int64_t)gridDim.x * NT;
+  const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
+  int64_t base = 0;
+  for (int ii = 0; ii < ra.count; ++ii) {
+    const InstDev &in = *ra.insts[ii];
+    const Ctrl &cr = *in.ctrl;
+    const int st = *(volatile const int32_t *)&cr.state;
+    if (st == ST_UPDATE) {
+      int32_t ro[TTC_MAXD], rn[TTC_MAXD], ad[TTC_MAXD];
+      for (int b = 0; b < in.nb; ++b) {
+        ro[b] = cr.r_old[b];
+        rn[b] = cr.r[b];
+        ad[b] = cr.add[b];
+      }
+      // C first: the replays are the longest items
+      for (int b = 1; b < in.nb; ++b) {
+        if (!ad[b - 1]) continue;
+        const int64_t nit = in.n[b];
+        const int64_t p = ro[b - 1];
+        for (int64_t x = first_item(base, gt, NTOT); x < base + nit; x += NTOT)
+          replay_row(in, b, p * in.n[b] + (x - base), rn[b]);
+        base += nit;
+      }
+      for (int b = 0; b < in.nb; ++b) {
+        const BondDev &B = in.bond[b];
+        if (ad[b]) {
+          const int z = ro[b];
+          const int64_t rows = rows_of(in, ro, b), cols = cols_of(in, ro, b);
+          for (int64_t x = first_item(base, gt, NTOT); x < base + rows; x += NTOT)
+            update_row(in, b, x - base, z);
+          base += rows;
+          const int64_t as = B.prow[z];
+          for (int64_t x = first_item(base, gt, NTOT); x < base + cols; x += NTOT)
+            B.R[(int64_t)z * B.ldR + (x - base)] = sb_entry(in, b, as, x - base);
+          base += cols;
+        }
+        if (b < in.nb - 1 && ad[b + 1]) {
+          const int64_t nb1 = in.n[b + 1];
+          const int64_t q = ro[b + 1];
+          const int64_t nit = (int64_t)rn[b] * nb1;
+          for (int64_t x = first_item(base, gt, NTOT); x < base + nit; x += NTOT) {
+            const int64_t l = x - base, t = l / nb1, jj = l - t * nb1;
+            const int64_t c = q * nb1 + jj;
+            B.R[t * B.ldR + c] = sb_entry(in, b, B.prow[t], c);
+          }
+          base += nit;
+        }
+      }
+    } else if (st == ST_VERIFY) {
+      double part = 0.0;
+      const int64_t ns = in.nsamples;
+      for (int64_t x = first_item(base, gt, NTOT); x < base + ns; x += NTOT) {
+        const double e = sample_residual(in, x - base);
+        part = __fma_rn(e, e, part);
+      }
+      base += ns;
+      const double s = block_sum(part, sm.red);
+      if (threadIdx.x == 0) in.err_part[blockIdx.x] = s;
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// init: first pivot (0,...,0) on every bond (ranks 1), X at the error samples
+// (its rms scales the stop threshold), then T(:,0) and R(0,:).
+__device__ void phase_init1(const RunArgs &ra, PhaseSmem &sm) {
+  const int64_t NTOT = (int64_t)gridDim.x * NT;
+  const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
+  int64_t base = 0;
+  for (int ii = 0; ii < ra.count; ++ii) {
+    const InstDev &in = *ra.insts[ii];
+    Ctrl &cr = *in.ctrl;
+    if (blockIdx.x == ii % gridDim.x && threadIdx.x == 0) {
+      int32_t zero[TTC_MAXD] = {0};
+      const double x0 = gen_full(in, zero);
+      if (x0 == 0.0 || !isfinite(x0)) {
+        cr.status = x0 == 0.0 ? 3 : 4;
+        cr.state = ST_DONE;
+      }
+      for (int b = 0; b < in.nb; ++b) {
+        const BondDev &B = in.bond[b];
+        for (int m = 0; m <= b; ++m) B.I.idx[m] = 0;
+        for (int m = 0; m < in.d - 1 - b; ++m) B.J.idx[m] = 0;
+        B.I.lin[0] = 0;
+        B.I.sum[0] = 0;
+        B.J.lin[0] = 0;
+        B.J.sum[0] = 0;
+        B.prow[0] = 0;
+        B.pcol[0] = 0;
+        const double delta = 1.0 / __dsub_rn(x0, 0.0);
+        B.delta[0] = delta;
+        B.U[0] = delta;
+        cr.r[b] = 1;
+        cr.r_old[b] = 0;
+        cr.add[b] = 1;
+      }
+    }
+    double part = 0.0;
+    const int64_t ns = in.nsamples;
+    for (int64_t x = first_item(base, gt, NTOT); x < base + ns; x += NTOT) {
+      int32_t idx[TTC_MAXD];
+      sample_index(in, x - base, idx);
+      const double v = gen_full(in, idx);
+      in.xs[x - base] = v;
+      part = __fma_rn(v, v, part);
+    }
+    base += ns;
+    const double s = block_sum(part, sm.red);
+    if (threadIdx.x == 0) in.err_part[blockIdx.x] = s;
+    __syncthreads();
+  }
+}
+
+__device__ void phase_init2(const RunArgs &ra, PhaseSmem &sm) {
+  const int64_t NTOT = (int64_t)gridDim.x * NT;
+  const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
+  int64_t base = 0;
+  for (int ii = 0; ii < ra.count; ++ii) {
+    const InstDev &in = *ra.insts[ii];
+    Ctrl &cr = *in.ctrl;
+    if (*(volatile int32_t *)&cr.state == ST_DONE) continue;
+    if (blockIdx.x == ii % gridDim.x) {
+      double part = 0.0;
+      for (int c = threadIdx.x; c < (int)gridDim.x; c += NT) part += in.err_part[c];
+      const double den = block_sum(part, sm.red);
+      if (threadIdx.x == 0) {
+        cr.den = den;
+        cr.xrms = sqrt(den / (double)in.nsamples);
+        if (!isfinite(den)) {
+          cr.status = 4;
+          cr.state = ST_DONE;
+        }
+      }
+    }
+    for (int b = 0; b < in.nb; ++b) {
+      const BondDev &B = in.bond[b];
+      const int64_t rows = in.n[b], cols = in.n[b + 1];
+      const double delta = B.delta[0];
+      for (int64_t x = first_item(base, gt, NTOT); x < base + rows; x += NTOT) {
+        const int64_t a = x - base;
+        const double s = __dsub_rn(0.0, sb_entry(in, b, a, 0));
+        B.T[a] = -__dmul_rn(delta, s);
+      }
+      base += rows;
+      for (int64_t x = first_item(base, gt, NTOT); x < base + cols; x += NTOT)
+        B.R[x - base] = sb_entry(in, b, 0, x - base);
+      base += cols;
+    }
+  }
+}
+
+__device__ bool all_done(const RunArgs &ra) {
+  __shared__ int done;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    done = 1;
+    for (int ii = 0; ii < ra.count; ++ii)
+      if (*(volatile const int32_t *)&ra.insts[ii]->ctrl->state != ST_DONE) done = 0;
+  }
+  __syncthreads();
+  return done != 0;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+
+extern __shared__ __align__(16) unsigned char dyn_smem[];
+
+__global__ void __launch_bounds__(NT, 2) k_persistent(RunArgs ra) {
+  PhaseSmem &sm = *reinterpret_cast<PhaseSmem *>(dyn_smem);
+  phase_init1(ra, sm);
+  if (!grid_barrier(ra, 1)) return;
+  phase_init2(ra, sm);
+  if (!grid_barrier(ra, 2)) return;
+  for (int it = 0;; ++it) {
+    if (all_done(ra)) break;
+    if (it >= ra.max_iters) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ra.bar->overrun, 1);
+      break;
+    }
+    phase_screen(ra, sm);
+    if (!grid_barrier(ra, 3)) return;
+    phase_decide(ra, sm);
+    if (!grid_barrier(ra, 4)) return;
+    phase_update(ra, sm);
+    if (!grid_barrier(ra, 5)) return;
+  }
+}
+
+__global__ void __launch_bounds__(NT, 2) k_init1(RunArgs ra) {
+  phase_init1(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
+}
+__global__ void __launch_bounds__(NT, 2) k_init2(RunArgs ra) {
+  phase_init2(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
+}
+__global__ void __launch_bounds__(NT, 2) k_screen(RunArgs ra) {
+  phase_screen(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
+}
+__global__ void __launch_bounds__(NT, 2) k_decide(RunArgs ra) {
+  phase_decide(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
+}
+__global__ void __launch_bounds__(NT, 2) k_update(RunArgs ra) {
+  phase_update(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
+}
+
+// cores: G_k = reshape(T_k, [s_{k-1}, n_k, s_k]) (eq. corereshape) written
+// row-major from the t-major T; the last core is R of the last bond.
+__global__ void k_core(const InstDev *inp, int m, double *dst) {
+  const InstDev &in = *inp;
+  const Ctrl &cr = *in.ctrl;
+  const int d = in.d;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t NTOT = (int64_t)gridDim.x * blockDim.x;
+  if (m < d - 1) {
+    const BondDev &B = in.bond[m];
+    const int rr = cr.r[m];
+    const int64_t rows = (int64_t)(m == 0 ? 1 : cr.r[m - 1]) * in.n[m];
+    for (int64_t x = gt; x < rows * rr; x += NTOT) {
+      const int64_t a = x / rr, t = x - a * rr;
+      dst[x] = B.T[t * B.ldT + a];
+    }
+  } else {
+    const BondDev &B = in.bond[d - 2];
+    const int rl = cr.r[d - 2];
+    const int64_t nn = in.n[d - 1];
+    for (int64_t x = gt; x < rl * nn; x += NTOT) {
+      const int64_t t = x / nn, j = x - t * nn;
+      dst[x] = B.R[t * B.ldR + j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch helpers (declared in ttc_launch.h)
+
+size_t phase_smem_bytes() { return sizeof(PhaseSmem); }
+
+static int64_t host_piece_tiles(int64_t n, int32_t C, int64_t T) {
+  int64_t s = 0;
+  for (int32_t k = 0; k < C; ++k) {
+    const int64_t lo = n * k / C, hi = n * (k + 1) / C;
+    s += (hi - lo + T - 1) / T;
+  }
+  return s;
+}
+
+int64_t host_tiles(int64_t n_b, int64_t n_b1, int64_t rl, int64_t rr, int32_t pr, int32_t pc) {
+  const int64_t nrt = pr > 0 ? rl * host_piece_tiles(n_b, pr, BM) : (rl * n_b + BM - 1) / BM;
+  const int64_t nct = pc > 0 ? rr * host_piece_tiles(n_b1, pc, BN) : (n_b1 * rr + BN - 1) / BN;
+  return nrt * nct;
+}
+
+cudaError_t persistent_occupancy(int *blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(PhaseSmem));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_persistent, NT,
+                                                       sizeof(PhaseSmem));
+}
+
+cudaError_t launch_persistent(const RunArgs &ra, int grid, cudaStream_t s) {
+  void *args[] = {(void *)&ra};
+  return cudaLaunchCooperativeKernel((const void *)k_persistent, dim3(grid), dim3(NT), args,
+                                     sizeof(PhaseSmem), s);
+}
+
+static cudaError_t prep(const void *f) {
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(PhaseSmem));
+}
+
+cudaError_t launch_phase(int phase, const RunArgs &ra, int grid, cudaStream_t s) {
+  const void *f = nullptr;
+  switch (phase) {
+    case PH_INIT1: f = (const void *)k_init1; break;
+    case PH_INIT2: f = (const void *)k_init2; break;
+    case PH_SCREEN: f = (const void *)k_screen; break;
+    case PH_DECIDE: f = (const void *)k_decide; break;
+    case PH_UPDATE: f = (const void *)k_update; break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = prep(f);
+  if (e != cudaSuccess) return e;
+  void *args[] = {(void *)&ra};
+  return cudaLaunchKernel(f, dim3(grid), dim3(NT), args, sizeof(PhaseSmem), s);
+}
+
+cudaError_t launch_core(const InstDev *d_inst, int m, double *dst, cudaStream_t s) {
+  k_core<<<152, 256, 0, s>>>(d_inst, m, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace ttc

@@ -1,0 +1,20 @@
+// ttc_launch.h -- host entry points into the kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ttc_internal.cuh"
+
+namespace ttc {
+
+enum Phase { PH_INIT1 = 0, PH_INIT2 = 1, PH_SCREEN = 2, PH_DECIDE = 3, PH_UPDATE = 4 };
+
+size_t phase_smem_bytes();
+cudaError_t persistent_occupancy(int *blocks_per_sm);
+cudaError_t launch_persistent(const RunArgs &ra, int grid, cudaStream_t s);
+cudaError_t launch_phase(int phase, const RunArgs &ra, int grid, cudaStream_t s);
+cudaError_t launch_core(const InstDev *d_inst, int m, double *dst, cudaStream_t s);
+
+// tile geometry used to size the candidate buffer (host mirror of tile_geo)
+int64_t host_tiles(int64_t n_b, int64_t n_b1, int64_t rl, int64_t rr, int32_t pr, int32_t pc);
+
+}  // namespace ttc

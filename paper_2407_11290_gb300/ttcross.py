@@ -1,0 +1,287 @@
+"""Thin ctypes binding of the C ABI in ``include/ttcross.h``.
+
+Argument marshalling only: every step of the TT cross runs in the CUDA library
+``_lib/libttcross.so``.  There is no CPU fallback -- if the library is missing
+or no GPU is present, the calls raise.  PyTorch supplies the CUDA stream
+(``torch.cuda.current_stream()``) and device buffers for device-side outputs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libttcross.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_ZERO_START, ERR_NONFINITE, ERR_DEVICE_TIMEOUT, ERR_CUDA, \
+    NOT_CONVERGED = range(8)
+STATUS_NAMES = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_OOM", 3: "ERR_ZERO_START",
+                4: "ERR_NONFINITE", 5: "ERR_DEVICE_TIMEOUT", 6: "ERR_CUDA", 7: "NOT_CONVERGED"}
+GEN_HILBERT, GEN_TT, GEN_MAXWELLIAN = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_SPLIT, PREC_AUTO = 0, 1, 2, 3
+PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "split": PREC_SPLIT, "auto": PREC_AUTO}
+
+# every symbol include/ttcross.h declares
+ABI_SYMBOLS = ("ttcross_default_options", "ttcross_create", "ttcross_run", "ttcross_run_batch",
+               "ttcross_sync", "ttcross_get_ranks", "ttcross_get_cores", "ttcross_get_pivots",
+               "ttcross_get_pivot_inverse", "ttcross_get_stats", "ttcross_destroy",
+               "ttcross_last_error_string")
+
+
+class TTCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Generator(C.Structure):
+    _fields_ = [("kind", C.c_int32),
+                ("tt_ranks", C.POINTER(C.c_int32)),
+                ("tt_cores", C.POINTER(C.c_double)),
+                ("dx", C.c_int32), ("dv", C.c_int32),
+                ("a_rho", C.c_double), ("a_u", C.c_double), ("a_T", C.c_double),
+                ("vmin", C.c_double), ("vmax", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("max_rank", C.c_int32),
+                ("bond_max_rank", C.POINTER(C.c_int32)),
+                ("precision", C.c_int32),
+                ("nsamples", C.c_int64),
+                ("seed", C.c_uint64),
+                ("max_refine", C.c_int32),
+                ("topk", C.c_int32),
+                ("host_loop", C.c_int32),
+                ("grid_ctas", C.c_int32),
+                ("wait_limit_s", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("sweeps", C.c_int64), ("entries_screened", C.c_int64),
+                ("refinements", C.c_int64), ("pivots_uncertified", C.c_int64),
+                ("screen_fmas", C.c_int64), ("error_fmas", C.c_int64),
+                ("tau", C.c_double), ("x_rms", C.c_double), ("err", C.c_double),
+                ("device_ms", C.c_double), ("status", C.c_int32),
+                ("device_error_where", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libttcross.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+        L = C.CDLL(path)
+        P = C.c_void_p
+        st = C.c_int
+        L.ttcross_default_options.argtypes = [C.POINTER(Options)]
+        L.ttcross_create.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(Generator),
+                                     C.POINTER(Options), C.POINTER(P)]
+        L.ttcross_run.argtypes = [P, C.c_double, C.c_int, C.POINTER(C.c_int32), P]
+        L.ttcross_run_batch.argtypes = [C.POINTER(P), C.c_int, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_int32), P]
+        L.ttcross_sync.argtypes = [P]
+        L.ttcross_get_ranks.argtypes = [P, C.POINTER(C.c_int64)]
+        L.ttcross_get_cores.argtypes = [P, C.c_int, P, C.c_int, P]
+        L.ttcross_get_pivots.argtypes = [P, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.ttcross_get_pivot_inverse.argtypes = [P, C.c_int, C.POINTER(C.c_double)]
+        L.ttcross_get_stats.argtypes = [P, C.POINTER(Stats)]
+        L.ttcross_destroy.argtypes = [P]
+        L.ttcross_last_error_string.restype = C.c_char_p
+        for name in ABI_SYMBOLS:
+            f = getattr(L, name)
+            if name != "ttcross_last_error_string":
+                f.restype = st
+        _lib = L
+        return L
+
+
+def _check(rc: int, allow=(OK,)):
+    if rc not in allow:
+        msg = _lib.ttcross_last_error_string().decode(errors="replace") if _lib else ""
+        raise TTCError(rc, msg)
+    return rc
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def default_options() -> Options:
+    L = load_library()
+    o = Options()
+    _check(L.ttcross_default_options(C.byref(o)))
+    return o
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class TTCross:
+    """One adaptive TT-cross instance on the current CUDA device.
+
+    ``n``: mode sizes; ``gen``: generator dict as produced by
+    :mod:`paper_2407_11290_gb300.workloads` (``{"kind": "hilbert"}``,
+    ``{"kind": "tt", ...}``, ``{"kind": "maxwellian", ...}``).
+    """
+
+    def __init__(self, n, gen, max_rank: int = 64, precision="fp64", nsamples: int = 10**6,
+                 seed: int = 20240715, max_refine: int = 6, topk: int = 8, host_loop: bool = False,
+                 grid_ctas: int = 0, wait_limit_s: float = 2.0, bond_max_rank=None):
+        L = load_library()
+        self._L = L
+        self.n = np.ascontiguousarray(n, dtype=np.int64)
+        self.d = int(self.n.size)
+        o = default_options()
+        o.max_rank = int(max_rank)
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.nsamples = int(nsamples)
+        o.seed = int(seed)
+        o.max_refine = int(max_refine)
+        o.topk = int(topk)
+        o.host_loop = 1 if host_loop else 0
+        o.grid_ctas = int(grid_ctas)
+        o.wait_limit_s = float(wait_limit_s)
+        keep = []
+        if bond_max_rank is not None:
+            bm = _i32(bond_max_rank)
+            keep.append(bm)
+            o.bond_max_rank = bm.ctypes.data_as(C.POINTER(C.c_int32))
+        g = Generator()
+        kind = gen["kind"]
+        if kind == "hilbert":
+            g.kind = GEN_HILBERT
+        elif kind == "tt":
+            g.kind = GEN_TT
+            ranks = _i32(gen["ranks"])
+            cores = np.ascontiguousarray(np.concatenate(
+                [np.asarray(c, dtype=np.float64).ravel() for c in gen["cores"]]))
+            keep += [ranks, cores]
+            g.tt_ranks = ranks.ctypes.data_as(C.POINTER(C.c_int32))
+            g.tt_cores = cores.ctypes.data_as(C.POINTER(C.c_double))
+        elif kind == "maxwellian":
+            g.kind = GEN_MAXWELLIAN
+            g.dx, g.dv = int(gen["dx"]), int(gen["dv"])
+            g.a_rho, g.a_u, g.a_T = float(gen["a_rho"]), float(gen["a_u"]), float(gen["a_T"])
+            g.vmin, g.vmax = float(gen["vmin"]), float(gen["vmax"])
+        else:
+            raise ValueError(f"unknown generator kind {kind!r}")
+        h = C.c_void_p()
+        _check(L.ttcross_create(self.d, self.n.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(g),
+                                C.byref(o), C.byref(h)))
+        self._h = h
+
+    # ------------------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._L.ttcross_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def run(self, eps: float, max_rank: int = 0, subtensor_grid=None, stream=None):
+        """Launch the cross (asynchronous); returns immediately."""
+        grid = None
+        if subtensor_grid is not None:
+            grid = _i32(subtensor_grid)
+            if grid.size != self.d:
+                raise ValueError("subtensor_grid needs d entries")
+        _check(self._L.ttcross_run(self._h, float(eps), int(max_rank),
+                                   grid.ctypes.data_as(C.POINTER(C.c_int32)) if grid is not None
+                                   else None, _stream_handle(stream)))
+
+    def sync(self, allow=(OK, NOT_CONVERGED)) -> int:
+        return _check(self._L.ttcross_sync(self._h), allow)
+
+    def ranks(self) -> np.ndarray:
+        s = np.zeros(self.d + 1, np.int64)
+        _check(self._L.ttcross_get_ranks(self._h, s.ctypes.data_as(C.POINTER(C.c_int64))))
+        return s
+
+    def core(self, k: int, device: bool = False, stream=None):
+        """Core k (1-based) as [s_{k-1}, n_k, s_k]; a torch CUDA tensor if device."""
+        s = self.ranks()
+        shape = (int(s[k - 1]), int(self.n[k - 1]), int(s[k]))
+        if device:
+            import torch
+            out = torch.empty(shape, dtype=torch.float64, device="cuda")
+            _check(self._L.ttcross_get_cores(self._h, int(k), C.c_void_p(out.data_ptr()), 1,
+                                             _stream_handle(stream)))
+            return out
+        out = np.zeros(shape, np.float64)
+        _check(self._L.ttcross_get_cores(self._h, int(k), out.ctypes.data_as(C.c_void_p), 0,
+                                         _stream_handle(stream)))
+        return out
+
+    def cores(self):
+        return [self.core(k) for k in range(1, self.d + 1)]
+
+    def pivots(self, k: int):
+        """(I_{<=k}, J_{>k}) of bond k (1-based) as int32 arrays."""
+        r = int(self.ranks()[k])
+        I = np.zeros((r, k), np.int32)
+        J = np.zeros((r, self.d - k), np.int32)
+        _check(self._L.ttcross_get_pivots(self._h, int(k), I.ctypes.data_as(C.POINTER(C.c_int32)),
+                                          J.ctypes.data_as(C.POINTER(C.c_int32))))
+        return I, J
+
+    def pivot_inverse(self, k: int) -> np.ndarray:
+        r = int(self.ranks()[k])
+        U = np.zeros((r, r), np.float64)
+        _check(self._L.ttcross_get_pivot_inverse(self._h, int(k),
+                                                 U.ctypes.data_as(C.POINTER(C.c_double))))
+        return U
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(self._L.ttcross_get_stats(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in Stats._fields_}
+
+
+def probe_fma_peak(fp64: bool = True, blocks_per_sm: int = 4, iters: int = 1 << 16):
+    """Measured FMA/s of the FP64 (or FP32) pipe on the current device."""
+    L = load_library()
+    f = L.ttcross_probe_fma_peak
+    f.argtypes = [C.c_int, C.c_int, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    f.restype = C.c_int
+    rate, ms = C.c_double(), C.c_double()
+    _check(f(1 if fp64 else 0, int(blocks_per_sm), int(iters), C.byref(rate), C.byref(ms)))
+    return rate.value, ms.value
+
+
+def run_batch(crosses, eps, max_rank=None, stream=None):
+    """Run several instances in one persistent launch (asynchronous)."""
+    L = load_library()
+    cnt = len(crosses)
+    hs = (C.c_void_p * cnt)(*[c.handle.value for c in crosses])
+    e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, np.float64), (cnt,)))
+    mr = None
+    if max_rank is not None:
+        mr = np.ascontiguousarray(np.broadcast_to(np.asarray(max_rank, np.int32), (cnt,)))
+    _check(L.ttcross_run_batch(hs, cnt, e.ctypes.data_as(C.POINTER(C.c_double)),
+                               mr.ctypes.data_as(C.POINTER(C.c_int32)) if mr is not None else None,
+                               _stream_handle(stream)))

@@ -1,0 +1,54 @@
+"""The C-ABI library builds, loads and exports every symbol include/ttcross.h
+declares (no compute calls: CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2407_11290_gb300 import build as B
+from paper_2407_11290_gb300 import ttcross
+
+HEADER = os.path.join(B.INCLUDE, "ttcross.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ttcross_\w+)\s*\(", text)))
+
+
+def test_library_builds_and_exports_header_symbols():
+    lib = B.build()
+    L = ctypes.CDLL(lib)
+    names = declared_functions()
+    assert names, "no declarations found"
+    for name in names:
+        assert hasattr(L, name), name
+    assert sorted(ttcross.ABI_SYMBOLS) == names
+
+
+def test_default_options_without_gpu():
+    o = ttcross.default_options()
+    assert o.max_rank == 64 and o.nsamples == 10**6 and o.seed == 20240715
+    assert o.wait_limit_s == 2.0 and o.precision == ttcross.PREC_FP64
+
+
+def test_create_fails_loudly_without_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(ttcross.TTCError):
+        ttcross.TTCross([4, 4], {"kind": "hilbert"}, max_rank=4)
+
+
+def test_invalid_arguments_rejected_on_host():
+    L = ttcross.load_library()
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 1)(4)
+    g = ttcross.Generator()
+    g.kind = ttcross.GEN_HILBERT
+    rc = L.ttcross_create(1, n, ctypes.byref(g), None, ctypes.byref(h))
+    assert rc == ttcross.ERR_INVALID_ARG
+    assert b"d=1" in L.ttcross_last_error_string()
+    assert L.ttcross_run(None, 1e-3, 0, None, None) == ttcross.ERR_INVALID_ARG

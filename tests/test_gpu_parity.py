@@ -1,0 +1,200 @@
+"""GPU FP64 form vs the CPU oracle: identical pivots (bit-exact integer
+work), identical T factors (same arithmetic contract), sampled error within
+1e-12.  Every call goes through the C ABI."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_11290_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+NT = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def tt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2407_11290_gb300 import ttcross
+    return ttcross
+
+
+def run_both(tt, w, eps, max_rank, nsamples, grid=None, **kw):
+    g = tt.TTCross(w["n"], w["gen"], max_rank=max_rank, nsamples=nsamples, **kw)
+    g.run(eps, subtensor_grid=grid)
+    rc = g.sync()
+    o = oracle.Oracle(w["n"], w["gen"], max_rank, nthreads=NT)
+    orc, ost = o.run(eps, nsamples=nsamples)
+    return g, rc, o, orc, ost
+
+
+def assert_same(g, o, cores=True):
+    d = o.d
+    r = g.ranks()
+    assert list(r[1:-1]) == list(o.ranks())
+    for k in range(1, d):
+        I, J = g.pivots(k)
+        Io, Jo = o.pivots(k - 1)
+        np.testing.assert_array_equal(I, Io)
+        np.testing.assert_array_equal(J, Jo)
+    if cores:
+        for k, (a, b) in enumerate(zip(g.cores(), o.cores()), start=1):
+            np.testing.assert_array_equal(a, b, err_msg=f"core {k}")
+
+
+def test_config0_hilbert3d(tt):
+    w = W.CONFIGS["hilbert3d_n32"]
+    g, rc, o, orc, ost = run_both(tt, w, w["eps"], w["max_rank"], 0, grid=w["grid"])
+    assert rc == orc == 0
+    assert_same(g, o)
+    st = g.stats()
+    assert abs(st["err"] - ost["err"]) <= 1e-12
+    assert st["err"] <= w["eps"]
+    for k in range(1, o.d):
+        np.testing.assert_array_equal(g.pivot_inverse(k), o.U(k - 1))
+
+
+def test_config1_hilbert6d_full_size(tt):
+    w = W.CONFIGS["hilbert6d_n64"]
+    g, rc, o, orc, ost = run_both(tt, w, w["eps"], w["max_rank"], w["nsamples"], grid=w["grid"])
+    assert rc == orc == 0
+    assert_same(g, o)
+    st = g.stats()
+    assert abs(st["err"] - ost["err"]) <= 1e-12
+    assert st["err"] <= w["eps"]
+    assert st["sweeps"] == ost["sweeps"] and st["entries_screened"] == ost["entries_screened"]
+
+
+@pytest.mark.parametrize("grid", [[1] * 6, [4] * 6, [3, 1, 2, 5, 1, 7]])
+def test_grid_invariance(tt, grid):
+    w = W.hilbert(6, 24)
+    ref = tt.TTCross(w["n"], w["gen"], max_rank=32, nsamples=20000)
+    ref.run(1e-9)
+    ref.sync()
+    g = tt.TTCross(w["n"], w["gen"], max_rank=32, nsamples=20000)
+    g.run(1e-9, subtensor_grid=grid)
+    g.sync()
+    assert list(g.ranks()) == list(ref.ranks())
+    for k in range(1, 6):
+        for a, b in zip(g.pivots(k), ref.pivots(k)):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_host_stepped_equals_persistent(tt):
+    w = W.hilbert(5, 20)
+    a = tt.TTCross(w["n"], w["gen"], max_rank=32, nsamples=30000)
+    a.run(1e-9)
+    a.sync()
+    b = tt.TTCross(w["n"], w["gen"], max_rank=32, nsamples=30000, host_loop=True)
+    b.run(1e-9)
+    b.sync()
+    for k in range(1, 6):
+        np.testing.assert_array_equal(a.core(k), b.core(k))
+    assert a.stats()["err"] == b.stats()["err"]
+
+
+def test_random_tt_known_ranks(tt):
+    w = W.random_tt([12, 12, 12, 12], [1, 3, 4, 3, 1], seed=7)
+    g, rc, o, orc, ost = run_both(tt, w, 1e-12, 10, 0)
+    assert rc == orc == 0
+    assert list(g.ranks()) == [1, 3, 4, 3, 1]
+    assert_same(g, o)
+    assert abs(g.stats()["err"] - ost["err"]) <= 1e-12
+
+
+def test_separable_rank1(tt):
+    w = W.separable([7, 9, 5, 6, 3])
+    g, rc, o, orc, ost = run_both(tt, w, 1e-12, 8, 0)
+    assert rc == orc == 0
+    assert list(g.ranks()) == [1, 1, 1, 1, 1, 1]
+    assert_same(g, o)
+
+
+@pytest.mark.parametrize("shape,seed", [((13, 29), 1), ((70, 45), 2), ((1, 9), 3), ((65, 130), 4)])
+def test_d2_matrix_prescribed(tt, shape, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal(shape)
+    A[0, 0] = 2.0
+    n1, n2 = shape
+    gen = {"kind": "tt", "ranks": [1, min(n1, 32), 1],
+           "cores": [np.eye(n1)[:, :32].reshape(1, n1, -1), A[:32].reshape(min(n1, 32), n2, 1)]}
+    w = {"n": [n1, n2], "gen": gen}
+    cap = min(n1, n2, 32)
+    g, rc, o, orc, ost = run_both(tt, w, 0.0, cap, 0)
+    assert rc == orc == 0
+    assert_same(g, o)
+
+
+def test_ragged_and_unit_modes(tt):
+    w = W.hilbert(4, 1)
+    w["n"] = [1, 67, 3, 130]
+    g, rc, o, orc, ost = run_both(tt, w, 1e-10, 24, 0)
+    assert rc == orc == 0
+    assert_same(g, o)
+
+
+def test_maxwellian_small(tt):
+    w = W.maxwellian(2, 2, 16, a_rho=0.4, a_u=0.3, a_T=0.2)
+    g, rc, o, orc, ost = run_both(tt, w, 1e-6, 24, 50000)
+    assert rc == orc == 0
+    # entries come from CUDA's sin/cos/exp, so equal pivots are expected but
+    # the factors may differ in the last bits
+    assert_same(g, o, cores=False)
+    assert abs(g.stats()["err"] - ost["err"]) <= 1e-12
+
+
+def test_prescribed_ranks_per_bond(tt):
+    w = W.hilbert(5, 30)
+    caps = [3, 5, 6, 4]
+    g = tt.TTCross(w["n"], w["gen"], max_rank=8, nsamples=10000, bond_max_rank=caps)
+    g.run(0.0)
+    assert g.sync() == 0
+    assert list(g.ranks()) == [1] + caps + [1]
+    o = oracle.Oracle(w["n"], w["gen"], caps, nthreads=NT)
+    o.run(0.0, nsamples=10000)
+    assert_same(g, o)
+
+
+def test_zero_start_and_nonfinite(tt):
+    w = W.random_tt([4, 5, 6], [1, 2, 2, 1], seed=3)
+    w["gen"]["cores"][0][:, 0, :] = 0.0
+    g = tt.TTCross(w["n"], w["gen"], max_rank=3, nsamples=0)
+    g.run(1e-6)
+    assert g.sync(allow=(tt.ERR_ZERO_START,)) == tt.ERR_ZERO_START
+    w = W.random_tt([4, 5, 6], [1, 2, 2, 1], seed=3)
+    w["gen"]["cores"][1][:, 3, :] = np.nan
+    g = tt.TTCross(w["n"], w["gen"], max_rank=3, nsamples=0)
+    g.run(1e-6)
+    assert g.sync(allow=(tt.ERR_NONFINITE,)) == tt.ERR_NONFINITE
+
+
+def test_device_wait_limit_returns_status(tt):
+    """A wait that runs out returns TTC_ERR_DEVICE_TIMEOUT; the context stays usable."""
+    w = W.hilbert(4, 16)
+    g = tt.TTCross(w["n"], w["gen"], max_rank=16, nsamples=1000, wait_limit_s=1e-9)
+    g.run(1e-8)
+    assert g.sync(allow=(tt.ERR_DEVICE_TIMEOUT,)) == tt.ERR_DEVICE_TIMEOUT
+    h = tt.TTCross(w["n"], w["gen"], max_rank=16, nsamples=1000)
+    h.run(1e-8)
+    assert h.sync() == 0
+
+
+def test_batch_equals_single(tt):
+    ws = [W.hilbert(3, 20), W.hilbert(4, 11), W.random_tt([6, 7, 8], [1, 2, 3, 1], seed=5)]
+    singles, batch = [], []
+    for w in ws:
+        a = tt.TTCross(w["n"], w["gen"], max_rank=16, nsamples=5000)
+        a.run(1e-9)
+        a.sync()
+        singles.append(a)
+        batch.append(tt.TTCross(w["n"], w["gen"], max_rank=16, nsamples=5000))
+    tt.run_batch(batch, [1e-9] * 3)
+    for a, b in zip(singles, batch):
+        b.sync()
+        assert list(a.ranks()) == list(b.ranks())
+        for k in range(1, a.d + 1):
+            np.testing.assert_array_equal(a.core(k), b.core(k))
