@@ -73,6 +73,8 @@ def lib():
             L.orc_entry.restype = C.c_double
             L.orc_entry.argtypes = [P, i32p]
             L.orc_init.argtypes = [P]
+            L.orc_init_at.argtypes = [P, i32p]
+            L.orc_sample_scan.argtypes = [P, C.c_int64, C.c_uint64, f64p, i32p]
             L.orc_screen.argtypes = [P, f64p, i64p, i32p, i32p, f64p]
             L.orc_apply.argtypes = [P, i32p, i32p, i32p]
             L.orc_run.argtypes = [P, C.c_double, C.c_int64, C.c_uint64, C.c_int, C.POINTER(Stats)]
@@ -156,6 +158,20 @@ class Oracle:
     # --- steps -------------------------------------------------------------
     def init(self) -> int:
         return int(self._L.orc_init(self._h))
+
+    def init_at(self, start) -> int:
+        a = np.ascontiguousarray(start, dtype=np.int32)
+        return int(self._L.orc_init_at(self._h, _p(a, C.c_int32)))
+
+    def sample_scan(self, nsamples: int = 10**6, seed: int = 20240715):
+        """(rms of X over the samples, start pivot multi-index)."""
+        rms = C.c_double()
+        start = np.zeros(self.d, np.int32)
+        rc = self._L.orc_sample_scan(self._h, int(nsamples), C.c_uint64(seed), C.byref(rms),
+                                     _p(start, C.c_int32))
+        if rc:
+            raise RuntimeError(f"orc_sample_scan -> {rc}")
+        return rms.value, start
 
     def screen(self):
         nb = self.d - 1

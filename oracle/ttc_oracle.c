@@ -244,27 +244,29 @@ static void replay_row(const orc_state *s, int b, int64_t a, int nz) {
 }
 
 /* ------------------------------------------------------------------------- */
-/* Start: every bond takes the pivot (0,...,0), so all ranks are 1.  The
-   paper's Alg. 1 starts from random samples; a fixed start keeps runs
-   reproducible.  Step z = 0 of eq. aca_approx_T with an empty T gives
+/* Start: every bond takes the same first pivot, the multi-index `start`, so
+   all ranks are 1.  Step z = 0 of eq. aca_approx_T with an empty T gives
    T(:,0) = A(:,c_0) / A(a_0,c_0) in the form delta*A.                      */
-int orc_init(orc_state *s) {
+int orc_init_at(orc_state *s, const int32_t *start) {
   int d = s->d;
-  int32_t zero[ORC_MAXD] = {0};
-  double x0 = orc_entry(s, zero);
+  for (int m = 0; m < d; ++m)
+    if (start[m] < 0 || start[m] >= s->n[m]) return ORC_ERR_INVALID_ARG;
+  double x0 = orc_entry(s, start);
   if (x0 == 0.0) return ORC_ERR_ZERO_START;
   if (!isfinite(x0)) return ORC_ERR_NONFINITE;
   for (int b = 0; b < d - 1; ++b) {
-    memset(s->I[b], 0, sizeof(int32_t) * (b + 1));
-    memset(s->J[b], 0, sizeof(int32_t) * (d - 1 - b));
+    memcpy(s->I[b], start, sizeof(int32_t) * (b + 1));
+    memcpy(s->J[b], start + b + 1, sizeof(int32_t) * (d - 1 - b));
     s->r[b] = 1;
-    s->prow[b][0] = 0;
-    s->pcol[b][0] = 0;
+    /* row (p = 0, i_b), column (i_{b+1}, q = 0) of the superblock */
+    s->prow[b][0] = start[b];
+    s->pcol[b][0] = start[b + 1];
   }
   for (int b = 0; b < d - 1; ++b) {
     int64_t rows = rows_of(s, b), cols = cols_of(s, b);
-    for (int64_t c = 0; c < cols; ++c) s->R[b][c] = sb_entry(s, b, 0, c);
-    double piv = sb_entry(s, b, 0, 0) - 0.0;
+    int64_t a0 = s->prow[b][0], c0 = s->pcol[b][0];
+    for (int64_t c = 0; c < cols; ++c) s->R[b][c] = sb_entry(s, b, a0, c);
+    double piv = sb_entry(s, b, a0, c0) - 0.0;
     double delta = 1.0 / piv;
     if (!isfinite(delta)) return ORC_ERR_NONFINITE;
     s->hdelta[b][0] = delta;
@@ -273,6 +275,11 @@ int orc_init(orc_state *s) {
   }
   s->initialized = 1;
   return ORC_OK;
+}
+
+int orc_init(orc_state *s) {
+  int32_t zero[ORC_MAXD] = {0};
+  return orc_init_at(s, zero);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -512,6 +519,22 @@ static uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
   return z ^ (z >> 31);
 }
 
+/* multi-index of sample k: SplitMix64 draws (sample-major, mode-minor),
+   index = floor(x * n / 2^64); or entry k in column-major order. */
+static void sample_at(const orc_state *s, int64_t k, int exhaustive, uint64_t seed,
+                      int32_t *idx) {
+  if (exhaustive) {
+    int64_t l = k;
+    for (int m = 0; m < s->d; ++m) { idx[m] = (int32_t)(l % s->n[m]); l /= s->n[m]; }
+  } else {
+    for (int m = 0; m < s->d; ++m) {
+      uint64_t x = splitmix64_at(seed, (uint64_t)(k * s->d + m));
+      unsigned __int128 pr = (unsigned __int128)x * (uint64_t)s->n[m];
+      idx[m] = (int32_t)(uint64_t)(pr >> 64);
+    }
+  }
+}
+
 int orc_sample_indices(int d, const int64_t *n, int64_t nsamples,
                        uint64_t seed, int32_t *out) {
   for (int64_t sidx = 0; sidx < nsamples; ++sidx)
@@ -543,16 +566,7 @@ int orc_sampled_error(const orc_state *s, int64_t nsamples, uint64_t seed,
 #endif
   for (int64_t k = 0; k < nsamples; ++k) {
     int32_t idx[ORC_MAXD];
-    if (exhaustive) {
-      int64_t l = k;
-      for (int m = 0; m < d; ++m) { idx[m] = (int32_t)(l % s->n[m]); l /= s->n[m]; }
-    } else {
-      for (int m = 0; m < d; ++m) {
-        uint64_t x = splitmix64_at(seed, (uint64_t)(k * d + m));
-        unsigned __int128 pr = (unsigned __int128)x * (uint64_t)s->n[m];
-        idx[m] = (int32_t)(uint64_t)(pr >> 64);
-      }
-    }
+    sample_at(s, k, exhaustive, seed, idx);
     xs[k] = orc_entry(s, idx);
     ys[k] = orc_tt_eval(s, idx);
   }
@@ -569,9 +583,11 @@ int orc_sampled_error(const orc_state *s, int64_t nsamples, uint64_t seed,
 }
 
 /* ------------------------------------------------------------------------- */
-/* Root mean square of X over the error's sample set (Sec. 5 sampling).     */
-int orc_sample_rms(const orc_state *s, int64_t nsamples, uint64_t seed,
-                   double *rms) {
+/* X over the error's sample set (Sec. 5 sampling): its root mean square, and
+   the start pivot = argmax |X| over the samples and the origin, i.e. Alg. 1
+   line 1 with the current approximation zero (ties: lowest linear index). */
+int orc_sample_scan(const orc_state *s, int64_t nsamples, uint64_t seed,
+                    double *rms, int32_t *start) {
   int d = s->d;
   int64_t total = 1;
   int exhaustive = 0;
@@ -587,23 +603,32 @@ int orc_sample_rms(const orc_state *s, int64_t nsamples, uint64_t seed,
 #endif
   for (int64_t k = 0; k < nsamples; ++k) {
     int32_t idx[ORC_MAXD];
-    if (exhaustive) {
-      int64_t l = k;
-      for (int m = 0; m < d; ++m) { idx[m] = (int32_t)(l % s->n[m]); l /= s->n[m]; }
-    } else {
-      for (int m = 0; m < d; ++m) {
-        uint64_t x = splitmix64_at(seed, (uint64_t)(k * d + m));
-        unsigned __int128 pr = (unsigned __int128)x * (uint64_t)s->n[m];
-        idx[m] = (int32_t)(uint64_t)(pr >> 64);
-      }
-    }
+    sample_at(s, k, exhaustive, seed, idx);
     xs[k] = orc_entry(s, idx);
   }
   double den = 0.0;
   for (int64_t k = 0; k < nsamples; ++k) den += xs[k] * xs[k];
-  free(xs);
   *rms = sqrt(den / (double)nsamples);
+  int32_t zero[ORC_MAXD] = {0};
+  double bv = fabs(orc_entry(s, zero));
+  int64_t bl = 0;
+  memcpy(start, zero, sizeof(int32_t) * d);
+  for (int64_t k = 0; k < nsamples; ++k) {
+    double v = fabs(xs[k]);
+    if (!(v >= bv)) continue;
+    int32_t idx[ORC_MAXD];
+    sample_at(s, k, exhaustive, seed, idx);
+    int64_t l = lin_index(s, idx);
+    if (v > bv || l < bl) { bv = v; bl = l; memcpy(start, idx, sizeof(int32_t) * d); }
+  }
+  free(xs);
   return ORC_OK;
+}
+
+int orc_sample_rms(const orc_state *s, int64_t nsamples, uint64_t seed,
+                   double *rms) {
+  int32_t start[ORC_MAXD];
+  return orc_sample_scan(s, nsamples, seed, rms, start);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -616,10 +641,12 @@ int orc_run(orc_state *s, double eps, int64_t nsamples, uint64_t seed,
             int max_refine, orc_stats *st) {
   int d = s->d;
   memset(st, 0, sizeof(*st));
-  int rc = orc_init(s);
-  if (rc) { st->status = rc; return rc; }
   double xrms = 0.0;
-  rc = orc_sample_rms(s, nsamples, seed, &xrms);
+  int32_t start[ORC_MAXD];
+  int rc = orc_sample_scan(s, nsamples, seed, &xrms, start);
+  if (rc) { st->status = rc; return rc; }
+  if (!isfinite(xrms)) { st->status = ORC_ERR_NONFINITE; return ORC_ERR_NONFINITE; }
+  rc = orc_init_at(s, start);
   if (rc) { st->status = rc; return rc; }
   double tau = eps;
   double best[ORC_MAXD], maxabs[ORC_MAXD];

@@ -86,7 +86,9 @@ void orc_destroy(orc_state *s);
 /* Exact entry X(idx) (idx has d 0-based indices). */
 double orc_entry(const orc_state *s, const int32_t *idx);
 
-/* First pivot (0,...,0) for every bond, ranks 1. */
+/* First pivot `start` (d indices) for every bond, ranks 1. */
+int orc_init_at(orc_state *s, const int32_t *start);
+/* The same with start = (0,...,0). */
 int orc_init(orc_state *s);
 
 /* Exhaustive screen of every bond's superblock.  Outputs per bond b:
@@ -100,7 +102,8 @@ int orc_screen(orc_state *s, double *best, int64_t *lin, int32_t *row,
 int orc_apply(orc_state *s, const int32_t *add, const int32_t *row,
               const int32_t *col);
 
-/* Whole adaptive run (init, sweeps, tau refinement, error).  A bond adds a
+/* Whole adaptive run (start pivot from orc_sample_scan, sweeps, tau
+   refinement, error).  A bond adds a
    pivot while its best |E| > tau * rms(X) (tau starts at eps, /10 per failed
    verification).  eps == 0 selects prescribed-rank mode (tau = 0, stop at the
    rank caps). */
@@ -111,7 +114,12 @@ int orc_run(orc_state *s, double eps, int64_t nsamples, uint64_t seed,
    drawn by SplitMix64(seed) (all entries when nsamples <= 0 or >= prod n). */
 int orc_sampled_error(const orc_state *s, int64_t nsamples, uint64_t seed,
                       double *err);
-/* rms of X over the same sample set (scales the pivot threshold). */
+/* rms of X over the error's sample set (scales the pivot threshold) and the
+   start pivot: argmax |X| over the samples and the origin, ties to the
+   lowest linear index (Alg. 1 line 1 with a zero approximation). */
+int orc_sample_scan(const orc_state *s, int64_t nsamples, uint64_t seed,
+                    double *rms, int32_t *start);
+/* rms only. */
 int orc_sample_rms(const orc_state *s, int64_t nsamples, uint64_t seed,
                    double *rms);
 /* The same indices the error uses: out[nsamples*d] sample-major. */

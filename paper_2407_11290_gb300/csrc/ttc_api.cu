@@ -166,6 +166,7 @@ ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, 
   // host-stepped: the same phases as separate launches, state read per sweep
   CU(launch_phase(PH_INIT1, ra, h0->grid, s));
   CU(launch_phase(PH_INIT2, ra, h0->grid, s));
+  CU(launch_phase(PH_INIT3, ra, h0->grid, s));
   for (int64_t it = 0; it <= ra.max_iters; ++it) {
     bool done = true;
     for (int i = 0; i < count; ++i) {
@@ -332,6 +333,7 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     double *tt = cv.take<double>(tt_total);
     double *xs = cv.take<double>(ns);
     double *errp = cv.take<double>(GRID_CAP);
+    Cand *spart = cv.take<Cand>(GRID_CAP);
     int32_t *eidx = cv.take<int32_t>(TTC_MAXD);
     int64_t *elin = cv.take<int64_t>(1);
     int32_t *esum = cv.take<int32_t>(1);
@@ -381,6 +383,7 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
       I.tt = tt;
       I.xs = xs;
       I.err_part = errp;
+      I.start_part = spart;
       I.err_part_cap = GRID_CAP;
       I.empty.idx = eidx;
       I.empty.lin = elin;

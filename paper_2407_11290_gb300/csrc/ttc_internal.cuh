@@ -86,6 +86,7 @@ struct InstDev {
   int32_t exhaustive;
   uint64_t seed;
   double *err_part;                  // [max grid] partial sums
+  struct Cand *start_part;           // [max grid] per-CTA argmax |X| over the samples
   int32_t err_part_cap;
   struct Cand *cand;
   Ctrl *ctrl;

@@ -708,41 +708,20 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
 }
 
 // ---------------------------------------------------------------------------
-// init: first pivot (0,...,0) on every bond (ranks 1), X at the error samples
-// (its rms scales the stop threshold), then T(:,0) and R(0,:).
+// init.  The start pivot is Alg. 1 line 1 with a zero approximation: the
+// argmax of |X| over the error's random samples and the origin (ties: lowest
+// linear index).  Every bond takes it as its first pivot (ranks 1).
+//   init1 (all CTAs): X at the samples, partial sums of X^2, per-CTA argmax
+//   init2 (owner CTA): reduce; pivot sets, delta_0, U = [delta_0]
+//   init3 (all CTAs): T(:,0) and R(0,:) of every bond
 __device__ void phase_init1(const RunArgs &ra, PhaseSmem &sm) {
   const int64_t NTOT = (int64_t)gridDim.x * NT;
   const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
   int64_t base = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = *ra.insts[ii];
-    Ctrl &cr = *in.ctrl;
-    if (blockIdx.x == ii % gridDim.x && threadIdx.x == 0) {
-      int32_t zero[TTC_MAXD] = {0};
-      const double x0 = gen_full(in, zero);
-      if (x0 == 0.0 || !isfinite(x0)) {
-        cr.status = x0 == 0.0 ? 3 : 4;
-        cr.state = ST_DONE;
-      }
-      for (int b = 0; b < in.nb; ++b) {
-        const BondDev &B = in.bond[b];
-        for (int m = 0; m <= b; ++m) B.I.idx[m] = 0;
-        for (int m = 0; m < in.d - 1 - b; ++m) B.J.idx[m] = 0;
-        B.I.lin[0] = 0;
-        B.I.sum[0] = 0;
-        B.J.lin[0] = 0;
-        B.J.sum[0] = 0;
-        B.prow[0] = 0;
-        B.pcol[0] = 0;
-        const double delta = 1.0 / __dsub_rn(x0, 0.0);
-        B.delta[0] = delta;
-        B.U[0] = delta;
-        cr.r[b] = 1;
-        cr.r_old[b] = 0;
-        cr.add[b] = 1;
-      }
-    }
     double part = 0.0;
+    KeyBest best{0ull, LLONG_MAX, -1, -1};
     const int64_t ns = in.nsamples;
     for (int64_t x = first_item(base, gt, NTOT); x < base + ns; x += NTOT) {
       int32_t idx[TTC_MAXD];
@@ -750,47 +729,133 @@ __device__ void phase_init1(const RunArgs &ra, PhaseSmem &sm) {
       const double v = gen_full(in, idx);
       in.xs[x - base] = v;
       part = __fma_rn(v, v, part);
+      const uint64_t k = abs_key(v);
+      if (best.row < 0 || k >= best.key) {
+        int64_t l = 0;
+        for (int m = 0; m < in.d; ++m) l += (int64_t)idx[m] * in.stride[m];
+        if (best.row < 0 || k > best.key || l < best.lin) {
+          best.key = k;
+          best.lin = l;
+          best.row = 0;
+        }
+      }
     }
     base += ns;
     const double s = block_sum(part, sm.red);
-    if (threadIdx.x == 0) in.err_part[blockIdx.x] = s;
+    __shared__ uint64_t sk[NT / 32];
+    __shared__ int64_t sl[NT / 32];
+    __shared__ int32_t sr[NT / 32], sc[NT / 32];
+    best = block_best(best, sk, sl, sr, sc);
+    if (threadIdx.x == 0) {
+      in.err_part[blockIdx.x] = s;
+      in.start_part[blockIdx.x].key = best.key;
+      in.start_part[blockIdx.x].lin = best.lin;
+      in.start_part[blockIdx.x].row = best.row;
+      in.start_part[blockIdx.x].col = 0;
+    }
     __syncthreads();
   }
 }
 
 __device__ void phase_init2(const RunArgs &ra, PhaseSmem &sm) {
+  for (int ii = blockIdx.x; ii < ra.count; ii += gridDim.x) {
+    const InstDev &in = *ra.insts[ii];
+    Ctrl &cr = *in.ctrl;
+    double part = 0.0;
+    KeyBest best{0ull, LLONG_MAX, -1, -1};
+    for (int c = threadIdx.x; c < (int)gridDim.x; c += NT) {
+      part += in.err_part[c];
+      const Cand &cd = in.start_part[c];
+      KeyBest o{cd.key, cd.lin, cd.row, cd.col};
+      kb_take(best, o);
+    }
+    const double den = block_sum(part, sm.d.red);
+    best = block_best(best, sm.d.rk, sm.d.rl, sm.d.rr, sm.d.rc);
+    if (threadIdx.x == 0) {
+      cr.den = den;
+      cr.xrms = sqrt(den / (double)in.nsamples);
+      int32_t zero[TTC_MAXD] = {0};
+      const double x0 = gen_full(in, zero);
+      KeyBest o{abs_key(x0), 0, 0, 0};
+      kb_take(best, o);
+      int32_t st[TTC_MAXD];
+      int64_t l = best.lin;
+      for (int m = 0; m < in.d; ++m) {
+        st[m] = (int32_t)(l % in.n[m]);
+        l /= in.n[m];
+      }
+      const double xs0 = gen_full(in, st);
+      if (!isfinite(den) || !isfinite(xs0)) {
+        cr.status = 4;
+        cr.state = ST_DONE;
+      } else if (xs0 == 0.0) {
+        cr.status = 3;
+        cr.state = ST_DONE;
+      }
+      for (int b = 0; b < in.nb && cr.state != ST_DONE; ++b) {
+        const BondDev &B = in.bond[b];
+        int64_t ll = 0;
+        int32_t ss = 0;
+        for (int m = 0; m <= b; ++m) {
+          B.I.idx[m] = st[m];
+          ll += (int64_t)st[m] * in.stride[m];
+          ss += st[m];
+        }
+        B.I.lin[0] = ll;
+        B.I.sum[0] = ss;
+        ll = 0;
+        ss = 0;
+        for (int m = b + 1; m < in.d; ++m) {
+          B.J.idx[m - b - 1] = st[m];
+          ll += (int64_t)st[m] * in.stride[m];
+          ss += st[m];
+        }
+        B.J.lin[0] = ll;
+        B.J.sum[0] = ss;
+        B.prow[0] = st[b];
+        B.pcol[0] = st[b + 1];
+        cr.r[b] = 1;
+        cr.r_old[b] = 0;
+        cr.add[b] = 1;
+      }
+      if (cr.state != ST_DONE) {
+        // the pivot entry of every superblock is X(start)
+        const double delta = 1.0 / __dsub_rn(xs0, 0.0);
+        if (!isfinite(delta)) {
+          cr.status = 4;
+          cr.state = ST_DONE;
+        }
+        for (int b = 0; b < in.nb; ++b) {
+          in.bond[b].delta[0] = delta;
+          in.bond[b].U[0] = delta;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void phase_init3(const RunArgs &ra, PhaseSmem &sm) {
   const int64_t NTOT = (int64_t)gridDim.x * NT;
   const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
   int64_t base = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = *ra.insts[ii];
-    Ctrl &cr = *in.ctrl;
-    if (*(volatile int32_t *)&cr.state == ST_DONE) continue;
-    if (blockIdx.x == ii % gridDim.x) {
-      double part = 0.0;
-      for (int c = threadIdx.x; c < (int)gridDim.x; c += NT) part += in.err_part[c];
-      const double den = block_sum(part, sm.red);
-      if (threadIdx.x == 0) {
-        cr.den = den;
-        cr.xrms = sqrt(den / (double)in.nsamples);
-        if (!isfinite(den)) {
-          cr.status = 4;
-          cr.state = ST_DONE;
-        }
-      }
-    }
+    const Ctrl &cr = *in.ctrl;
+    if (*(volatile const int32_t *)&cr.state == ST_DONE) continue;
     for (int b = 0; b < in.nb; ++b) {
       const BondDev &B = in.bond[b];
       const int64_t rows = in.n[b], cols = in.n[b + 1];
       const double delta = B.delta[0];
+      const int64_t a0 = B.prow[0], c0 = B.pcol[0];
       for (int64_t x = first_item(base, gt, NTOT); x < base + rows; x += NTOT) {
         const int64_t a = x - base;
-        const double s = __dsub_rn(0.0, sb_entry(in, b, a, 0));
+        const double s = __dsub_rn(0.0, sb_entry(in, b, a, c0));
         B.T[a] = -__dmul_rn(delta, s);
       }
       base += rows;
       for (int64_t x = first_item(base, gt, NTOT); x < base + cols; x += NTOT)
-        B.R[x - base] = sb_entry(in, b, 0, x - base);
+        B.R[x - base] = sb_entry(in, b, a0, x - base);
       base += cols;
     }
   }
@@ -819,6 +884,8 @@ __global__ void __launch_bounds__(NT, 2) k_persistent(RunArgs ra) {
   if (!grid_barrier(ra, 1)) return;
   phase_init2(ra, sm);
   if (!grid_barrier(ra, 2)) return;
+  phase_init3(ra, sm);
+  if (!grid_barrier(ra, 6)) return;
   for (int it = 0;; ++it) {
     if (all_done(ra)) break;
     if (it >= ra.max_iters) {
@@ -839,6 +906,9 @@ __global__ void __launch_bounds__(NT, 2) k_init1(RunArgs ra) {
 }
 __global__ void __launch_bounds__(NT, 2) k_init2(RunArgs ra) {
   phase_init2(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
+}
+__global__ void __launch_bounds__(NT, 2) k_init3(RunArgs ra) {
+  phase_init3(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
 __global__ void __launch_bounds__(NT, 2) k_screen(RunArgs ra) {
   phase_screen(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
@@ -921,6 +991,7 @@ cudaError_t launch_phase(int phase, const RunArgs &ra, int grid, cudaStream_t s)
   switch (phase) {
     case PH_INIT1: f = (const void *)k_init1; break;
     case PH_INIT2: f = (const void *)k_init2; break;
+    case PH_INIT3: f = (const void *)k_init3; break;
     case PH_SCREEN: f = (const void *)k_screen; break;
     case PH_DECIDE: f = (const void *)k_decide; break;
     case PH_UPDATE: f = (const void *)k_update; break;

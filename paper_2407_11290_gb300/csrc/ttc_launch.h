@@ -6,7 +6,7 @@
 
 namespace ttc {
 
-enum Phase { PH_INIT1 = 0, PH_INIT2 = 1, PH_SCREEN = 2, PH_DECIDE = 3, PH_UPDATE = 4 };
+enum Phase { PH_INIT1 = 0, PH_INIT2 = 1, PH_INIT3 = 2, PH_SCREEN = 3, PH_DECIDE = 4, PH_UPDATE = 5 };
 
 size_t phase_smem_bytes();
 cudaError_t persistent_occupancy(int *blocks_per_sm);

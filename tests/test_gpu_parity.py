@@ -139,7 +139,7 @@ def test_ragged_and_unit_modes(tt):
 
 def test_maxwellian_small(tt):
     w = W.maxwellian(2, 2, 16, a_rho=0.4, a_u=0.3, a_T=0.2)
-    g, rc, o, orc, ost = run_both(tt, w, 1e-6, 24, 50000)
+    g, rc, o, orc, ost = run_both(tt, w, 1e-6, 64, 50000)
     assert rc == orc == 0
     # entries come from CUDA's sin/cos/exp, so equal pivots are expected but
     # the factors may differ in the last bits
@@ -160,8 +160,14 @@ def test_prescribed_ranks_per_bond(tt):
 
 
 def test_zero_start_and_nonfinite(tt):
+    # X(0,...,0) = 0 but other entries are not: the start moves to the max
     w = W.random_tt([4, 5, 6], [1, 2, 2, 1], seed=3)
     w["gen"]["cores"][0][:, 0, :] = 0.0
+    g, rc, o, orc, ost = run_both(tt, w, 1e-10, 4, 0)
+    assert rc == orc == 0
+    assert_same(g, o)
+    # X = 0 everywhere
+    w["gen"]["cores"][1][:] = 0.0
     g = tt.TTCross(w["n"], w["gen"], max_rank=3, nsamples=0)
     g.run(1e-6)
     assert g.sync(allow=(tt.ERR_ZERO_START,)) == tt.ERR_ZERO_START

@@ -301,6 +301,24 @@ def test_thread_split_does_not_change_pivots():
             np.testing.assert_array_equal(b, d)
 
 
+def test_start_pivot_is_argmax_over_samples_and_origin():
+    """Alg. 1 line 1 with a zero approximation: argmax |X| over the random
+    samples (plus the origin), ties to the lowest column-major index."""
+    w = W.maxwellian(2, 2, [6, 7, 16, 16])
+    o = oracle.Oracle(w["n"], w["gen"], 4)
+    rms, start = o.sample_scan(3000, seed=9)
+    S = oracle.sample_indices(w["n"], 3000, seed=9)
+    cand = np.vstack([np.zeros((1, 4), np.int32), S])
+    vals = np.array([abs(o.entry(c)) for c in cand])
+    best = cand[vals == vals.max()]
+    lin = best[:, 0] + 6 * (best[:, 1] + 7 * (best[:, 2] + 16 * best[:, 3]))
+    np.testing.assert_array_equal(start, best[np.argmin(lin)])
+    assert abs(rms - np.sqrt((vals[1:] ** 2).mean())) <= 1e-15 * rms
+    # the Hilbert tensor peaks at the origin, which is then the start
+    h = oracle.Oracle([9, 9, 9], {"kind": "hilbert"}, 4)
+    assert list(h.sample_scan(500, seed=1)[1]) == [0, 0, 0]
+
+
 def test_zero_start_and_nonfinite():
     w = W.random_tt([4, 5, 6], [1, 2, 2, 1], seed=3)
     w["gen"]["cores"][0][:, 0, :] = 0.0
