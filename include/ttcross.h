@@ -181,6 +181,32 @@ ttc_status ttcross_get_stats(ttc_handle *h, ttc_stats *st);
 /* Frees the instance (waits for its last run).  NULL is accepted. */
 ttc_status ttcross_destroy(ttc_handle *h);
 
+/* Sampled relative error of a TT, computed without allocating memory.
+   The paper has no counterpart: this is for callers that cannot call
+   cudaMalloc (a custom allocator or memory-pool callback, a process whose
+   GPU memory budget is fixed at start-up, a host application that forbids
+   allocation after initialisation).  It evaluates
+   sqrt(sum (X - X~)^2 / sum X^2) over the same SplitMix64 samples as
+   ttcross_run (all entries when nsamples <= 0 or >= prod n), where X is the
+   Hilbert or Maxwellian generator *gen (TTC_GEN_TT is rejected: it would need
+   device data) and X~ the TT whose core m (0-based) is the device array
+   cores[m] laid out [s_m][n_m][s_{m+1}] row-major, as ttcross_get_cores
+   writes it (s: host array of d+1 sizes, s_0 = s_d = 1, s_m <= 128).
+   The result is written to *err, a caller-owned device double, in stream
+   order on `stream`; the call returns after enqueueing two kernels.
+   Scratch: a static 64 KiB device array per GPU holds one partial sum per
+   chunk of 4096 samples, so nsamples is limited to 16,777,216 (larger
+   requests return TTC_ERR_INVALID_ARG).  The first call on a device looks up
+   that array's address; make it before any stream capture.  Every call uses
+   the same array and overwrites what it reads, so calls whose kernels may
+   overlap on the GPU (other streams or host threads) race and must be
+   ordered by the caller.  No cudaMalloc, cudaFree or allocating library call
+   is made.  Errors: INVALID_ARG, CUDA. */
+ttc_status ttcross_sampled_error_noalloc(int d, const int64_t *n, const ttc_generator *gen,
+                                         const double *const *cores, const int64_t *s,
+                                         int64_t nsamples, uint64_t seed, double *err,
+                                         void *stream);
+
 /* Description of the last error on this host thread ("" if none). */
 const char *ttcross_last_error_string(void);
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libttcross.so")
-SOURCES = ["ttc_kernels.cu", "ttc_api.cu", "ttc_probe.cu"]
+SOURCES = ["ttc_kernels.cu", "ttc_api.cu", "ttc_probe.cu", "ttc_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]

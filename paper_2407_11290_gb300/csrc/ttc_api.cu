@@ -51,6 +51,10 @@ struct Carver {
 
 }  // namespace
 
+namespace ttc {
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace ttc
+
 struct ttc_handle {
   int d = 0, nb = 0;
   int64_t n[TTC_MAXD] = {};

@@ -28,7 +28,7 @@ PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "split": PREC_SPLIT, "auto":
 ABI_SYMBOLS = ("ttcross_default_options", "ttcross_create", "ttcross_run", "ttcross_run_batch",
                "ttcross_sync", "ttcross_get_ranks", "ttcross_get_cores", "ttcross_get_pivots",
                "ttcross_get_pivot_inverse", "ttcross_get_stats", "ttcross_destroy",
-               "ttcross_last_error_string")
+               "ttcross_sampled_error_noalloc", "ttcross_last_error_string")
 
 
 class TTCError(RuntimeError):
@@ -96,6 +96,10 @@ def load_library(path: str = LIB_PATH):
         L.ttcross_get_pivot_inverse.argtypes = [P, C.c_int, C.POINTER(C.c_double)]
         L.ttcross_get_stats.argtypes = [P, C.POINTER(Stats)]
         L.ttcross_destroy.argtypes = [P]
+        L.ttcross_sampled_error_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int64),
+                                                    C.POINTER(Generator), C.POINTER(P),
+                                                    C.POINTER(C.c_int64), C.c_int64, C.c_uint64,
+                                                    P, P]
         L.ttcross_last_error_string.restype = C.c_char_p
         for name in ABI_SYMBOLS:
             f = getattr(L, name)
@@ -260,6 +264,37 @@ class TTCross:
         st = Stats()
         _check(self._L.ttcross_get_stats(self._h, C.byref(st)))
         return {f: getattr(st, f) for f, _ in Stats._fields_}
+
+
+def make_generator(gen):
+    """ctypes Generator for a Hilbert / Maxwellian generator dict."""
+    g = Generator()
+    if gen["kind"] == "hilbert":
+        g.kind = GEN_HILBERT
+    elif gen["kind"] == "maxwellian":
+        g.kind = GEN_MAXWELLIAN
+        g.dx, g.dv = int(gen["dx"]), int(gen["dv"])
+        g.a_rho, g.a_u, g.a_T = float(gen["a_rho"]), float(gen["a_u"]), float(gen["a_T"])
+        g.vmin, g.vmax = float(gen["vmin"]), float(gen["vmax"])
+    else:
+        g.kind = GEN_TT
+    return g
+
+
+def sampled_error_noalloc(n, gen, cores, nsamples: int, seed: int, out, stream=None):
+    """Enqueue ttcross_sampled_error_noalloc: ``cores`` are CUDA float64 torch
+    tensors [s_{m-1}, n_m, s_m]; the error is written to the CUDA float64
+    tensor ``out`` (one element).  Allocates nothing."""
+    L = load_library()
+    n = np.ascontiguousarray(n, dtype=np.int64)
+    d = int(n.size)
+    s = np.ascontiguousarray([1] + [int(c.shape[2]) for c in cores[:-1]] + [1], dtype=np.int64)
+    ptrs = (C.c_void_p * d)(*[c.data_ptr() for c in cores])
+    g = make_generator(gen)
+    _check(L.ttcross_sampled_error_noalloc(d, n.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(g),
+                                           ptrs, s.ctypes.data_as(C.POINTER(C.c_int64)),
+                                           int(nsamples), C.c_uint64(seed),
+                                           C.c_void_p(out.data_ptr()), _stream_handle(stream)))
 
 
 def probe_fma_peak(fp64: bool = True, blocks_per_sm: int = 4, iters: int = 1 << 16):
