@@ -118,6 +118,8 @@ typedef struct {
   double x_rms;              /* rms of X over the error samples */
   double err;                /* sampled relative Frobenius error */
   double device_ms;          /* GPU time of the last run (events around it) */
+  double phase_ms[6];        /* persistent runs: GPU time per phase (init, screen,
+                                decide, update, error verification, FP64 refinement) */
   int32_t status;            /* ttc_status of the last run */
   int32_t device_error_where;/* for TTC_ERR_DEVICE_TIMEOUT: the wait that gave up */
 } ttc_stats;

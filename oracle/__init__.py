@@ -76,6 +76,8 @@ def lib():
             L.orc_init_at.argtypes = [P, i32p]
             L.orc_sample_scan.argtypes = [P, C.c_int64, C.c_uint64, f64p, i32p]
             L.orc_screen.argtypes = [P, f64p, i64p, i32p, i32p, f64p]
+            L.orc_residual.restype = C.c_double
+            L.orc_residual.argtypes = [P, C.c_int, C.c_int64, C.c_int64]
             L.orc_apply.argtypes = [P, i32p, i32p, i32p]
             L.orc_run.argtypes = [P, C.c_double, C.c_int64, C.c_uint64, C.c_int, C.POINTER(Stats)]
             L.orc_sampled_error.argtypes = [P, C.c_int64, C.c_uint64, f64p]
@@ -180,6 +182,9 @@ class Oracle:
         rc = self._L.orc_screen(self._h, _p(best, C.c_double), _p(lin, C.c_int64),
                                 _p(row, C.c_int32), _p(col, C.c_int32), _p(mx, C.c_double))
         return rc, dict(best=best, lin=lin, row=row, col=col, maxabs=mx)
+
+    def residual(self, b, a, c) -> float:
+        return float(self._L.orc_residual(self._h, int(b), int(a), int(c)))
 
     def apply(self, add, row, col) -> int:
         add = np.ascontiguousarray(add, dtype=np.int32)

@@ -319,6 +319,11 @@ static best_t screen_rows(const orc_state *s, int b, int64_t a0, int64_t a1) {
   return bt;
 }
 
+double orc_residual(const orc_state *s, int b, int64_t a, int64_t c) {
+  return sb_entry(s, b, a, c) -
+         chain(s->T[b] + a * s->maxr[b], 1, s->R[b] + c, s->cols_cap[b], s->r[b]);
+}
+
 int orc_screen(orc_state *s, double *best, int64_t *lin, int32_t *row,
                int32_t *col, double *maxabs) {
   if (!s->initialized) return ORC_ERR_INVALID_ARG;

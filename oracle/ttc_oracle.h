@@ -96,6 +96,10 @@ int orc_init(orc_state *s);
 int orc_screen(orc_state *s, double *best, int64_t *lin, int32_t *row,
                int32_t *col, double *maxabs);
 
+/* Residual E(a,c) = A(a,c) - chain(T(a,:), R(:,c)) of superblock entry (a,c)
+   of bond b, as the screen computes it. */
+double orc_residual(const orc_state *s, int b, int64_t a, int64_t c);
+
 /* Append pivot (row[b], col[b]) to every bond b with add[b] != 0 (row/col are
    superblock coordinates of the sweep-start superblock), update T, R, U and
    the history, then extend the neighbouring superblocks. */

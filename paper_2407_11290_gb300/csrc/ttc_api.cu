@@ -598,8 +598,10 @@ ttc_status ttcross_get_stats(ttc_handle *h, ttc_stats *out) {
   float ms = 0.f;
   if (h->events_ok && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) out->device_ms = ms;
   Barrier bar;
-  if (cudaMemcpy(&bar, h->d_bar, sizeof bar, cudaMemcpyDeviceToHost) == cudaSuccess)
+  if (cudaMemcpy(&bar, h->d_bar, sizeof bar, cudaMemcpyDeviceToHost) == cudaSuccess) {
     out->device_error_where = bar.where;
+    for (int i = 0; i < 6; ++i) out->phase_ms[i] = bar.phase_ns[i] * 1e-6;
+  }
   return TTC_OK;
 }
 

@@ -104,7 +104,11 @@ struct Barrier {
   int32_t abort;
   int32_t where;         // first wait that ran out
   int32_t overrun;       // the sweep cap was reached before every instance finished
+  int32_t pad;
+  uint64_t phase_ns[8];  // time per phase (CTA 0, barrier exit to barrier exit)
 };
+
+enum PhaseSlot { T_INIT = 0, T_SCREEN = 1, T_DECIDE = 2, T_UPDATE = 3, T_VERIFY = 4, T_REFINE = 5 };
 
 struct RunArgs {
   InstDev *const *insts; // device array of instance pointers

@@ -878,14 +878,44 @@ __device__ bool all_done(const RunArgs &ra) {
 
 extern __shared__ __align__(16) unsigned char dyn_smem[];
 
+// CTA 0 accounts the time between barrier exits to the phase that ran
+struct PhaseClock {
+  uint64_t t;
+  __device__ void start() {
+    if (blockIdx.x == 0 && threadIdx.x == 0) t = globaltimer_ns();
+  }
+  __device__ void lap(const RunArgs &ra, int slot) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const uint64_t now = globaltimer_ns();
+      ra.bar->phase_ns[slot] += now - t;
+      t = now;
+    }
+  }
+};
+
+__device__ bool any_state(const RunArgs &ra, int st) {
+  __shared__ int hit;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    hit = 0;
+    for (int ii = 0; ii < ra.count; ++ii)
+      if (*(volatile const int32_t *)&ra.insts[ii]->ctrl->state == st) hit = 1;
+  }
+  __syncthreads();
+  return hit != 0;
+}
+
 __global__ void __launch_bounds__(NT, 2) k_persistent(RunArgs ra) {
   PhaseSmem &sm = *reinterpret_cast<PhaseSmem *>(dyn_smem);
+  PhaseClock clk;
+  clk.start();
   phase_init1(ra, sm);
   if (!grid_barrier(ra, 1)) return;
   phase_init2(ra, sm);
   if (!grid_barrier(ra, 2)) return;
   phase_init3(ra, sm);
   if (!grid_barrier(ra, 6)) return;
+  clk.lap(ra, T_INIT);
   for (int it = 0;; ++it) {
     if (all_done(ra)) break;
     if (it >= ra.max_iters) {
@@ -894,10 +924,14 @@ __global__ void __launch_bounds__(NT, 2) k_persistent(RunArgs ra) {
     }
     phase_screen(ra, sm);
     if (!grid_barrier(ra, 3)) return;
+    clk.lap(ra, T_SCREEN);
     phase_decide(ra, sm);
     if (!grid_barrier(ra, 4)) return;
+    clk.lap(ra, T_DECIDE);
+    const bool verify = any_state(ra, ST_VERIFY);
     phase_update(ra, sm);
     if (!grid_barrier(ra, 5)) return;
+    clk.lap(ra, verify ? T_VERIFY : T_UPDATE);
   }
 }
 

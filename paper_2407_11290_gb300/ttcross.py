@@ -64,7 +64,8 @@ class Stats(C.Structure):
                 ("refinements", C.c_int64), ("pivots_uncertified", C.c_int64),
                 ("screen_fmas", C.c_int64), ("error_fmas", C.c_int64),
                 ("tau", C.c_double), ("x_rms", C.c_double), ("err", C.c_double),
-                ("device_ms", C.c_double), ("status", C.c_int32),
+                ("device_ms", C.c_double), ("phase_ms", C.c_double * 6),
+                ("status", C.c_int32),
                 ("device_error_where", C.c_int32)]
 
 
@@ -263,7 +264,10 @@ class TTCross:
     def stats(self) -> dict:
         st = Stats()
         _check(self._L.ttcross_get_stats(self._h, C.byref(st)))
-        return {f: getattr(st, f) for f, _ in Stats._fields_}
+        out = {f: getattr(st, f) for f, _ in Stats._fields_}
+        out["phase_ms"] = dict(zip(("init", "screen", "decide", "update", "verify", "refine"),
+                                   list(st.phase_ms)))
+        return out
 
 
 def make_generator(gen):
