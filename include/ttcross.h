@@ -109,8 +109,8 @@ typedef struct {
   int64_t sweeps;            /* residual screens (simultaneous over bonds) */
   int64_t entries_screened;  /* candidate entries screened, summed over sweeps */
   int64_t refinements;       /* tau reductions */
-  int64_t pivots_uncertified;/* mixed forms: pivots whose FP64 re-score could not
-                                prove them the FP64 argmax */
+  int64_t tiles_refined;     /* mixed forms: screen tiles whose error bound could hide
+                                the FP64 argmax and were re-screened in FP64 */
   int64_t screen_fmas;       /* algorithmic FMAs of the screens: sum over sweeps and
                                 bonds of r_k * |superblock_k| */
   int64_t error_fmas;        /* algorithmic FMAs of the sampled-error evaluations */

@@ -111,8 +111,16 @@ ttc_status ensure_cands(ttc_handle *h, const int32_t *grid) {
     CU(cudaFree(h->cand));
     h->cand = nullptr;
   }
-  CU(cudaMalloc(&h->cand, sizeof(Cand) * (size_t)total));
+  // one allocation: FP64 candidates, mixed candidates, refinement list and results
+  const size_t bytes = (sizeof(Cand) + sizeof(MCand) + 2 * sizeof(int32_t) + sizeof(Cand)) *
+                       (size_t)total;
+  CU(cudaMalloc(&h->cand, bytes));
   h->cand_cap = total;
+  char *base = reinterpret_cast<char *>(h->cand);
+  h->hi.mcand = reinterpret_cast<MCand *>(base + sizeof(Cand) * total);
+  h->hi.refine_cand = reinterpret_cast<Cand *>(base + (sizeof(Cand) + sizeof(MCand)) * total);
+  h->hi.refine_list =
+      reinterpret_cast<int32_t *>(base + (2 * sizeof(Cand) + sizeof(MCand)) * total);
   int64_t off = 0;
   for (int b = 0; b < h->nb; ++b) {
     h->bond_cand_cap[b] = need[b];
@@ -155,6 +163,9 @@ ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, 
   ra.bar = h0->d_bar;
   ra.wait_ns = (int64_t)(h0->opt.wait_limit_s * 1e9);
   ra.persistent = h0->opt.host_loop ? 0 : 1;
+  ra.mixed = 0;
+  for (int i = 0; i < count; ++i)
+    if (hs[i]->hi.prec != P_FP64) ra.mixed = 1;
   int64_t iters = 0;
   for (int i = 0; i < count; ++i) {
     int64_t s = hs[i]->opt.max_refine + 4;
@@ -182,6 +193,10 @@ ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, 
     if (done) return TTC_OK;
     CU(launch_phase(PH_SCREEN, ra, h0->grid, s));
     CU(launch_phase(PH_DECIDE, ra, h0->grid, s));
+    if (ra.mixed) {
+      CU(launch_phase(PH_REFINE, ra, h0->grid, s));
+      CU(launch_phase(PH_DECIDE2, ra, h0->grid, s));
+    }
     CU(launch_phase(PH_UPDATE, ra, h0->grid, s));
   }
   return fail(TTC_ERR_CUDA, "host-stepped run did not finish");
@@ -222,8 +237,7 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     return fail(TTC_ERR_INVALID_ARG, "max_rank=%d outside [1,%d]", o.max_rank, RCAP);
   if (o.precision < TTC_PREC_FP64 || o.precision > TTC_PREC_AUTO)
     return fail(TTC_ERR_INVALID_ARG, "unknown precision %d", o.precision);
-  if (o.precision != TTC_PREC_FP64)
-    return fail(TTC_ERR_INVALID_ARG, "precision %d is not built in this library", o.precision);
+  if (o.topk < 1 || o.topk > 16) return fail(TTC_ERR_INVALID_ARG, "topk outside [1,16]");
   if (o.max_refine < 0) return fail(TTC_ERR_INVALID_ARG, "max_refine < 0");
   if (!(o.wait_limit_s > 0.0) || o.wait_limit_s > 600.0)
     return fail(TTC_ERR_INVALID_ARG, "wait_limit_s must be in (0, 600]");
@@ -306,7 +320,9 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     st = overflow ? st : st * n[m];
   }
   I.gen = gen->kind;
-  I.prec = o.precision;
+  // AUTO: the float-float screen; plain FP32 resolves residuals only down to
+  // about 1e-7 of the largest entries, which the stop thresholds here undercut
+  I.prec = o.precision == TTC_PREC_AUTO ? P_SPLIT : o.precision;
   I.topk = o.topk;
   I.nsamples = ns;
   I.exhaustive = exhaustive ? 1 : 0;
@@ -334,6 +350,8 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     InstDev *dinst = cv.take<InstDev>(1);
     InstDev **dlist = cv.take<InstDev *>(1);
     double *hilb = cv.take<double>(hlen);
+    float *hilb_hi = cv.take<float>(hlen);
+    float *hilb_lo = cv.take<float>(hlen);
     double *tt = cv.take<double>(tt_total);
     double *xs = cv.take<double>(ns);
     double *errp = cv.take<double>(GRID_CAP);
@@ -366,6 +384,12 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
       B.J.lin = cv.take<int64_t>(cap);
       B.J.sum = cv.take<int32_t>(cap);
       B.Thi = B.Tlo = B.Rhi = B.Rlo = nullptr;
+      if (I.prec != P_FP64) {
+        B.Thi = cv.take<float>(cap * B.ldT);
+        B.Tlo = cv.take<float>(cap * B.ldT);
+        B.Rhi = cv.take<float>(cap * B.ldR);
+        B.Rlo = cv.take<float>(cap * B.ldR);
+      }
       core_cap = std::max(core_cap, B.ldT * cap);
     }
     core_cap = std::max(core_cap, h->bond_cap[d - 2] * n[d - 1]);
@@ -384,6 +408,8 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
       h->d_inst = dinst;
       h->d_list = dlist;
       I.hilb = hilb;
+      I.hilb_hi = hilb_hi;
+      I.hilb_lo = hilb_lo;
       I.tt = tt;
       I.xs = xs;
       I.err_part = errp;
@@ -408,9 +434,18 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     return cleanup(fail(TTC_ERR_CUDA, "cudaMemset failed"));
   if (gen->kind == TTC_GEN_HILBERT) {
     std::vector<double> tab(hlen);
-    for (int64_t s = 0; s < hlen; ++s) tab[s] = 1.0 / (double)(s + 1);
+    std::vector<float> thi(hlen), tlo(hlen);
+    for (int64_t s = 0; s < hlen; ++s) {
+      tab[s] = 1.0 / (double)(s + 1);
+      thi[s] = (float)tab[s];
+      tlo[s] = (float)(tab[s] - (double)thi[s]);
+    }
     if (cudaMemcpy((void *)I.hilb, tab.data(), sizeof(double) * hlen, cudaMemcpyHostToDevice) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaMemcpy((void *)I.hilb_hi, thi.data(), sizeof(float) * hlen, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy((void *)I.hilb_lo, tlo.data(), sizeof(float) * hlen, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
       return cleanup(fail(TTC_ERR_CUDA, "copy of the Hilbert table failed"));
   }
   if (gen->kind == TTC_GEN_TT) {
@@ -588,7 +623,7 @@ ttc_status ttcross_get_stats(ttc_handle *h, ttc_stats *out) {
   out->sweeps = c.sweeps;
   out->entries_screened = c.entries;
   out->refinements = c.refinements;
-  out->pivots_uncertified = c.uncertified;
+  out->tiles_refined = c.tiles_refined;
   out->screen_fmas = c.screen_fmas;
   out->error_fmas = c.error_fmas;
   out->tau = c.tau;

@@ -59,7 +59,11 @@ struct Ctrl {
   int64_t best_lin[TTC_MAXD];
   int32_t best_row[TTC_MAXD], best_col[TTC_MAXD];
   double eps, tau, xrms, den, err;
-  int64_t sweeps, entries, refinements, uncertified;
+  int64_t sweeps, entries, refinements, tiles_refined;
+  int32_t screened;          // screened in this sweep (set by the screen, cleared by decide)
+  int32_t pad2;
+  int32_t pending[TTC_MAXD]; // mixed forms: bond merged, waiting for the refinement
+  int32_t nrefine_bond[TTC_MAXD];
   int64_t screen_fmas, error_fmas;  // algorithmic FMAs of the screens / errors
   int32_t max_refine;
   int32_t grid[TTC_MAXD];  // subtensor pieces per mode (0 = library tiles)
@@ -89,7 +93,20 @@ struct InstDev {
   struct Cand *start_part;           // [max grid] per-CTA argmax |X| over the samples
   int32_t err_part_cap;
   struct Cand *cand;
+  struct MCand *mcand;               // mixed-form tile candidates (same slots as cand)
+  int32_t *refine_list;              // [cand capacity][2]: (bond, tile) to re-screen in FP64
+  struct Cand *refine_cand;          // their FP64 results
   Ctrl *ctrl;
+};
+
+// Mixed-form tile candidate: the tile's best |E| in FP32 / float-float and
+// bounds on the FP64 residual of the tile's entries:
+//   |E64(best)| <= v * (1 + 4u) + eabs,  |E64(other)| <= rest * (1 + 4u) + eabs
+struct MCand {
+  float v, rest;
+  double eabs;
+  int64_t lin;
+  int32_t row, col;
 };
 
 struct Cand {            // one screen candidate (max |E| of a tile, or top-k)
@@ -110,9 +127,16 @@ struct Barrier {
 
 enum PhaseSlot { T_INIT = 0, T_SCREEN = 1, T_DECIDE = 2, T_UPDATE = 3, T_VERIFY = 4, T_REFINE = 5 };
 
+// shadows of an FP64 value as (hi, lo) floats
+__device__ __forceinline__ void split2(double x, float &hi, float &lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(x - (double)hi);
+}
+
 struct RunArgs {
   InstDev *const *insts; // device array of instance pointers
   int32_t count;
+  int32_t mixed;         // some instance screens in FP32 / float-float
   Barrier *bar;
   int64_t wait_ns;
   int32_t persistent;

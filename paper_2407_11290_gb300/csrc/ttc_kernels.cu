@@ -30,16 +30,36 @@ constexpr int NT = 256;  // threads per CTA
 constexpr int KC = 32;   // depth of the T / R chunks staged in shared memory
 
 struct ScreenSmem {
-  double Ts[KC][BM];
-  double Rs[KC][BN];
+  union {
+    struct {
+      double Ts[KC][BM];
+      double Rs[KC][BN];
+    } d;
+    struct {
+      float Th[KC][BM], Tl[KC][BM];
+      float Rh[KC][BN], Rl[KC][BN];
+    } f;
+  } op;
   int32_t srow[BM], scol[BN];
   int64_t lrow[BM], lcol[BN];
   int32_t ridx[BM][TTC_MAXD];
   int32_t cidx[BN][TTC_MAXD];
+  float rowS[BM], colR[BN];
+  uint64_t sk[NT / 32];
+  int64_t sl[NT / 32];
+  int32_t sr[NT / 32], sc[NT / 32];
+  float fred[NT / 32];
 };
+
+constexpr int TOPK_MAX = 16;
 
 struct DecideSmem {
   double ua[RCAP], bu[RCAP], brow[RCAP];
+  int32_t sel[TOPK_MAX];
+  uint64_t skey[TOPK_MAX];
+  int64_t slin[TOPK_MAX];
+  int32_t srow[TOPK_MAX], scol[TOPK_MAX];
+  int32_t cnt;
   double red[NT / 32];
   uint64_t rk[NT / 32];
   int64_t rl[NT / 32];
@@ -235,16 +255,16 @@ __device__ __forceinline__ void tile_cols(const InstDev &in, const TileGeo &g, i
 // screen of one tile in FP64: A - chain(T(a,:), R(:,c)) for a 64 x 64 tile,
 // 4 x 4 entries per thread, T / R staged through shared memory in 32-deep
 // chunks; the accumulation order over t is the contract's serial chain.
-__device__ void screen_tile_fp64(const InstDev &in, int b, int K, int64_t r0, int nr, int64_t c0,
-                                 int nc, Cand *out, ScreenSmem &sm) {
-  const BondDev &B = in.bond[b];
+// per-row / per-column data of a tile: linear-index parts, index sums
+// (Hilbert) or the multi-indices (other generators)
+__device__ void stage_meta(const InstDev &in, int b, int64_t r0, int nr, int64_t c0, int nc,
+                           ScreenSmem &sm) {
   const SetDev &L = left_set(in, b);
   const SetDev &Rset = right_set(in, b);
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x;
   const int64_t nb0 = in.n[b], nb1 = in.n[b + 1];
   const bool hil = in.gen == 0;
   const int wl = b, wr = in.d - b - 2;
-  __syncthreads();
   for (int x = tid; x < BM; x += NT) {
     if (x < nr) {
       const int64_t a = r0 + x, p = a / nb0, i = a - p * nb0;
@@ -269,6 +289,25 @@ __device__ void screen_tile_fp64(const InstDev &in, int b, int K, int64_t r0, in
       }
     }
   }
+}
+
+__device__ __forceinline__ double tile_entry(const InstDev &in, const ScreenSmem &sm, int wl, int wr,
+                                             int rr, int cc) {
+  if (in.gen == 0) return in.hilb[sm.srow[rr] + sm.scol[cc]];
+  int32_t idx[TTC_MAXD];
+  for (int m = 0; m <= wl; ++m) idx[m] = sm.ridx[rr][m];
+  for (int m = 0; m <= wr; ++m) idx[wl + 1 + m] = sm.cidx[cc][m];
+  return gen_full(in, idx);
+}
+
+template <bool HIL>
+__device__ __noinline__ void screen_tile_fp64_t(const InstDev &in, int b, int K, int64_t r0, int nr,
+                                                int64_t c0, int nc, Cand *out, ScreenSmem &sm) {
+  const BondDev &B = in.bond[b];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int wl = b, wr = in.d - b - 2;
+  __syncthreads();
+  stage_meta(in, b, r0, nr, c0, nc, sm);
   double acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -279,19 +318,19 @@ __device__ void screen_tile_fp64(const InstDev &in, int b, int K, int64_t r0, in
     __syncthreads();
     for (int x = tid; x < kc * BM; x += NT) {
       const int tt = x / BM, rr = x - tt * BM;
-      sm.Ts[tt][rr] = rr < nr ? B.T[(int64_t)(t0 + tt) * B.ldT + r0 + rr] : 0.0;
+      sm.op.d.Ts[tt][rr] = rr < nr ? B.T[(int64_t)(t0 + tt) * B.ldT + r0 + rr] : 0.0;
     }
     for (int x = tid; x < kc * BN; x += NT) {
       const int tt = x / BN, cc = x - tt * BN;
-      sm.Rs[tt][cc] = cc < nc ? B.R[(int64_t)(t0 + tt) * B.ldR + c0 + cc] : 0.0;
+      sm.op.d.Rs[tt][cc] = cc < nc ? B.R[(int64_t)(t0 + tt) * B.ldR + c0 + cc] : 0.0;
     }
     __syncthreads();
     for (int tt = 0; tt < kc; ++tt) {
       double tv[4], rv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) tv[u] = sm.Ts[tt][ty + 16 * u];
+      for (int u = 0; u < 4; ++u) tv[u] = sm.op.d.Ts[tt][ty + 16 * u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) rv[v] = sm.Rs[tt][tx + 16 * v];
+      for (int v = 0; v < 4; ++v) rv[v] = sm.op.d.Rs[tt][tx + 16 * v];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -307,15 +346,7 @@ __device__ void screen_tile_fp64(const InstDev &in, int b, int K, int64_t r0, in
     for (int v = 0; v < 4; ++v) {
       const int cc = tx + 16 * v;
       if (cc >= nc) continue;
-      double A;
-      if (hil) {
-        A = in.hilb[sm.srow[rr] + sm.scol[cc]];
-      } else {
-        int32_t idx[TTC_MAXD];
-        for (int m = 0; m <= wl; ++m) idx[m] = sm.ridx[rr][m];
-        for (int m = 0; m <= wr; ++m) idx[wl + 1 + m] = sm.cidx[cc][m];
-        A = gen_full(in, idx);
-      }
+      const double A = HIL ? in.hilb[sm.srow[rr] + sm.scol[cc]] : tile_entry(in, sm, wl, wr, rr, cc);
       const double e = __dsub_rn(A, acc[u][v]);
       const uint64_t k = abs_key(e);
       if (best.row < 0 || k >= best.key) {
@@ -329,16 +360,210 @@ __device__ void screen_tile_fp64(const InstDev &in, int b, int K, int64_t r0, in
       }
     }
   }
-  __shared__ uint64_t sk[NT / 32];
-  __shared__ int64_t sl[NT / 32];
-  __shared__ int32_t sr[NT / 32], sc[NT / 32];
-  best = block_best(best, sk, sl, sr, sc);
+  best = block_best(best, sm.sk, sm.sl, sm.sr, sm.sc);
   if (tid == 0) {
     out->key = best.key;
     out->lin = best.lin;
     out->row = best.row;
     out->col = best.col;
   }
+}
+
+__device__ __forceinline__ void screen_tile_fp64(const InstDev &in, int b, int K, int64_t r0,
+                                                 int nr, int64_t c0, int nc, Cand *out,
+                                                 ScreenSmem &sm) {
+  if (in.gen == 0)
+    screen_tile_fp64_t<true>(in, b, K, r0, nr, c0, nc, out, sm);
+  else
+    screen_tile_fp64_t<false>(in, b, K, r0, nr, c0, nc, out, sm);
+}
+
+// ---------------------------------------------------------------------------
+// screen of one tile in FP32 (SPLIT = false) or float-float (SPLIT = true)
+// from the (hi, lo) shadows of T and R.  Besides the tile's best |E| it
+// bounds the FP64 residual of every entry (MCand), so that the merge can
+// prove which tiles cannot hold the FP64 argmax.
+//   float-float product: T R = (Th + Tl)(Rh + Rl) ~ Th Rh (exact as p + pl)
+//   + (Th Rl + Tl Rh); sums (sh, sl) by TwoSum, renormalised every step.
+//   bound, with S = max_a sum_t |T(a,t)|, Rm = max |R(t,c)|, A = max |A|:
+//     FP32 : 2 (K + 3) u (A + S Rm),  u = 2^-24
+//     split: 4 (3K + 8) u^2 (A + S Rm)
+//   plus 4u |E| for the last roundings.
+template <bool SPLIT, bool HIL>
+__device__ __noinline__ void screen_tile_mixed_t(const InstDev &in, int b, int K, int64_t r0,
+                                                 int nr, int64_t c0, int nc, MCand *out,
+                                                 ScreenSmem &sm) {
+  const BondDev &B = in.bond[b];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int wl = b, wr = in.d - b - 2;
+  __syncthreads();
+  stage_meta(in, b, r0, nr, c0, nc, sm);
+  for (int x = tid; x < BM; x += NT) sm.rowS[x] = 0.f;
+  for (int x = tid; x < BN; x += NT) sm.colR[x] = 0.f;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      sh[u][v] = 0.f;
+      sl[u][v] = 0.f;
+    }
+  for (int t0 = 0; t0 < K; t0 += KC) {
+    const int kc = min(KC, K - t0);
+    __syncthreads();
+    for (int x = tid; x < kc * BM; x += NT) {
+      const int tt = x / BM, rr = x - tt * BM;
+      const int64_t o = (int64_t)(t0 + tt) * B.ldT + r0 + rr;
+      sm.op.f.Th[tt][rr] = rr < nr ? B.Thi[o] : 0.f;
+      if (SPLIT) sm.op.f.Tl[tt][rr] = rr < nr ? B.Tlo[o] : 0.f;
+    }
+    for (int x = tid; x < kc * BN; x += NT) {
+      const int tt = x / BN, cc = x - tt * BN;
+      const int64_t o = (int64_t)(t0 + tt) * B.ldR + c0 + cc;
+      sm.op.f.Rh[tt][cc] = cc < nc ? B.Rhi[o] : 0.f;
+      if (SPLIT) sm.op.f.Rl[tt][cc] = cc < nc ? B.Rlo[o] : 0.f;
+    }
+    __syncthreads();
+    if (tid < BM) {
+      float acc = sm.rowS[tid];
+      for (int tt = 0; tt < kc; ++tt) acc += fabsf(sm.op.f.Th[tt][tid]);
+      sm.rowS[tid] = acc;
+    } else if (tid < BM + BN) {
+      const int c = tid - BM;
+      float m = sm.colR[c];
+      for (int tt = 0; tt < kc; ++tt) m = fmaxf(m, fabsf(sm.op.f.Rh[tt][c]));
+      sm.colR[c] = m;
+    }
+    for (int tt = 0; tt < kc; ++tt) {
+      float th[4], tl[4], rh[4], rl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        th[u] = sm.op.f.Th[tt][ty + 16 * u];
+        tl[u] = SPLIT ? sm.op.f.Tl[tt][ty + 16 * u] : 0.f;
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        rh[v] = sm.op.f.Rh[tt][tx + 16 * v];
+        rl[v] = SPLIT ? sm.op.f.Rl[tt][tx + 16 * v] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          if (SPLIT) {
+            const float p = __fmul_rn(th[u], rh[v]);
+            const float pl = __fmaf_rn(th[u], rh[v], -p);
+            const float c = __fmaf_rn(th[u], rl[v], __fmul_rn(tl[u], rh[v]));
+            const float s1 = __fadd_rn(sh[u][v], p);
+            const float bb = __fsub_rn(s1, sh[u][v]);
+            const float e = __fadd_rn(__fsub_rn(sh[u][v], __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+            const float lo = __fadd_rn(sl[u][v], __fadd_rn(e, __fadd_rn(pl, c)));
+            const float s2 = __fadd_rn(s1, lo);
+            sl[u][v] = __fsub_rn(lo, __fsub_rn(s2, s1));
+            sh[u][v] = s2;
+          } else {
+            sh[u][v] = __fmaf_rn(th[u], rh[v], sh[u][v]);
+          }
+        }
+    }
+  }
+  float bv = -1.f, v2 = 0.f, amax = 0.f;
+  int64_t bl = LLONG_MAX;
+  int32_t brow = -1, bcol = -1;
+  bool bad = false;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int rr = ty + 16 * u;
+    if (rr >= nr) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int cc = tx + 16 * v;
+      if (cc >= nc) continue;
+      float ah, al;
+      if (HIL) {
+        ah = in.hilb_hi[sm.srow[rr] + sm.scol[cc]];
+        al = in.hilb_lo[sm.srow[rr] + sm.scol[cc]];
+      } else {
+        split2(tile_entry(in, sm, wl, wr, rr, cc), ah, al);
+      }
+      const float e = __fadd_rn(__fsub_rn(ah, sh[u][v]), __fsub_rn(al, sl[u][v]));
+      const float ae = fabsf(e);
+      amax = fmaxf(amax, fabsf(ah));
+      if (!(ae <= FLT_MAX)) bad = true;
+      const int64_t l = sm.lrow[rr] + sm.lcol[cc];
+      if (ae > bv || (ae == bv && l < bl)) {
+        v2 = fmaxf(v2, bv);
+        bv = ae;
+        bl = l;
+        brow = (int32_t)(r0 + rr);
+        bcol = (int32_t)(c0 + cc);
+      } else {
+        v2 = fmaxf(v2, ae);
+      }
+    }
+  }
+  KeyBest best{brow >= 0 ? (uint64_t)__float_as_uint(bv) : 0ull, bl, brow, bcol};
+  best = block_best(best, sm.sk, sm.sl, sm.sr, sm.sc);
+  __shared__ int32_t wrow, wcol;
+  __shared__ float wval;
+  __shared__ int wbad;
+  if (tid == 0) {
+    wrow = best.row;
+    wcol = best.col;
+    wval = __uint_as_float((unsigned)best.key);
+    wbad = 0;
+  }
+  __syncthreads();
+  if (bad) wbad = 1;
+  // the tile's best among the others: every thread's second value, and the
+  // thread bests that lost to the winner
+  float rest = (brow == wrow && bcol == wcol) ? v2 : fmaxf(fmaxf(bv, 0.f), v2);
+  float Smax = 0.f, Rmax = 0.f;
+  for (int x = tid; x < nr; x += NT) Smax = fmaxf(Smax, sm.rowS[x]);
+  for (int x = tid; x < nc; x += NT) Rmax = fmaxf(Rmax, sm.colR[x]);
+  for (int off = 16; off > 0; off >>= 1) {
+    rest = fmaxf(rest, __shfl_down_sync(0xffffffffu, rest, off));
+    amax = fmaxf(amax, __shfl_down_sync(0xffffffffu, amax, off));
+    Smax = fmaxf(Smax, __shfl_down_sync(0xffffffffu, Smax, off));
+    Rmax = fmaxf(Rmax, __shfl_down_sync(0xffffffffu, Rmax, off));
+  }
+  __shared__ float wr4[NT / 32][4];
+  const int w = tid >> 5;
+  if ((tid & 31) == 0) {
+    wr4[w][0] = rest;
+    wr4[w][1] = amax;
+    wr4[w][2] = Smax;
+    wr4[w][3] = Rmax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 1; i < NT / 32; ++i) {
+      rest = fmaxf(rest, wr4[i][0]);
+      amax = fmaxf(amax, wr4[i][1]);
+      Smax = fmaxf(Smax, wr4[i][2]);
+      Rmax = fmaxf(Rmax, wr4[i][3]);
+    }
+    const double u = 5.9604644775390625e-8;  // 2^-24
+    const double scale = (double)amax + (double)Smax * (double)Rmax;
+    const double eabs = SPLIT ? 4.0 * (3.0 * K + 8.0) * u * u * scale
+                              : 2.0 * (K + 3.0) * u * scale;
+    out->v = wbad ? INFINITY : wval;
+    out->rest = wbad ? INFINITY : rest;
+    out->eabs = isfinite(eabs) ? eabs : INFINITY;
+    out->lin = best.lin;
+    out->row = best.row;
+    out->col = best.col;
+  }
+}
+
+template <bool SPLIT>
+__device__ __forceinline__ void screen_tile_mixed(const InstDev &in, int b, int K, int64_t r0,
+                                                  int nr, int64_t c0, int nc, MCand *out,
+                                                  ScreenSmem &sm) {
+  if (in.gen == 0)
+    screen_tile_mixed_t<SPLIT, true>(in, b, K, r0, nr, c0, nc, out, sm);
+  else
+    screen_tile_mixed_t<SPLIT, false>(in, b, K, r0, nr, c0, nc, out, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -351,9 +576,24 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
     const InstDev &in = *ra.insts[ii];
     const Ctrl &cr = *in.ctrl;
     const int st = *(volatile const int32_t *)&cr.state;
-    if (st != ST_SCREEN && st != ST_UPDATE) continue;
+    if (st != ST_SCREEN) continue;
     int32_t r[TTC_MAXD];
     for (int b = 0; b < in.nb; ++b) r[b] = *(volatile const int32_t *)&cr.r[b];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      // bookkeeping of this screen, from the ranks it uses
+      Ctrl &cw = *in.ctrl;
+      int64_t entries = 0, fmas = 0;
+      for (int b = 0; b < in.nb; ++b) {
+        const TileGeo g = tile_geo(in, cr, r, b);
+        cw.ntiles[b] = (int32_t)(g.nrt * g.nct);
+        entries += g.rows * g.cols;
+        fmas += g.rows * g.cols * r[b];
+      }
+      cw.sweeps += 1;
+      cw.entries += entries;
+      cw.screen_fmas += fmas;
+      cw.screened = 1;
+    }
     for (int b = 0; b < in.nb; ++b) {
       const TileGeo g = tile_geo(in, cr, r, b);
       const int64_t nt = g.nrt * g.nct;
@@ -365,7 +605,14 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
         int nr, nc;
         tile_rows(in, g, b, tr, r0, nr);
         tile_cols(in, g, b, tc, c0, nc);
-        screen_tile_fp64(in, b, r[b], r0, nr, c0, nc, in.cand + in.bond[b].cand_base + lt, sm.s);
+        if (in.prec == P_SPLIT)
+          screen_tile_mixed<true>(in, b, r[b], r0, nr, c0, nc,
+                                  in.mcand + in.bond[b].cand_base + lt, sm.s);
+        else if (in.prec == P_FP32)
+          screen_tile_mixed<false>(in, b, r[b], r0, nr, c0, nc,
+                                   in.mcand + in.bond[b].cand_base + lt, sm.s);
+        else
+          screen_tile_fp64(in, b, r[b], r0, nr, c0, nc, in.cand + in.bond[b].cand_base + lt, sm.s);
       }
       base += nt;
     }
@@ -439,139 +686,276 @@ __device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int
   return true;
 }
 
-// stop test on the cached best residuals: add a pivot on bond b while its
-// best |E| exceeds tau * rms(X) and the cap allows; returns bonds added.
-__device__ int decide_and_append(const InstDev &in, Ctrl &cr, DecideSmem &sm) {
-  const double theta = cr.tau * cr.xrms;
-  int32_t add[TTC_MAXD];
-  int nadd = 0;
-  for (int b = 0; b < in.nb; ++b) {
-    const double v = __longlong_as_double((long long)cr.best_key[b]);
-    add[b] = (v > theta && v > 0.0 && cr.r[b] < cr.maxr[b]) ? 1 : 0;
-    nadd += add[b];
+// FP64 residual of superblock entry (a, c) with the contract's chain
+__device__ double residual64(const InstDev &in, const Ctrl &cr, int b, int64_t a, int64_t c) {
+  const BondDev &B = in.bond[b];
+  double acc = 0.0;
+  for (int t = 0; t < cr.r[b]; ++t)
+    acc = __fma_rn(B.T[(int64_t)t * B.ldT + a], B.R[(int64_t)t * B.ldR + c], acc);
+  return __dsub_rn(sb_entry(in, b, a, c), acc);
+}
+
+__device__ void fail_instance(Ctrl &cr, int32_t status) {
+  if (threadIdx.x == 0) {
+    cr.status = status;
+    cr.state = ST_DONE;
   }
-  if (nadd == 0) return 0;
-  for (int b = 0; b < in.nb; ++b) {
-    if (!add[b]) continue;
-    if (!append_pivot(in, cr, b, cr.best_row[b], cr.best_col[b], sm)) {
-      if (threadIdx.x == 0) {
-        cr.status = 4;  // TTC_ERR_NONFINITE
-        cr.state = ST_DONE;
+}
+
+// stop test and pivot append for bond b on its merged best (block-wide): add
+// the pivot while the best |E| exceeds tau * rms(X) and the cap allows.  The
+// bond's own rank is the only rank this touches, so bonds decide in parallel.
+__device__ void finalize_bond(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
+  const uint64_t key = cr.best_key[b];
+  const int32_t row = cr.best_row[b], col = cr.best_col[b];
+  __syncthreads();
+  if (key > KEY_INF || row < 0) {
+    fail_instance(cr, 4);  // TTC_ERR_NONFINITE
+    if (threadIdx.x == 0) cr.add[b] = 0;
+    __syncthreads();
+    return;
+  }
+  const double v = __longlong_as_double((long long)key);
+  const bool add = v > cr.tau * cr.xrms && v > 0.0 && cr.r[b] < cr.maxr[b];
+  bool ok = true;
+  if (add) ok = append_pivot(in, cr, b, row, col, sm);
+  if (!ok) fail_instance(cr, 4);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cr.add[b] = (add && ok) ? 1 : 0;
+    cr.r[b] += (add && ok) ? 1 : 0;
+  }
+  __syncthreads();
+}
+
+// FP64 form: merge the tile candidates of bond b (the Allgather of Alg. 3)
+__device__ void merge_bond_fp64(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
+  const int64_t nt = cr.ntiles[b];
+  KeyBest best{0ull, LLONG_MAX, -1, -1};
+  const Cand *cand = in.cand + in.bond[b].cand_base;
+  for (int64_t t = threadIdx.x; t < nt; t += NT) {
+    KeyBest o{cand[t].key, cand[t].lin, cand[t].row, cand[t].col};
+    kb_take(best, o);
+  }
+  best = block_best(best, sm.rk, sm.rl, sm.rr, sm.rc);
+  if (threadIdx.x == 0) {
+    cr.best_key[b] = best.key;
+    cr.best_lin[b] = best.lin;
+    cr.best_row[b] = best.row;
+    cr.best_col[b] = best.col;
+  }
+  __syncthreads();
+}
+
+// mixed forms, part 1 for bond b: re-score the top-k tile bests in FP64,
+// then queue for the FP64 refinement every tile whose bound reaches the best
+// exact value (when that exceeds the threshold theta: the tile could hold the
+// FP64 argmax, or an equal residual with a lower index) or exceeds theta
+// (otherwise: the tile could hold an entry that must become a pivot).
+__device__ void merge_bond_mixed(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
+  const int64_t nt = cr.ntiles[b];
+  const MCand *mc = in.mcand + in.bond[b].cand_base;
+  int32_t *list = in.refine_list + 2 * in.bond[b].cand_base;
+  const int k = (int)min((int64_t)min(in.topk, TOPK_MAX), nt);
+  // one pass: every thread keeps its k best tiles, the block merges them
+  KeyBest loc[TOPK_MAX];
+  for (int j = 0; j < k; ++j) loc[j] = KeyBest{0ull, LLONG_MAX, -1, -1};
+  for (int64_t t = threadIdx.x; t < nt; t += NT) {
+    const float v = mc[t].v;
+    KeyBest o{(v == v) ? (uint64_t)__float_as_uint(v) : 0xFFFFFFFFull, mc[t].lin, 0, (int32_t)t};
+    for (int j = 0; j < k; ++j) {
+      if (loc[j].row < 0 || key_better(o.key, o.lin, loc[j].key, loc[j].lin)) {
+        const KeyBest tmp = loc[j];
+        loc[j] = o;
+        o = tmp;
+        if (o.row < 0) break;
       }
-      __syncthreads();
-      return -1;
+    }
+  }
+  for (int j = 0; j < k; ++j) {
+    // the block's j-th best: the best head among the threads' lists
+    KeyBest head = loc[0];
+    KeyBest win = block_best(head, sm.rk, sm.rl, sm.rr, sm.rc);
+    if (threadIdx.x == 0) sm.sel[j] = win.row >= 0 ? win.col : -1;
+    __syncthreads();
+    if (loc[0].row >= 0 && loc[0].col == sm.sel[j]) {
+      for (int q = 0; q + 1 < k; ++q) loc[q] = loc[q + 1];
+      loc[k - 1] = KeyBest{0ull, LLONG_MAX, -1, -1};
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < k) {
+    const int32_t t = sm.sel[threadIdx.x];
+    if (t >= 0) {
+      const MCand &c = mc[t];
+      sm.skey[threadIdx.x] = abs_key(residual64(in, cr, b, c.row, c.col));
+      sm.slin[threadIdx.x] = c.lin;
+      sm.srow[threadIdx.x] = c.row;
+      sm.scol[threadIdx.x] = c.col;
+    } else {
+      sm.skey[threadIdx.x] = 0ull;
+      sm.slin[threadIdx.x] = LLONG_MAX;
+      sm.srow[threadIdx.x] = -1;
+      sm.scol[threadIdx.x] = -1;
+    }
+  }
+  if (threadIdx.x == 0) sm.cnt = 0;
+  __syncthreads();
+  KeyBest vb{0ull, LLONG_MAX, -1, -1};
+  for (int j = 0; j < k; ++j) {
+    KeyBest o{sm.skey[j], sm.slin[j], sm.srow[j], sm.scol[j]};
+    kb_take(vb, o);
+  }
+  const double vstar = __longlong_as_double((long long)(vb.key > KEY_INF ? KEY_INF : vb.key));
+  const double theta = cr.tau * cr.xrms;
+  const bool strict = !(vstar > theta);
+  const double thr = strict ? theta : vstar;
+  const double g = 1.0 + 4.0 * 5.9604644775390625e-8;
+  for (int64_t t = threadIdx.x; t < nt; t += NT) {
+    const MCand &c = mc[t];
+    bool taken = false;
+    for (int q = 0; q < k; ++q) taken |= sm.sel[q] == (int32_t)t;
+    const double top = taken ? (double)c.rest : fmax((double)c.v, (double)c.rest);
+    const double U = top * g + c.eabs;
+    if (!(U == U) || (strict ? U > thr : U >= thr)) {
+      const int slot = atomicAdd(&sm.cnt, 1);
+      list[2 * slot] = b;
+      list[2 * slot + 1] = (int32_t)t;
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int b = 0; b < in.nb; ++b) {
-      cr.r_old[b] = cr.r[b];
-      cr.add[b] = add[b];
-      cr.r[b] += add[b];
-    }
-    cr.state = ST_UPDATE;
+    cr.best_key[b] = vb.key;
+    cr.best_lin[b] = vb.lin;
+    cr.best_row[b] = vb.row;
+    cr.best_col[b] = vb.col;
+    cr.nrefine_bond[b] = sm.cnt;
+    cr.pending[b] = 1;
+    atomicAdd((unsigned long long *)&cr.tiles_refined, (unsigned long long)sm.cnt);
   }
   __syncthreads();
-  return nadd;
 }
 
-__device__ void decide_instance(const RunArgs &ra, int ii, DecideSmem &sm) {
-  const InstDev &in = *ra.insts[ii];
-  Ctrl &cr = *in.ctrl;
-  const int st = cr.state;
+// sampled-error verification of an instance whose bonds all stopped (Sec. 5)
+__device__ void verify_instance(const InstDev &in, Ctrl &cr, DecideSmem &sm) {
+  double part = 0.0;
+  for (int c = threadIdx.x; c < (int)gridDim.x; c += NT) part += in.err_part[c];
+  const double num = block_sum(part, sm.red);
+  if (threadIdx.x == 0) {
+    cr.screened = 0;
+    const double err = sqrt(num / cr.den);
+    cr.err = err;
+    int64_t per = cr.r[0];
+    for (int b = 1; b < in.nb; ++b) per += (int64_t)cr.r[b - 1] * cr.r[b];
+    per += cr.r[in.nb - 1];
+    cr.error_fmas += per * in.nsamples;
+    for (int b = 0; b < in.nb; ++b) cr.add[b] = 0;
+    sm.flag = 0;
+    if (!isfinite(err)) {
+      cr.status = 4;
+      cr.state = ST_DONE;
+    } else if (cr.eps == 0.0 || err <= cr.eps) {
+      cr.status = 0;
+      cr.state = ST_DONE;
+    } else {
+      sm.flag = 1;
+    }
+  }
   __syncthreads();
-  if (st == ST_DONE) return;
-  if (st == ST_VERIFY) {
-    // sampled error (Sec. 5) from the partial sums of the update phase
-    double part = 0.0;
-    for (int c = threadIdx.x; c < (int)gridDim.x; c += NT) part += in.err_part[c];
-    const double num = block_sum(part, sm.red);
+  // tau /= 10 until a bond adds, the caps are hit or the refinements run out
+  while (sm.flag) {
+    __syncthreads();
     if (threadIdx.x == 0) {
-      const double err = sqrt(num / cr.den);
-      cr.err = err;
-      int64_t per = cr.r[0];
-      for (int b = 1; b < in.nb; ++b) per += (int64_t)cr.r[b - 1] * cr.r[b];
-      per += cr.r[in.nb - 1];
-      cr.error_fmas += per * in.nsamples;
-      sm.flag = 0;
-      if (!isfinite(err)) {
-        cr.status = 4;
+      bool capped = true;
+      for (int b = 0; b < in.nb; ++b)
+        if (cr.r[b] < cr.maxr[b]) capped = false;
+      if (capped || cr.refinements >= cr.max_refine) {
+        cr.status = 7;  // TTC_NOT_CONVERGED
         cr.state = ST_DONE;
-      } else if (cr.eps == 0.0 || err <= cr.eps) {
-        cr.status = 0;
-        cr.state = ST_DONE;
+        sm.flag = 0;
       } else {
-        sm.flag = 1;  // refine
+        cr.tau = cr.tau / 10.0;
+        cr.refinements += 1;
+        cr.state = ST_SCREEN;
+        // the mixed forms certified their bests only against the old
+        // threshold: they screen again
+        sm.flag = in.prec == P_FP64 ? 1 : 0;
       }
     }
     __syncthreads();
     if (!sm.flag) return;
-    // tau /= 10 until a bond adds, the caps are hit or the refinements run out
-    for (;;) {
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        bool capped = true;
-        for (int b = 0; b < in.nb; ++b)
-          if (cr.r[b] < cr.maxr[b]) capped = false;
-        if (capped || cr.refinements >= cr.max_refine) {
-          cr.status = 7;  // TTC_NOT_CONVERGED
-          cr.state = ST_DONE;
-          sm.flag = 0;
-        } else {
-          cr.tau = cr.tau / 10.0;
-          cr.refinements += 1;
-          sm.flag = 1;
-        }
-      }
-      __syncthreads();
-      if (!sm.flag) return;
-      const int n = decide_and_append(in, cr, sm);
-      if (n != 0) return;
+    // FP64: the cached bests are exact, decide again at the new threshold
+    int nadd = 0;
+    for (int b = 0; b < in.nb; ++b) {
+      finalize_bond(in, cr, b, sm);
+      nadd += cr.add[b];
+    }
+    if (nadd > 0 || cr.state == ST_DONE) return;
+  }
+}
+
+// decide work items: (instance, bond) for screened instances, (instance, -1)
+// for instances waiting for their verification; CTA g takes items g, g + G, ..
+template <class F>
+__device__ void for_decide_items(const RunArgs &ra, bool second, F &&f) {
+  int64_t j = 0;
+  for (int ii = 0; ii < ra.count; ++ii) {
+    const InstDev &in = *ra.insts[ii];
+    const Ctrl &cr = *in.ctrl;
+    const int st = *(volatile const int32_t *)&cr.state;
+    if (st == ST_DONE) continue;
+    if (!second && st == ST_VERIFY) {
+      if (j++ % gridDim.x == blockIdx.x) f(ii, -1);
+      continue;
+    }
+    if (!*(volatile const int32_t *)&cr.screened) continue;
+    for (int b = 0; b < in.nb; ++b) {
+      if (second && !*(volatile const int32_t *)&cr.pending[b]) continue;
+      if (j++ % gridDim.x == blockIdx.x) f(ii, b);
     }
   }
-  // SCREEN / UPDATE: merge the tile candidates of every bond
-  int64_t entries = 0, fmas = 0;
-  for (int b = 0; b < in.nb; ++b) {
-    const TileGeo g = tile_geo(in, cr, cr.r, b);
-    const int64_t nt = g.nrt * g.nct;
-    entries += g.rows * g.cols;
-    fmas += g.rows * g.cols * cr.r[b];
-    KeyBest best{0ull, LLONG_MAX, -1, -1};
-    const Cand *cand = in.cand + in.bond[b].cand_base;
-    for (int64_t t = threadIdx.x; t < nt; t += NT) {
-      KeyBest o{cand[t].key, cand[t].lin, cand[t].row, cand[t].col};
+}
+
+__device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
+  for_decide_items(ra, false, [&](int ii, int b) {
+    const InstDev &in = *ra.insts[ii];
+    Ctrl &cr = *in.ctrl;
+    if (b < 0) {
+      verify_instance(in, cr, sm.d);
+    } else if (in.prec == P_FP64) {
+      merge_bond_fp64(in, cr, b, sm.d);
+      finalize_bond(in, cr, b, sm.d);
+    } else {
+      merge_bond_mixed(in, cr, b, sm.d);
+    }
+  });
+}
+
+// mixed forms, part 2: the FP64 results of the refined tiles join the
+// re-scored candidates; the best is the FP64 argmax of the screen.
+__device__ void phase_decide2(const RunArgs &ra, PhaseSmem &sm) {
+  for_decide_items(ra, true, [&](int ii, int b) {
+    const InstDev &in = *ra.insts[ii];
+    Ctrl &cr = *in.ctrl;
+    DecideSmem &d = sm.d;
+    const int32_t cnt = cr.nrefine_bond[b];
+    const Cand *rc = in.refine_cand + in.bond[b].cand_base;
+    KeyBest best{cr.best_key[b], cr.best_lin[b], cr.best_row[b], cr.best_col[b]};
+    for (int32_t t = threadIdx.x; t < cnt; t += NT) {
+      KeyBest o{rc[t].key, rc[t].lin, rc[t].row, rc[t].col};
       kb_take(best, o);
     }
-    best = block_best(best, sm.rk, sm.rl, sm.rr, sm.rc);
+    best = block_best(best, d.rk, d.rl, d.rr, d.rc);
     if (threadIdx.x == 0) {
       cr.best_key[b] = best.key;
       cr.best_lin[b] = best.lin;
       cr.best_row[b] = best.row;
       cr.best_col[b] = best.col;
+      cr.pending[b] = 0;
     }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    cr.sweeps += 1;
-    cr.entries += entries;
-    cr.screen_fmas += fmas;
-    sm.flag = 1;
-    for (int b = 0; b < in.nb; ++b)
-      if (cr.best_key[b] > KEY_INF || cr.best_row[b] < 0) sm.flag = 0;
-    if (!sm.flag) {
-      cr.status = 4;
-      cr.state = ST_DONE;
-    }
-  }
-  __syncthreads();
-  if (!sm.flag) return;
-  const int n = decide_and_append(in, cr, sm);
-  if (n == 0 && threadIdx.x == 0) cr.state = ST_VERIFY;
-  __syncthreads();
-}
-
-__device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
-  for (int ii = blockIdx.x; ii < ra.count; ii += gridDim.x) decide_instance(ra, ii, sm.d);
+    __syncthreads();
+    finalize_bond(in, cr, b, d);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -580,6 +964,26 @@ __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
 //   A: eq. aca_approx_T_sub on the sweep-start rows           rows_old items
 //   B: new row z of R on the sweep-start columns              cols_old items
 //   D: new columns of R for the new suffix                    r_new * n_{b+1}
+// stores into T / R keep the FP32 (hi, lo) shadows of the mixed forms
+__device__ __forceinline__ void putT(const InstDev &in, const BondDev &B, int64_t o, double v) {
+  B.T[o] = v;
+  if (in.prec != P_FP64) {
+    float hi, lo;
+    split2(v, hi, lo);
+    B.Thi[o] = hi;
+    B.Tlo[o] = lo;
+  }
+}
+__device__ __forceinline__ void putR(const InstDev &in, const BondDev &B, int64_t o, double v) {
+  B.R[o] = v;
+  if (in.prec != P_FP64) {
+    float hi, lo;
+    split2(v, hi, lo);
+    B.Rhi[o] = hi;
+    B.Rlo[o] = lo;
+  }
+}
+
 __device__ void replay_row(const InstDev &in, int b, int64_t a, int nz) {
   const BondDev &B = in.bond[b];
   double Tr[RCAP];
@@ -592,7 +996,7 @@ __device__ void replay_row(const InstDev &in, int b, int64_t a, int nz) {
     for (int t = 0; t < z; ++t) Tr[t] = __fma_rn(w, hp[t], Tr[t]);
     Tr[z] = -w;
   }
-  for (int t = 0; t < nz; ++t) B.T[(int64_t)t * B.ldT + a] = Tr[t];
+  for (int t = 0; t < nz; ++t) putT(in, B, (int64_t)t * B.ldT + a, Tr[t]);
 }
 
 __device__ void update_row(const InstDev &in, int b, int64_t a, int z) {
@@ -606,8 +1010,8 @@ __device__ void update_row(const InstDev &in, int b, int64_t a, int z) {
   for (int t = 0; t < z; ++t) acc = __fma_rn(T[t * ld], hc[t], acc);
   const double s = __dsub_rn(acc, sb_entry(in, b, a, B.pcol[z]));
   const double w = __dmul_rn(B.delta[z], s);
-  for (int t = 0; t < z; ++t) T[t * ld] = __fma_rn(w, hp[t], T[t * ld]);
-  T[(int64_t)z * ld] = -w;
+  for (int t = 0; t < z; ++t) putT(in, B, a + t * ld, __fma_rn(w, hp[t], T[t * ld]));
+  putT(in, B, a + (int64_t)z * ld, -w);
 }
 
 // error of one sample: X(i) - X~(i), X~ = G_1(i_1) ... G_d(i_d) from T and R
@@ -651,13 +1055,21 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
     const InstDev &in = *ra.insts[ii];
     const Ctrl &cr = *in.ctrl;
     const int st = *(volatile const int32_t *)&cr.state;
-    if (st == ST_UPDATE) {
-      int32_t ro[TTC_MAXD], rn[TTC_MAXD], ad[TTC_MAXD];
-      for (int b = 0; b < in.nb; ++b) {
-        ro[b] = cr.r_old[b];
-        rn[b] = cr.r[b];
-        ad[b] = cr.add[b];
-      }
+    if (st == ST_DONE) continue;
+    // the work follows from the decisions (every CTA reads the same flags;
+    // the state word is rewritten by the owner CTA during this phase)
+    int32_t ro[TTC_MAXD], rn[TTC_MAXD], ad[TTC_MAXD];
+    int nadd = 0;
+    for (int b = 0; b < in.nb; ++b) {
+      ad[b] = *(volatile const int32_t *)&cr.add[b];
+      rn[b] = *(volatile const int32_t *)&cr.r[b];
+      ro[b] = rn[b] - ad[b];
+      nadd += ad[b];
+    }
+    const bool screened = *(volatile const int32_t *)&cr.screened != 0;
+    if (nadd == 0 && screened && blockIdx.x == ii % gridDim.x && threadIdx.x == 0)
+      in.ctrl->state = ST_VERIFY;
+    if (nadd > 0) {
       // C first: the replays are the longest items
       for (int b = 1; b < in.nb; ++b) {
         if (!ad[b - 1]) continue;
@@ -677,7 +1089,7 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
           base += rows;
           const int64_t as = B.prow[z];
           for (int64_t x = first_item(base, gt, NTOT); x < base + cols; x += NTOT)
-            B.R[(int64_t)z * B.ldR + (x - base)] = sb_entry(in, b, as, x - base);
+            putR(in, B, (int64_t)z * B.ldR + (x - base), sb_entry(in, b, as, x - base));
           base += cols;
         }
         if (b < in.nb - 1 && ad[b + 1]) {
@@ -687,12 +1099,12 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
           for (int64_t x = first_item(base, gt, NTOT); x < base + nit; x += NTOT) {
             const int64_t l = x - base, t = l / nb1, jj = l - t * nb1;
             const int64_t c = q * nb1 + jj;
-            B.R[t * B.ldR + c] = sb_entry(in, b, B.prow[t], c);
+            putR(in, B, t * B.ldR + c, sb_entry(in, b, B.prow[t], c));
           }
           base += nit;
         }
       }
-    } else if (st == ST_VERIFY) {
+    } else if (screened) {
       double part = 0.0;
       const int64_t ns = in.nsamples;
       for (int64_t x = first_item(base, gt, NTOT); x < base + ns; x += NTOT) {
@@ -815,8 +1227,8 @@ __device__ void phase_init2(const RunArgs &ra, PhaseSmem &sm) {
         B.prow[0] = st[b];
         B.pcol[0] = st[b + 1];
         cr.r[b] = 1;
-        cr.r_old[b] = 0;
-        cr.add[b] = 1;
+        cr.r_old[b] = 1;
+        cr.add[b] = 0;
       }
       if (cr.state != ST_DONE) {
         // the pivot entry of every superblock is X(start)
@@ -851,12 +1263,44 @@ __device__ void phase_init3(const RunArgs &ra, PhaseSmem &sm) {
       for (int64_t x = first_item(base, gt, NTOT); x < base + rows; x += NTOT) {
         const int64_t a = x - base;
         const double s = __dsub_rn(0.0, sb_entry(in, b, a, c0));
-        B.T[a] = -__dmul_rn(delta, s);
+        putT(in, B, a, -__dmul_rn(delta, s));
       }
       base += rows;
       for (int64_t x = first_item(base, gt, NTOT); x < base + cols; x += NTOT)
-        B.R[x - base] = sb_entry(in, b, a0, x - base);
+        putR(in, B, x - base, sb_entry(in, b, a0, x - base));
       base += cols;
+    }
+  }
+}
+
+// refine (mixed forms): FP64 screen of the queued tiles
+__device__ void phase_refine(const RunArgs &ra, PhaseSmem &sm) {
+  const int64_t G = gridDim.x;
+  int64_t base = 0;
+  for (int ii = 0; ii < ra.count; ++ii) {
+    const InstDev &in = *ra.insts[ii];
+    const Ctrl &cr = *in.ctrl;
+    if (*(volatile const int32_t *)&cr.state == ST_DONE) continue;
+    if (!*(volatile const int32_t *)&cr.screened) continue;
+    int32_t r[TTC_MAXD];
+    for (int b = 0; b < in.nb; ++b) r[b] = *(volatile const int32_t *)&cr.r[b];
+    for (int b = 0; b < in.nb; ++b) {
+      if (!*(volatile const int32_t *)&cr.pending[b]) continue;
+      const int64_t cnt = *(volatile const int32_t *)&cr.nrefine_bond[b];
+      const int32_t *list = in.refine_list + 2 * in.bond[b].cand_base;
+      Cand *out = in.refine_cand + in.bond[b].cand_base;
+      const TileGeo g = tile_geo(in, cr, r, b);
+      for (int64_t t = base + ((blockIdx.x - base) % G + G) % G; t < base + cnt; t += G) {
+        const int64_t li = t - base;
+        const int64_t tile = list[2 * li + 1];
+        const int64_t tr = tile / g.nct, tc = tile - tr * g.nct;
+        int64_t r0, c0;
+        int nr, nc;
+        tile_rows(in, g, b, tr, r0, nr);
+        tile_cols(in, g, b, tc, c0, nc);
+        screen_tile_fp64(in, b, r[b], r0, nr, c0, nc, out + li, sm.s);
+      }
+      base += cnt;
     }
   }
 }
@@ -893,13 +1337,20 @@ struct PhaseClock {
   }
 };
 
-__device__ bool any_state(const RunArgs &ra, int st) {
+// some instance evaluates its sampled error in the coming update phase
+__device__ bool any_verify(const RunArgs &ra) {
   __shared__ int hit;
   __syncthreads();
   if (threadIdx.x == 0) {
     hit = 0;
-    for (int ii = 0; ii < ra.count; ++ii)
-      if (*(volatile const int32_t *)&ra.insts[ii]->ctrl->state == st) hit = 1;
+    for (int ii = 0; ii < ra.count; ++ii) {
+      const Ctrl &cr = *ra.insts[ii]->ctrl;
+      if (*(volatile const int32_t *)&cr.state == ST_DONE) continue;
+      if (!*(volatile const int32_t *)&cr.screened) continue;
+      int nadd = 0;
+      for (int b = 0; b < ra.insts[ii]->nb; ++b) nadd += *(volatile const int32_t *)&cr.add[b];
+      if (nadd == 0) hit = 1;
+    }
   }
   __syncthreads();
   return hit != 0;
@@ -928,7 +1379,15 @@ __global__ void __launch_bounds__(NT, 2) k_persistent(RunArgs ra) {
     phase_decide(ra, sm);
     if (!grid_barrier(ra, 4)) return;
     clk.lap(ra, T_DECIDE);
-    const bool verify = any_state(ra, ST_VERIFY);
+    if (ra.mixed) {
+      phase_refine(ra, sm);
+      if (!grid_barrier(ra, 7)) return;
+      clk.lap(ra, T_REFINE);
+      phase_decide2(ra, sm);
+      if (!grid_barrier(ra, 8)) return;
+      clk.lap(ra, T_DECIDE);
+    }
+    const bool verify = any_verify(ra);
     phase_update(ra, sm);
     if (!grid_barrier(ra, 5)) return;
     clk.lap(ra, verify ? T_VERIFY : T_UPDATE);
@@ -949,6 +1408,12 @@ __global__ void __launch_bounds__(NT, 2) k_screen(RunArgs ra) {
 }
 __global__ void __launch_bounds__(NT, 2) k_decide(RunArgs ra) {
   phase_decide(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
+}
+__global__ void __launch_bounds__(NT, 2) k_refine(RunArgs ra) {
+  phase_refine(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
+}
+__global__ void __launch_bounds__(NT, 2) k_decide2(RunArgs ra) {
+  phase_decide2(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
 __global__ void __launch_bounds__(NT, 2) k_update(RunArgs ra) {
   phase_update(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
@@ -1029,6 +1494,8 @@ cudaError_t launch_phase(int phase, const RunArgs &ra, int grid, cudaStream_t s)
     case PH_SCREEN: f = (const void *)k_screen; break;
     case PH_DECIDE: f = (const void *)k_decide; break;
     case PH_UPDATE: f = (const void *)k_update; break;
+    case PH_REFINE: f = (const void *)k_refine; break;
+    case PH_DECIDE2: f = (const void *)k_decide2; break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = prep(f);
