@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "time-to-eps TT cross (ms), 6D Hilbert n=64 eps=1e-8"
+METRIC = "time-to-eps TT cross (ms)"
 WORKLOAD = "hilbert6d_n64"
 THROTTLE_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
                  0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
@@ -121,7 +121,7 @@ def bench_reference(args, rank, world):
     from paper_2407_11290_gb300 import workloads
     if rank != 0:
         return
-    cfg = workloads.CONFIGS[WORKLOAD]
+    cfg = workloads.CONFIGS[args.workload]
     threads = os.cpu_count() or 1
     warm, _ = cpu_oracle_time(cfg, threads, reps=args.warmup)
     times, st = cpu_oracle_time(cfg, threads, reps=args.steps)
@@ -131,8 +131,9 @@ def bench_reference(args, rank, world):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (analytic tensor)",
-        "config": {"workload": WORKLOAD, "d": 6, "n": 64, "eps": cfg["eps"],
-                   "max_rank": cfg["max_rank"], "nsamples": cfg["nsamples"], "l2": "n/a (CPU)"},
+        "config": {"workload": args.workload, "d": len(cfg["n"]), "n": cfg["n"][0],
+                   "eps": cfg["eps"], "max_rank": cfg["max_rank"], "nsamples": cfg["nsamples"],
+                   "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": ms, "unit": "ms", "cores": threads, "kind": "oracle",
                          "sample": f"{args.steps} full runs of the workload"},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -149,10 +150,10 @@ def bench_gpu(args, rank, world, local):
     from paper_2407_11290_gb300 import ttcross, workloads
 
     torch.cuda.set_device(local)
-    cfg = workloads.CONFIGS[WORKLOAD]
+    cfg = workloads.CONFIGS[args.workload]
     stream = torch.cuda.Stream()
     tc = ttcross.TTCross(cfg["n"], cfg["gen"], max_rank=cfg["max_rank"], nsamples=cfg["nsamples"],
-                         precision=args.precision)
+                         precision=args.precision, host_loop=args.host_loop)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def one_step():
@@ -212,14 +213,16 @@ def bench_gpu(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else args.precision,
         "data": "synthetic (analytic tensor, never formed)",
-        "config": {"workload": WORKLOAD, "d": 6, "n": 64, "eps": cfg["eps"],
-                   "max_rank": cfg["max_rank"], "grid": cfg["grid"], "nsamples": cfg["nsamples"],
+        "config": {"workload": args.workload, "d": len(cfg["n"]), "n": cfg["n"][0],
+                   "eps": cfg["eps"], "max_rank": cfg["max_rank"], "grid": cfg["grid"],
+                   "nsamples": cfg["nsamples"],
                    "precision": args.precision, "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "min_ms": min(step_ms), "median_ms": statistics.median(step_ms),
         "entries_screened": st["entries_screened"],
         "entries_per_s": st["entries_screened"] * world / (ms * 1e-3),
         "sweeps": st["sweeps"], "ranks": [int(x) for x in tc.ranks()], "err": st["err"],
+        "tiles_refined": st["tiles_refined"], "phase_ms": st["phase_ms"],
         "status": ttcross.STATUS_NAMES.get(st["status"], st["status"]),
         "e2e": {"value": statistics.median(e2e), "unit": "ms", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(d2h)},
@@ -250,6 +253,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "split", "auto"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=["hilbert3d_n32", "hilbert6d_n64", "hilbert6d_n256", "maxwellian6d_n64"])
+    ap.add_argument("--host-loop", action="store_true",
+                    help="phases as separate launches (per-phase kernels for profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if world > 1:

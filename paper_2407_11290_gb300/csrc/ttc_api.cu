@@ -197,6 +197,7 @@ ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, 
       CU(launch_phase(PH_REFINE, ra, h0->grid, s));
       CU(launch_phase(PH_DECIDE2, ra, h0->grid, s));
     }
+    CU(launch_phase(PH_TABLES, ra, h0->grid, s));
     CU(launch_phase(PH_UPDATE, ra, h0->grid, s));
   }
   return fail(TTC_ERR_CUDA, "host-stepped run did not finish");
@@ -394,6 +395,28 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     }
     core_cap = std::max(core_cap, h->bond_cap[d - 2] * n[d - 1]);
     double *stage = cv.take<double>(core_cap);
+    // prefix / suffix tables of the error check: the longest prefix (suffix)
+    // with at most max(nsamples, 4096) index combinations and 128 MiB
+    int64_t tl = 0, trr = 0;
+    {
+      const int64_t lim = std::max<int64_t>(ns, 4096), bytes = (int64_t)128 << 20;
+      int64_t N = n[0];
+      for (int a = 2; a < d; ++a) {
+        N *= n[a - 1];
+        const int64_t c = N * h->bond_cap[a - 1];
+        if (N > lim || c * 8 > bytes) break;
+        tl = c;
+      }
+      N = n[d - 1];
+      for (int c = 2; c < d; ++c) {
+        N *= n[d - c];
+        const int64_t cc = N * h->bond_cap[d - c - 1];
+        if (N > lim || cc * 8 > bytes) break;
+        trr = cc;
+      }
+    }
+    double *tabL = cv.take<double>(tl);
+    double *tabR = cv.take<double>(trr);
     if (pass == 0) {
       h->pool_bytes = cv.off;
       cudaError_t e = cudaMalloc(&h->pool, h->pool_bytes);
@@ -422,6 +445,10 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
       I.ctrl = ctrl;
       h->core_stage = stage;
       h->core_stage_cap = core_cap;
+      I.tabL = tabL;
+      I.tabR = tabR;
+      I.tabL_cap = tl;
+      I.tabR_cap = trr;
     }
   }
   auto cleanup = [&](ttc_status s) {

@@ -86,6 +86,8 @@ struct InstDev {
   BondDev bond[TTC_MAXB];
   SetDev empty;                      // I_{<=0} / J_{>d}: one empty multi-index
   double *xs;                        // X at the error samples
+  double *tabL, *tabR;               // prefix / suffix contractions of the TT (error check)
+  int64_t tabL_cap, tabR_cap;        // their capacities (doubles)
   int64_t nsamples;                  // samples used (== prod n when exhaustive)
   int32_t exhaustive;
   uint64_t seed;

@@ -1014,38 +1014,211 @@ __device__ void update_row(const InstDev &in, int b, int64_t a, int z) {
   putT(in, B, a + (int64_t)z * ld, -w);
 }
 
-// error of one sample: X(i) - X~(i), X~ = G_1(i_1) ... G_d(i_d) from T and R
-__device__ double sample_residual(const InstDev &in, int64_t k) {
-  int32_t idx[TTC_MAXD];
-  sample_index(in, k, idx);
-  double v[RCAP], w[RCAP];
-  const Ctrl &cr = *in.ctrl;
-  const BondDev &B0 = in.bond[0];
-  int rl = cr.r[0];
-  for (int t = 0; t < rl; ++t) v[t] = B0.T[(int64_t)t * B0.ldT + idx[0]];
-  const int d = in.d;
-  for (int m = 1; m < d - 1; ++m) {
-    const BondDev &B = in.bond[m];
-    const int rr = cr.r[m];
-    const int64_t a0 = idx[m];
-    const int64_t nm = in.n[m];
-    for (int u = 0; u < rr; ++u) {
-      const double *col = B.T + (int64_t)u * B.ldT + a0;
-      double acc = 0.0;
-      for (int p = 0; p < rl; ++p) acc = __fma_rn(v[p], col[p * nm], acc);
-      w[u] = acc;
-    }
-    for (int u = 0; u < rr; ++u) v[u] = w[u];
-    rl = rr;
-  }
-  const BondDev &BL = in.bond[d - 2];
-  const double xt = chain(v, 1, BL.R + idx[d - 1], BL.ldR, rl);
-  return __dsub_rn(in.xs[k], xt);
-}
-
 __device__ __forceinline__ int64_t first_item(int64_t base, int64_t gt, int64_t NTOT) {
   return base + ((gt - base) % NTOT + NTOT) % NTOT;
 }
+
+// ---------------------------------------------------------------------------
+// sampled error (Sec. 5).  X~(i) = G_1(i_1) ... G_d(i_d), cores read from T
+// (core m < d: element (p, i, u) = T_m[u][p n_m + i]) and R (last core).
+// The leading pL and trailing pR cores are contracted once for every index
+// combination of their modes (tables tabL, tabR), so a sample pays only the
+// middle cores and one dot product.  (pL, pR) minimise
+//   NL * s_{pL-1} s_pL + NR * s_{d-pR} s_{d-pR+1} + ns * (middle + s_{d-pR})
+// within the table capacities; every CTA evaluates the same choice.
+
+// core size s_m (s_0 = s_d = 1, s_m = r_{m-1})
+__device__ __forceinline__ int64_t core_s(const InstDev &in, const int32_t *r, int m) {
+  return (m == 0 || m == in.d) ? 1 : r[m - 1];
+}
+
+__device__ void choose_split(const InstDev &in, const int32_t *r, int &pL, int &pR) {
+  const int d = in.d;
+  double best = 1e300;
+  pL = 1;
+  pR = 1;
+  double NL = 1.0;
+  for (int a = 1; a < d; ++a) {
+    NL *= (double)in.n[a - 1];
+    if (a >= 2 && NL * core_s(in, r, a) > (double)in.tabL_cap) break;
+    const double tl = a >= 2 ? NL * core_s(in, r, a - 1) * core_s(in, r, a) : 0.0;
+    double NR = 1.0;
+    for (int c = 1; a + c <= d; ++c) {
+      NR *= (double)in.n[d - c];
+      if (c >= 2 && NR * core_s(in, r, d - c) > (double)in.tabR_cap) break;
+      const double tr = c >= 2 ? NR * core_s(in, r, d - c) * core_s(in, r, d - c + 1) : 0.0;
+      double mid = (double)core_s(in, r, d - c);
+      for (int m = a; m < d - c; ++m) mid += (double)core_s(in, r, m) * core_s(in, r, m + 1);
+      const double cost = tl + tr + (double)in.nsamples * mid;
+      if (cost < best) {
+        best = cost;
+        pL = a;
+        pR = c;
+      }
+    }
+  }
+}
+
+// v (length s_m) <- v G_m(i) for a middle core 1 <= m <= d-2
+__device__ __forceinline__ int mul_core(const InstDev &in, const int32_t *r, int m, int64_t i,
+                                        double *v, double *w) {
+  const BondDev &B = in.bond[m];
+  const int rl = (int)core_s(in, r, m), rr = (int)core_s(in, r, m + 1);
+  const int64_t nm = in.n[m];
+  for (int u = 0; u < rr; ++u) {
+    const double *col = B.T + (int64_t)u * B.ldT + i;
+    double acc = 0.0;
+    for (int p = 0; p < rl; ++p) acc = __fma_rn(v[p], col[p * nm], acc);
+    w[u] = acc;
+  }
+  for (int u = 0; u < rr; ++u) v[u] = w[u];
+  return rr;
+}
+
+// w (length s_{m+1}) <- G_m(i) w for a core 1 <= m <= d-2 (right to left)
+__device__ __forceinline__ int mul_core_right(const InstDev &in, const int32_t *r, int m,
+                                              int64_t i, double *w, double *t) {
+  const BondDev &B = in.bond[m];
+  const int rl = (int)core_s(in, r, m), rr = (int)core_s(in, r, m + 1);
+  const int64_t nm = in.n[m];
+  for (int p = 0; p < rl; ++p) {
+    const double *row = B.T + (int64_t)p * nm + i;
+    double acc = 0.0;
+    for (int u = 0; u < rr; ++u) acc = __fma_rn(row[(int64_t)u * B.ldT], w[u], acc);
+    t[p] = acc;
+  }
+  for (int p = 0; p < rl; ++p) w[p] = t[p];
+  return rl;
+}
+
+constexpr int TAB_CHUNK = 8;  // last-mode indices per table work item
+
+// tables of the verifying instances: a work item is a prefix of pL-1 modes
+// (suffix of pR-1 modes) and a chunk of TAB_CHUNK values of the next mode
+__device__ void phase_tables(const RunArgs &ra) {
+  const int64_t NTOT = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t base = 0;
+  for (int ii = 0; ii < ra.count; ++ii) {
+    const InstDev &in = *ra.insts[ii];
+    const Ctrl &cr = *in.ctrl;
+    if (*(volatile const int32_t *)&cr.state == ST_DONE) continue;
+    if (!*(volatile const int32_t *)&cr.screened) continue;
+    int32_t r[TTC_MAXD];
+    int nadd = 0;
+    for (int b = 0; b < in.nb; ++b) {
+      r[b] = *(volatile const int32_t *)&cr.r[b];
+      nadd += *(volatile const int32_t *)&cr.add[b];
+    }
+    if (nadd) continue;
+    int pL, pR;
+    choose_split(in, r, pL, pR);
+    const int d = in.d;
+    double v[RCAP], w[RCAP];
+    if (pL >= 2) {
+      int64_t np = 1;
+      for (int m = 0; m < pL - 1; ++m) np *= in.n[m];
+      const int64_t nl = in.n[pL - 1], nch = (nl + TAB_CHUNK - 1) / TAB_CHUNK;
+      const int64_t sl = core_s(in, r, pL);
+      const int64_t items = np * nch;
+      for (int64_t x = first_item(base, gt, NTOT); x < base + items; x += NTOT) {
+        const int64_t pre = (x - base) / nch, ch = (x - base) - pre * nch;
+        int64_t l = pre;
+        int32_t idx[TTC_MAXD];
+        for (int m = 0; m < pL - 1; ++m) {
+          idx[m] = (int32_t)(l % in.n[m]);
+          l /= in.n[m];
+        }
+        const BondDev &B0 = in.bond[0];
+        int len = (int)core_s(in, r, 1);
+        for (int t = 0; t < len; ++t) v[t] = B0.T[(int64_t)t * B0.ldT + idx[0]];
+        for (int m = 1; m < pL - 1; ++m) len = mul_core(in, r, m, idx[m], v, w);
+        // last mode of the prefix: core pL-1 (a middle core, pL-1 <= d-2)
+        const BondDev &B = in.bond[pL - 1];
+        for (int64_t i = ch * TAB_CHUNK; i < min(nl, (ch + 1) * TAB_CHUNK); ++i) {
+          double *out = in.tabL + (pre + i * np) * sl;
+          for (int u = 0; u < sl; ++u) {
+            const double *col = B.T + (int64_t)u * B.ldT + i;
+            double acc = 0.0;
+            for (int p = 0; p < len; ++p) acc = __fma_rn(v[p], col[p * nl], acc);
+            out[u] = acc;
+          }
+        }
+      }
+      base += items;
+    }
+    if (pR >= 2) {
+      int64_t np = 1;
+      for (int m = d - pR + 1; m < d; ++m) np *= in.n[m];
+      const int mf = d - pR;  // first mode of the suffix
+      const int64_t nf = in.n[mf], nch = (nf + TAB_CHUNK - 1) / TAB_CHUNK;
+      const int64_t sr = core_s(in, r, mf);
+      const int64_t items = np * nch;
+      for (int64_t x = first_item(base, gt, NTOT); x < base + items; x += NTOT) {
+        const int64_t suf = (x - base) / nch, ch = (x - base) - suf * nch;
+        int64_t l = suf;
+        int32_t idx[TTC_MAXD];
+        for (int m = mf + 1; m < d; ++m) {
+          idx[m] = (int32_t)(l % in.n[m]);
+          l /= in.n[m];
+        }
+        const BondDev &BL = in.bond[d - 2];
+        int len = (int)core_s(in, r, d - 1);
+        for (int t = 0; t < len; ++t) w[t] = BL.R[(int64_t)t * BL.ldR + idx[d - 1]];
+        for (int m = d - 2; m > mf; --m) len = mul_core_right(in, r, m, idx[m], w, v);
+        const BondDev &B = in.bond[mf];
+        for (int64_t i = ch * TAB_CHUNK; i < min(nf, (ch + 1) * TAB_CHUNK); ++i) {
+          double *out = in.tabR + (i + nf * suf) * sr;
+          for (int p = 0; p < sr; ++p) {
+            const double *row = B.T + (int64_t)p * nf + i;
+            double acc = 0.0;
+            for (int u = 0; u < len; ++u) acc = __fma_rn(row[(int64_t)u * B.ldT], w[u], acc);
+            out[p] = acc;
+          }
+        }
+      }
+      base += items;
+    }
+  }
+}
+
+// error of one sample: X(i) - X~(i), using the tables of (pL, pR)
+__device__ double sample_residual(const InstDev &in, const int32_t *r, int pL, int pR, int64_t k) {
+  int32_t idx[TTC_MAXD];
+  sample_index(in, k, idx);
+  double v[RCAP], w[RCAP];
+  const int d = in.d;
+  int len;
+  if (pL >= 2) {
+    int64_t e = 0, st = 1;
+    for (int m = 0; m < pL; ++m) {
+      e += idx[m] * st;
+      st *= in.n[m];
+    }
+    len = (int)core_s(in, r, pL);
+    const double *src = in.tabL + e * len;
+    for (int t = 0; t < len; ++t) v[t] = src[t];
+  } else {
+    const BondDev &B0 = in.bond[0];
+    len = (int)core_s(in, r, 1);
+    for (int t = 0; t < len; ++t) v[t] = B0.T[(int64_t)t * B0.ldT + idx[0]];
+  }
+  for (int m = pL; m < d - pR; ++m) len = mul_core(in, r, m, idx[m], v, w);
+  double xt;
+  if (pR >= 2) {
+    int64_t e = 0, st = 1;
+    for (int m = d - pR; m < d; ++m) {
+      e += idx[m] * st;
+      st *= in.n[m];
+    }
+    xt = chain(v, 1, in.tabR + e * len, 1, len);
+  } else {
+    const BondDev &BL = in.bond[d - 2];
+    xt = chain(v, 1, BL.R + idx[d - 1], BL.ldR, len);
+  }
+  return __dsub_rn(in.xs[k], xt);
+}
+
 
 __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
   const int64_t NTOT = (int64_t)gridDim.x * NT;
@@ -1107,8 +1280,10 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
     } else if (screened) {
       double part = 0.0;
       const int64_t ns = in.nsamples;
+      int pL, pR;
+      choose_split(in, rn, pL, pR);
       for (int64_t x = first_item(base, gt, NTOT); x < base + ns; x += NTOT) {
-        const double e = sample_residual(in, x - base);
+        const double e = sample_residual(in, rn, pL, pR, x - base);
         part = __fma_rn(e, e, part);
       }
       base += ns;
@@ -1388,6 +1563,10 @@ __global__ void __launch_bounds__(NT, 2) k_persistent(RunArgs ra) {
       clk.lap(ra, T_DECIDE);
     }
     const bool verify = any_verify(ra);
+    if (verify) {
+      phase_tables(ra);
+      if (!grid_barrier(ra, 9)) return;
+    }
     phase_update(ra, sm);
     if (!grid_barrier(ra, 5)) return;
     clk.lap(ra, verify ? T_VERIFY : T_UPDATE);
@@ -1415,6 +1594,7 @@ __global__ void __launch_bounds__(NT, 2) k_refine(RunArgs ra) {
 __global__ void __launch_bounds__(NT, 2) k_decide2(RunArgs ra) {
   phase_decide2(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
+__global__ void __launch_bounds__(NT, 2) k_tables(RunArgs ra) { phase_tables(ra); }
 __global__ void __launch_bounds__(NT, 2) k_update(RunArgs ra) {
   phase_update(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
@@ -1496,6 +1676,7 @@ cudaError_t launch_phase(int phase, const RunArgs &ra, int grid, cudaStream_t s)
     case PH_UPDATE: f = (const void *)k_update; break;
     case PH_REFINE: f = (const void *)k_refine; break;
     case PH_DECIDE2: f = (const void *)k_decide2; break;
+    case PH_TABLES: f = (const void *)k_tables; break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = prep(f);
