@@ -98,7 +98,9 @@ ttc_status ensure_cands(ttc_handle *h, const int32_t *grid) {
   int64_t need[TTC_MAXB], total = 0;
   bool grow = false;
   for (int b = 0; b < h->nb; ++b) {
-    need[b] = cand_need(h, b, grid);
+    // 64 x 64 tiles at the rank caps, and room for the 32 x 32 tiles the
+    // kernels switch to when a sweep has fewer than two waves of tiles
+    need[b] = std::max<int64_t>(cand_need(h, b, grid), 8192);
     if (need[b] > h->bond_cand_cap[b]) grow = true;
   }
   if (!grow && h->cand) return TTC_OK;

@@ -74,6 +74,10 @@ union __align__(16) PhaseSmem {
   double red[NT / 32];
 };
 
+// sampled-error split (defined with the error evaluation below)
+__device__ void choose_split(const InstDev &in, const int32_t *r, int &pL, int &pR);
+__device__ double split_cost(const InstDev &in, const int32_t *r, int pL, int pR);
+
 // ---------------------------------------------------------------------------
 // reductions
 
@@ -171,6 +175,7 @@ struct TileGeo {
   int64_t rows, cols;
   int32_t pr, pc;          // pieces (0 = none)
   int64_t rtpb, ctpb;      // tiles per block of n_b rows / n_{b+1} columns
+  int32_t te;              // tile edge (64, or 32 for small sweeps)
 };
 
 __device__ __forceinline__ int64_t piece_tiles(int64_t n, int32_t C, int64_t T) {
@@ -198,8 +203,9 @@ __device__ __forceinline__ void piece_locate(int64_t n, int32_t C, int64_t T, in
   len = 0;
 }
 
-__device__ TileGeo tile_geo(const InstDev &in, const Ctrl &cr, const int32_t *r, int b) {
+__device__ TileGeo tile_geo_e(const InstDev &in, const Ctrl &cr, const int32_t *r, int b, int te) {
   TileGeo g;
+  g.te = te;
   g.rows = rows_of(in, r, b);
   g.cols = cols_of(in, r, b);
   g.pr = cr.grid[b];
@@ -207,20 +213,42 @@ __device__ TileGeo tile_geo(const InstDev &in, const Ctrl &cr, const int32_t *r,
   const int64_t nrb = b == 0 ? 1 : r[b - 1];
   const int64_t ncb = b == in.nb - 1 ? 1 : r[b + 1];
   if (g.pr > 0) {
-    g.rtpb = piece_tiles(in.n[b], g.pr, BM);
+    g.rtpb = piece_tiles(in.n[b], g.pr, te);
     g.nrt = nrb * g.rtpb;
   } else {
     g.rtpb = 0;
-    g.nrt = (g.rows + BM - 1) / BM;
+    g.nrt = (g.rows + te - 1) / te;
   }
   if (g.pc > 0) {
-    g.ctpb = piece_tiles(in.n[b + 1], g.pc, BN);
+    g.ctpb = piece_tiles(in.n[b + 1], g.pc, te);
     g.nct = ncb * g.ctpb;
   } else {
     g.ctpb = 0;
-    g.nct = (g.cols + BN - 1) / BN;
+    g.nct = (g.cols + te - 1) / te;
   }
   return g;
+}
+
+// Tile autotuner: 64 x 64 tiles, unless the instance's superblocks give
+// fewer than two waves of them on this grid; then 32 x 32 tiles (four times
+// the CTAs busy in the early, small sweeps), if the candidate slots allow.
+// A pure function of the ranks and the grid, so every phase agrees.
+__device__ int tile_edge(const InstDev &in, const Ctrl &cr, const int32_t *r) {
+  int64_t t64 = 0;
+  for (int b = 0; b < in.nb; ++b) {
+    const TileGeo g = tile_geo_e(in, cr, r, b, 64);
+    t64 += g.nrt * g.nct;
+  }
+  if (t64 >= 2 * (int64_t)gridDim.x) return 64;
+  for (int b = 0; b < in.nb; ++b) {
+    const TileGeo g = tile_geo_e(in, cr, r, b, 32);
+    if (g.nrt * g.nct > in.bond[b].cand_cap) return 64;
+  }
+  return 32;
+}
+
+__device__ TileGeo tile_geo(const InstDev &in, const Ctrl &cr, const int32_t *r, int b) {
+  return tile_geo_e(in, cr, r, b, tile_edge(in, cr, r));
 }
 
 __device__ __forceinline__ void tile_rows(const InstDev &in, const TileGeo &g, int b, int64_t t,
@@ -228,12 +256,12 @@ __device__ __forceinline__ void tile_rows(const InstDev &in, const TileGeo &g, i
   if (g.pr > 0) {
     const int64_t p = t / g.rtpb;
     int64_t s, len;
-    piece_locate(in.n[b], g.pr, BM, t - p * g.rtpb, s, len);
+    piece_locate(in.n[b], g.pr, g.te, t - p * g.rtpb, s, len);
     r0 = p * in.n[b] + s;
     nr = (int)len;
   } else {
-    r0 = t * BM;
-    nr = (int)min((int64_t)BM, g.rows - r0);
+    r0 = t * g.te;
+    nr = (int)min((int64_t)g.te, g.rows - r0);
   }
 }
 
@@ -242,12 +270,12 @@ __device__ __forceinline__ void tile_cols(const InstDev &in, const TileGeo &g, i
   if (g.pc > 0) {
     const int64_t q = t / g.ctpb;
     int64_t s, len;
-    piece_locate(in.n[b + 1], g.pc, BN, t - q * g.ctpb, s, len);
+    piece_locate(in.n[b + 1], g.pc, g.te, t - q * g.ctpb, s, len);
     c0 = q * in.n[b + 1] + s;
     nc = (int)len;
   } else {
-    c0 = t * BN;
-    nc = (int)min((int64_t)BN, g.cols - c0);
+    c0 = t * g.te;
+    nc = (int)min((int64_t)g.te, g.cols - c0);
   }
 }
 
@@ -300,50 +328,51 @@ __device__ __forceinline__ double tile_entry(const InstDev &in, const ScreenSmem
   return gen_full(in, idx);
 }
 
-template <bool HIL>
+template <bool HIL, int TE>
 __device__ __noinline__ void screen_tile_fp64_t(const InstDev &in, int b, int K, int64_t r0, int nr,
                                                 int64_t c0, int nc, Cand *out, ScreenSmem &sm) {
+  constexpr int U = TE / 16;  // entries per thread and dimension
   const BondDev &B = in.bond[b];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int wl = b, wr = in.d - b - 2;
   __syncthreads();
   stage_meta(in, b, r0, nr, c0, nc, sm);
-  double acc[4][4];
+  double acc[U][U];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < U; ++v) acc[u][v] = 0.0;
   for (int t0 = 0; t0 < K; t0 += KC) {
     const int kc = min(KC, K - t0);
     __syncthreads();
-    for (int x = tid; x < kc * BM; x += NT) {
-      const int tt = x / BM, rr = x - tt * BM;
+    for (int x = tid; x < kc * TE; x += NT) {
+      const int tt = x / TE, rr = x - tt * TE;
       sm.op.d.Ts[tt][rr] = rr < nr ? B.T[(int64_t)(t0 + tt) * B.ldT + r0 + rr] : 0.0;
     }
-    for (int x = tid; x < kc * BN; x += NT) {
-      const int tt = x / BN, cc = x - tt * BN;
+    for (int x = tid; x < kc * TE; x += NT) {
+      const int tt = x / TE, cc = x - tt * TE;
       sm.op.d.Rs[tt][cc] = cc < nc ? B.R[(int64_t)(t0 + tt) * B.ldR + c0 + cc] : 0.0;
     }
     __syncthreads();
     for (int tt = 0; tt < kc; ++tt) {
-      double tv[4], rv[4];
+      double tv[U], rv[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) tv[u] = sm.op.d.Ts[tt][ty + 16 * u];
+      for (int u = 0; u < U; ++u) tv[u] = sm.op.d.Ts[tt][ty + 16 * u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) rv[v] = sm.op.d.Rs[tt][tx + 16 * v];
+      for (int v = 0; v < U; ++v) rv[v] = sm.op.d.Rs[tt][tx + 16 * v];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = __fma_rn(tv[u], rv[v], acc[u][v]);
+        for (int v = 0; v < U; ++v) acc[u][v] = __fma_rn(tv[u], rv[v], acc[u][v]);
     }
   }
   KeyBest best{0ull, LLONG_MAX, -1, -1};
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < U; ++u) {
     const int rr = ty + 16 * u;
     if (rr >= nr) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < U; ++v) {
       const int cc = tx + 16 * v;
       if (cc >= nc) continue;
       const double A = HIL ? in.hilb[sm.srow[rr] + sm.scol[cc]] : tile_entry(in, sm, wl, wr, rr, cc);
@@ -370,12 +399,19 @@ __device__ __noinline__ void screen_tile_fp64_t(const InstDev &in, int b, int K,
 }
 
 __device__ __forceinline__ void screen_tile_fp64(const InstDev &in, int b, int K, int64_t r0,
-                                                 int nr, int64_t c0, int nc, Cand *out,
+                                                 int nr, int64_t c0, int nc, int te, Cand *out,
                                                  ScreenSmem &sm) {
-  if (in.gen == 0)
-    screen_tile_fp64_t<true>(in, b, K, r0, nr, c0, nc, out, sm);
-  else
-    screen_tile_fp64_t<false>(in, b, K, r0, nr, c0, nc, out, sm);
+  if (te == 32) {
+    if (in.gen == 0)
+      screen_tile_fp64_t<true, 32>(in, b, K, r0, nr, c0, nc, out, sm);
+    else
+      screen_tile_fp64_t<false, 32>(in, b, K, r0, nr, c0, nc, out, sm);
+  } else {
+    if (in.gen == 0)
+      screen_tile_fp64_t<true, 64>(in, b, K, r0, nr, c0, nc, out, sm);
+    else
+      screen_tile_fp64_t<false, 64>(in, b, K, r0, nr, c0, nc, out, sm);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -389,10 +425,11 @@ __device__ __forceinline__ void screen_tile_fp64(const InstDev &in, int b, int K
 //     FP32 : 2 (K + 3) u (A + S Rm),  u = 2^-24
 //     split: 4 (3K + 8) u^2 (A + S Rm)
 //   plus 4u |E| for the last roundings.
-template <bool SPLIT, bool HIL>
+template <bool SPLIT, bool HIL, int TE>
 __device__ __noinline__ void screen_tile_mixed_t(const InstDev &in, int b, int K, int64_t r0,
                                                  int nr, int64_t c0, int nc, MCand *out,
                                                  ScreenSmem &sm) {
+  constexpr int U = TE / 16;  // entries per thread and dimension
   const BondDev &B = in.bond[b];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int wl = b, wr = in.d - b - 2;
@@ -400,25 +437,25 @@ __device__ __noinline__ void screen_tile_mixed_t(const InstDev &in, int b, int K
   stage_meta(in, b, r0, nr, c0, nc, sm);
   for (int x = tid; x < BM; x += NT) sm.rowS[x] = 0.f;
   for (int x = tid; x < BN; x += NT) sm.colR[x] = 0.f;
-  float sh[4][4], sl[4][4];
+  float sh[U][U], sl[U][U];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < U; ++v) {
       sh[u][v] = 0.f;
       sl[u][v] = 0.f;
     }
   for (int t0 = 0; t0 < K; t0 += KC) {
     const int kc = min(KC, K - t0);
     __syncthreads();
-    for (int x = tid; x < kc * BM; x += NT) {
-      const int tt = x / BM, rr = x - tt * BM;
+    for (int x = tid; x < kc * TE; x += NT) {
+      const int tt = x / TE, rr = x - tt * TE;
       const int64_t o = (int64_t)(t0 + tt) * B.ldT + r0 + rr;
       sm.op.f.Th[tt][rr] = rr < nr ? B.Thi[o] : 0.f;
       if (SPLIT) sm.op.f.Tl[tt][rr] = rr < nr ? B.Tlo[o] : 0.f;
     }
-    for (int x = tid; x < kc * BN; x += NT) {
-      const int tt = x / BN, cc = x - tt * BN;
+    for (int x = tid; x < kc * TE; x += NT) {
+      const int tt = x / TE, cc = x - tt * TE;
       const int64_t o = (int64_t)(t0 + tt) * B.ldR + c0 + cc;
       sm.op.f.Rh[tt][cc] = cc < nc ? B.Rhi[o] : 0.f;
       if (SPLIT) sm.op.f.Rl[tt][cc] = cc < nc ? B.Rlo[o] : 0.f;
@@ -435,29 +472,29 @@ __device__ __noinline__ void screen_tile_mixed_t(const InstDev &in, int b, int K
       sm.colR[c] = m;
     }
     for (int tt = 0; tt < kc; ++tt) {
-      float th[4], tl[4], rh[4], rl[4];
+      float th[U], tl[U], rh[U], rl[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < U; ++u) {
         th[u] = sm.op.f.Th[tt][ty + 16 * u];
         tl[u] = SPLIT ? sm.op.f.Tl[tt][ty + 16 * u] : 0.f;
       }
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
+      for (int v = 0; v < U; ++v) {
         rh[v] = sm.op.f.Rh[tt][tx + 16 * v];
         rl[v] = SPLIT ? sm.op.f.Rl[tt][tx + 16 * v] : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
+        for (int v = 0; v < U; ++v) {
           if (SPLIT) {
+            // th rh = p + pl exactly; the cross terms join pl by FMA
             const float p = __fmul_rn(th[u], rh[v]);
-            const float pl = __fmaf_rn(th[u], rh[v], -p);
-            const float c = __fmaf_rn(th[u], rl[v], __fmul_rn(tl[u], rh[v]));
+            const float pc = __fmaf_rn(tl[u], rh[v], __fmaf_rn(th[u], rl[v], __fmaf_rn(th[u], rh[v], -p)));
             const float s1 = __fadd_rn(sh[u][v], p);
             const float bb = __fsub_rn(s1, sh[u][v]);
             const float e = __fadd_rn(__fsub_rn(sh[u][v], __fsub_rn(s1, bb)), __fsub_rn(p, bb));
-            const float lo = __fadd_rn(sl[u][v], __fadd_rn(e, __fadd_rn(pl, c)));
+            const float lo = __fadd_rn(sl[u][v], __fadd_rn(e, pc));
             const float s2 = __fadd_rn(s1, lo);
             sl[u][v] = __fsub_rn(lo, __fsub_rn(s2, s1));
             sh[u][v] = s2;
@@ -472,11 +509,11 @@ __device__ __noinline__ void screen_tile_mixed_t(const InstDev &in, int b, int K
   int32_t brow = -1, bcol = -1;
   bool bad = false;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < U; ++u) {
     const int rr = ty + 16 * u;
     if (rr >= nr) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < U; ++v) {
       const int cc = tx + 16 * v;
       if (cc >= nc) continue;
       float ah, al;
@@ -558,12 +595,19 @@ __device__ __noinline__ void screen_tile_mixed_t(const InstDev &in, int b, int K
 
 template <bool SPLIT>
 __device__ __forceinline__ void screen_tile_mixed(const InstDev &in, int b, int K, int64_t r0,
-                                                  int nr, int64_t c0, int nc, MCand *out,
+                                                  int nr, int64_t c0, int nc, int te, MCand *out,
                                                   ScreenSmem &sm) {
-  if (in.gen == 0)
-    screen_tile_mixed_t<SPLIT, true>(in, b, K, r0, nr, c0, nc, out, sm);
-  else
-    screen_tile_mixed_t<SPLIT, false>(in, b, K, r0, nr, c0, nc, out, sm);
+  if (te == 32) {
+    if (in.gen == 0)
+      screen_tile_mixed_t<SPLIT, true, 32>(in, b, K, r0, nr, c0, nc, out, sm);
+    else
+      screen_tile_mixed_t<SPLIT, false, 32>(in, b, K, r0, nr, c0, nc, out, sm);
+  } else {
+    if (in.gen == 0)
+      screen_tile_mixed_t<SPLIT, true, 64>(in, b, K, r0, nr, c0, nc, out, sm);
+    else
+      screen_tile_mixed_t<SPLIT, false, 64>(in, b, K, r0, nr, c0, nc, out, sm);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -606,13 +650,14 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
         tile_rows(in, g, b, tr, r0, nr);
         tile_cols(in, g, b, tc, c0, nc);
         if (in.prec == P_SPLIT)
-          screen_tile_mixed<true>(in, b, r[b], r0, nr, c0, nc,
+          screen_tile_mixed<true>(in, b, r[b], r0, nr, c0, nc, g.te,
                                   in.mcand + in.bond[b].cand_base + lt, sm.s);
         else if (in.prec == P_FP32)
-          screen_tile_mixed<false>(in, b, r[b], r0, nr, c0, nc,
+          screen_tile_mixed<false>(in, b, r[b], r0, nr, c0, nc, g.te,
                                    in.mcand + in.bond[b].cand_base + lt, sm.s);
         else
-          screen_tile_fp64(in, b, r[b], r0, nr, c0, nc, in.cand + in.bond[b].cand_base + lt, sm.s);
+          screen_tile_fp64(in, b, r[b], r0, nr, c0, nc, g.te, in.cand + in.bond[b].cand_base + lt,
+                           sm.s);
       }
       base += nt;
     }
@@ -845,10 +890,9 @@ __device__ void verify_instance(const InstDev &in, Ctrl &cr, DecideSmem &sm) {
     cr.screened = 0;
     const double err = sqrt(num / cr.den);
     cr.err = err;
-    int64_t per = cr.r[0];
-    for (int b = 1; b < in.nb; ++b) per += (int64_t)cr.r[b - 1] * cr.r[b];
-    per += cr.r[in.nb - 1];
-    cr.error_fmas += per * in.nsamples;
+    int pL, pR;
+    choose_split(in, cr.r, pL, pR);
+    cr.error_fmas += (int64_t)split_cost(in, cr.r, pL, pR);
     for (int b = 0; b < in.nb; ++b) cr.add[b] = 0;
     sm.flag = 0;
     if (!isfinite(err)) {
@@ -1032,6 +1076,20 @@ __device__ __forceinline__ int64_t core_s(const InstDev &in, const int32_t *r, i
   return (m == 0 || m == in.d) ? 1 : r[m - 1];
 }
 
+// FMAs of the error evaluation with tables of pL / pR modes (the last table
+// level dominates; the chunked build adds its lower levels once per chunk)
+__device__ double split_cost(const InstDev &in, const int32_t *r, int pL, int pR) {
+  const int d = in.d;
+  double NL = 1.0, NR = 1.0;
+  for (int m = 0; m < pL; ++m) NL *= (double)in.n[m];
+  for (int m = d - pR; m < d; ++m) NR *= (double)in.n[m];
+  const double tl = pL >= 2 ? NL * core_s(in, r, pL - 1) * core_s(in, r, pL) : 0.0;
+  const double tr = pR >= 2 ? NR * core_s(in, r, d - pR) * core_s(in, r, d - pR + 1) : 0.0;
+  double mid = (double)core_s(in, r, d - pR);
+  for (int m = pL; m < d - pR; ++m) mid += (double)core_s(in, r, m) * core_s(in, r, m + 1);
+  return tl + tr + (double)in.nsamples * mid;
+}
+
 __device__ void choose_split(const InstDev &in, const int32_t *r, int &pL, int &pR) {
   const int d = in.d;
   double best = 1e300;
@@ -1041,15 +1099,11 @@ __device__ void choose_split(const InstDev &in, const int32_t *r, int &pL, int &
   for (int a = 1; a < d; ++a) {
     NL *= (double)in.n[a - 1];
     if (a >= 2 && NL * core_s(in, r, a) > (double)in.tabL_cap) break;
-    const double tl = a >= 2 ? NL * core_s(in, r, a - 1) * core_s(in, r, a) : 0.0;
     double NR = 1.0;
     for (int c = 1; a + c <= d; ++c) {
       NR *= (double)in.n[d - c];
       if (c >= 2 && NR * core_s(in, r, d - c) > (double)in.tabR_cap) break;
-      const double tr = c >= 2 ? NR * core_s(in, r, d - c) * core_s(in, r, d - c + 1) : 0.0;
-      double mid = (double)core_s(in, r, d - c);
-      for (int m = a; m < d - c; ++m) mid += (double)core_s(in, r, m) * core_s(in, r, m + 1);
-      const double cost = tl + tr + (double)in.nsamples * mid;
+      const double cost = split_cost(in, r, a, c);
       if (cost < best) {
         best = cost;
         pL = a;
@@ -1473,7 +1527,7 @@ __device__ void phase_refine(const RunArgs &ra, PhaseSmem &sm) {
         int nr, nc;
         tile_rows(in, g, b, tr, r0, nr);
         tile_cols(in, g, b, tc, c0, nc);
-        screen_tile_fp64(in, b, r[b], r0, nr, c0, nc, out + li, sm.s);
+        screen_tile_fp64(in, b, r[b], r0, nr, c0, nc, g.te, out + li, sm.s);
       }
       base += cnt;
     }
