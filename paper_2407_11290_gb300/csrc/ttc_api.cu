@@ -344,6 +344,19 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     }
   }
   const int64_t hlen = gen->kind == TTC_GEN_HILBERT ? hsum + 1 : 1;
+  int64_t ncombo = 1, ncos = 1;
+  if (gen->kind == TTC_GEN_MAXWELLIAN) {
+    ncos = 0;
+    for (int m = 0; m < gen->dx; ++m) {
+      I.mx_stride[m] = ncombo;
+      I.mx_off[m] = ncos;
+      ncombo *= n[m];
+      ncos += n[m];
+    }
+    if (ncombo > ((int64_t)1 << 27))
+      return fail(TTC_ERR_INVALID_ARG, "Maxwellian x grid too large (%lld index combinations)",
+                  (long long)ncombo);
+  }
   int64_t core_cap = 0;
   for (int pass = 0; pass < 2; ++pass) {
     Carver cv;
@@ -353,6 +366,9 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     InstDev *dinst = cv.take<InstDev>(1);
     InstDev **dlist = cv.take<InstDev *>(1);
     double *hilb = cv.take<double>(hlen);
+    double *mxc = cv.take<double>(gen->kind == TTC_GEN_MAXWELLIAN ? ncombo : 1);
+    double *mxn = cv.take<double>(gen->kind == TTC_GEN_MAXWELLIAN ? ncombo : 1);
+    double *mxcos = cv.take<double>(ncos);
     float *hilb_hi = cv.take<float>(hlen);
     float *hilb_lo = cv.take<float>(hlen);
     double *tt = cv.take<double>(tt_total);
@@ -433,6 +449,9 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
       h->d_inst = dinst;
       h->d_list = dlist;
       I.hilb = hilb;
+      I.mx_coef = mxc;
+      I.mx_nh = mxn;
+      I.mx_cos = mxcos;
       I.hilb_hi = hilb_hi;
       I.hilb_lo = hilb_lo;
       I.tt = tt;
@@ -487,6 +506,13 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     return cleanup(fail(TTC_ERR_CUDA, "copy of the instance list failed"));
   ttc_status s = ensure_cands(h, nullptr);
   if (s != TTC_OK) return cleanup(s);
+  if (gen->kind == TTC_GEN_MAXWELLIAN) {
+    if (launch_maxwellian_tables(h->d_inst, const_cast<double *>(I.mx_coef),
+                                 const_cast<double *>(I.mx_nh),
+                                 const_cast<double *>(I.mx_cos)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+      return cleanup(fail(TTC_ERR_CUDA, "Maxwellian tables failed"));
+  }
   if (cudaEventCreate(&h->ev0) == cudaSuccess && cudaEventCreate(&h->ev1) == cudaSuccess)
     h->events_ok = true;
   if (!bcaps.empty()) {

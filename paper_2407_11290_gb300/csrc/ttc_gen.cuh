@@ -53,6 +53,42 @@ __device__ __noinline__ double gen_maxwellian(const InstDev &in, const int32_t *
                    exp(-q / __dmul_rn(2.0, T)));
 }
 
+// The same function from the create-time tables: one exp per entry.
+__device__ __forceinline__ double gen_maxwellian_tab(const InstDev &in, const int32_t *idx) {
+  int64_t combo = 0;
+  for (int m = 0; m < in.dx; ++m) combo += (int64_t)idx[m] * in.mx_stride[m];
+  double q = 0.0;
+  for (int j = 0; j < in.dv; ++j) {
+    const int m = in.dx + j;
+    const int mu = (j + 1) % in.dx;
+    const double v = __dadd_rn(in.vmin, __dmul_rn(__dsub_rn(in.vmax, in.vmin), (double)idx[m]) /
+                                            (double)(in.n[m] - 1));
+    const double u = __dmul_rn(in.a_u, in.mx_cos[in.mx_off[mu] + idx[mu]]);
+    const double dvu = __dsub_rn(v, u);
+    q = __fma_rn(dvu, dvu, q);
+  }
+  return __dmul_rn(in.mx_coef[combo], exp(__dmul_rn(q, in.mx_nh[combo])));
+}
+
+// one entry of the tables: x-index combination `combo` (column-major)
+__device__ void maxwellian_table_entry(const InstDev &in, int64_t combo, double *coef,
+                                       double *nh) {
+  const double two_pi = 6.283185307179586476925286766559;
+  double prod_sin = 1.0, sum_x = 0.0;
+  int64_t l = combo;
+  for (int m = 0; m < in.dx; ++m) {
+    const int64_t i = l % in.n[m];
+    l /= in.n[m];
+    const double x = __dmul_rn(two_pi, (double)i) / (double)in.n[m];
+    prod_sin = __dmul_rn(prod_sin, sin(x));
+    sum_x = __dadd_rn(sum_x, x);
+  }
+  const double rho = __dadd_rn(1.0, __dmul_rn(in.a_rho, prod_sin));
+  const double T = __dadd_rn(1.0, __dmul_rn(in.a_T, cos(sum_x)));
+  *coef = rho / pow(__dmul_rn(two_pi, T), 0.5 * (double)in.dv);
+  *nh = -1.0 / __dmul_rn(2.0, T);
+}
+
 __device__ __forceinline__ double gen_full(const InstDev &in, const int32_t *idx) {
   if (in.gen == 0) {
     int s = 0;
@@ -60,7 +96,7 @@ __device__ __forceinline__ double gen_full(const InstDev &in, const int32_t *idx
     return in.hilb[s];
   }
   if (in.gen == 1) return gen_tt(in, idx);
-  return gen_maxwellian(in, idx);
+  return gen_maxwellian_tab(in, idx);
 }
 
 // Entry (a, c) of the superblock of bond b: rows a = p*n_b + i (p indexes

@@ -81,6 +81,12 @@ struct InstDev {
   int64_t core_off[TTC_MAXD + 1];
   int32_t dx, dv;
   double a_rho, a_u, a_T, vmin, vmax;
+  // Maxwellian tables (built on the device at create): for every combination
+  // of the x indices, coef = rho / (2 pi T)^{dv/2} and nh = -1 / (2 T); and
+  // cos x_m per x mode (mx_cos + mx_off[m])
+  const double *mx_coef, *mx_nh, *mx_cos;
+  int64_t mx_off[TTC_MAXD];
+  int64_t mx_stride[TTC_MAXD];
   int32_t prec;
   int32_t topk;
   BondDev bond[TTC_MAXB];

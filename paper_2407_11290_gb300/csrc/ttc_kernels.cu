@@ -230,16 +230,20 @@ __device__ TileGeo tile_geo_e(const InstDev &in, const Ctrl &cr, const int32_t *
 }
 
 // Tile autotuner: 64 x 64 tiles, unless the instance's superblocks give
-// fewer than two waves of them on this grid; then 32 x 32 tiles (four times
-// the CTAs busy in the early, small sweeps), if the candidate slots allow.
-// A pure function of the ranks and the grid, so every phase agrees.
+// under a quarter wave of them on this grid while the contraction is deep
+// (rank >= 24): then 32 x 32 tiles put four times the CTAs to work.  At
+// small ranks the per-tile overhead dominates and 64 x 64 stays faster
+// (measured on the 6D Hilbert workloads).  A pure function of the ranks and
+// the grid, so every phase agrees.
 __device__ int tile_edge(const InstDev &in, const Ctrl &cr, const int32_t *r) {
   int64_t t64 = 0;
+  int kmax = 0;
   for (int b = 0; b < in.nb; ++b) {
     const TileGeo g = tile_geo_e(in, cr, r, b, 64);
     t64 += g.nrt * g.nct;
+    kmax = max(kmax, (int)r[b]);
   }
-  if (t64 >= 2 * (int64_t)gridDim.x) return 64;
+  if (4 * t64 >= (int64_t)gridDim.x || kmax < 24) return 64;
   for (int b = 0; b < in.nb; ++b) {
     const TileGeo g = tile_geo_e(in, cr, r, b, 32);
     if (g.nrt * g.nct > in.bond[b].cand_cap) return 64;
@@ -1737,6 +1741,25 @@ cudaError_t launch_phase(int phase, const RunArgs &ra, int grid, cudaStream_t s)
   if (e != cudaSuccess) return e;
   void *args[] = {(void *)&ra};
   return cudaLaunchKernel(f, dim3(grid), dim3(NT), args, sizeof(PhaseSmem), s);
+}
+
+// Maxwellian tables of an instance (create time)
+__global__ void k_maxwellian_tables(const InstDev *inp, double *coef, double *nh, double *cosx) {
+  const InstDev &in = *inp;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t NTOT = (int64_t)gridDim.x * blockDim.x;
+  int64_t ncombo = 1;
+  for (int m = 0; m < in.dx; ++m) ncombo *= in.n[m];
+  for (int64_t c = gt; c < ncombo; c += NTOT) maxwellian_table_entry(in, c, coef + c, nh + c);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < in.dx; ++m)
+    for (int64_t i = gt; i < in.n[m]; i += NTOT)
+      cosx[in.mx_off[m] + i] = cos(__dmul_rn(two_pi, (double)i) / (double)in.n[m]);
+}
+
+cudaError_t launch_maxwellian_tables(const InstDev *d_inst, double *coef, double *nh, double *cosx) {
+  k_maxwellian_tables<<<152 * 4, 256>>>(d_inst, coef, nh, cosx);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_core(const InstDev *d_inst, int m, double *dst, cudaStream_t s) {

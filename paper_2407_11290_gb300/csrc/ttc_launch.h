@@ -16,6 +16,7 @@ cudaError_t persistent_occupancy(int *blocks_per_sm);
 cudaError_t launch_persistent(const RunArgs &ra, int grid, cudaStream_t s);
 cudaError_t launch_phase(int phase, const RunArgs &ra, int grid, cudaStream_t s);
 cudaError_t launch_core(const InstDev *d_inst, int m, double *dst, cudaStream_t s);
+cudaError_t launch_maxwellian_tables(const InstDev *d_inst, double *coef, double *nh, double *cosx);
 
 // tile geometry used to size the candidate buffer (host mirror of tile_geo)
 int64_t host_tiles(int64_t n_b, int64_t n_b1, int64_t rl, int64_t rr, int32_t pr, int32_t pc);
