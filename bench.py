@@ -245,6 +245,68 @@ def bench_gpu(args, rank, world, local):
     tc.close()
 
 
+def bench_batch(args, rank, world, local):
+    """The batch workload: independent Maxwellians of uneven d, n and
+    amplitudes, all in one persistent launch, against one launch per instance
+    in a loop.  A step is the whole batch to eps."""
+    import torch
+
+    from paper_2407_11290_gb300 import ttcross, workloads
+
+    torch.cuda.set_device(local)
+    ws = workloads.maxwellian_batch(args.batch_count)
+    stream = torch.cuda.Stream()
+    eps = 1e-6
+    make = lambda w: ttcross.TTCross(w["n"], w["gen"], max_rank=64, nsamples=10**6,  # noqa: E731
+                                     precision=args.precision)
+    batch = [make(w) for w in ws]
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def run_batch():
+        ttcross.run_batch(batch, eps, stream=stream)
+        for c in batch:
+            c.sync(allow=(ttcross.OK, ttcross.NOT_CONVERGED))
+
+    def run_loop():
+        for c in batch:
+            c.run(eps, stream=stream)
+            c.sync(allow=(ttcross.OK, ttcross.NOT_CONVERGED))
+
+    for _ in range(args.warmup):
+        run_batch()
+    times = {}
+    for name, fn in (("batched", run_batch), ("loop", run_loop)):
+        ms = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        times[name] = sum(ms) / len(ms)
+    stats = [c.stats() for c in batch]
+    conv = sum(1 for s in stats if s["status"] == ttcross.OK)
+    line = {
+        "metric": METRIC, "value": times["batched"], "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": times["batched"],
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else args.precision,
+        "data": "synthetic (analytic tensors, never formed)",
+        "config": {"workload": f"maxwellian_batch x{args.batch_count}", "eps": eps,
+                   "max_rank": 64, "nsamples": 10**6, "precision": args.precision,
+                   "l2": "working set of the batch exceeds L2"},
+        "loop_ms": times["loop"], "batched_speedup": times["loop"] / times["batched"],
+        "converged": conv, "not_converged": len(batch) - conv,
+        "entries_screened": sum(s["entries_screened"] for s in stats),
+        "gpu_launches": 1 + 2 * len(batch),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for c in batch:
+        c.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -254,7 +316,10 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "split", "auto"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=["hilbert3d_n32", "hilbert6d_n64", "hilbert6d_n256", "maxwellian6d_n64"])
+                    choices=["hilbert3d_n32", "hilbert6d_n64", "hilbert6d_n256", "maxwellian6d_n64",
+                             "maxwellian_batch"])
+    ap.add_argument("--batch-count", type=int, default=256,
+                    help="instances of the maxwellian_batch workload")
     ap.add_argument("--host-loop", action="store_true",
                     help="phases as separate launches (per-phase kernels for profiling)")
     args = ap.parse_args()
@@ -268,6 +333,8 @@ def main():
         dist.init_process_group(backend)
     if args.impl == "reference":
         bench_reference(args, rank, world)
+    elif args.workload == "maxwellian_batch":
+        bench_batch(args, rank, world, local)
     else:
         bench_gpu(args, rank, world, local)
     if world > 1:

@@ -251,9 +251,7 @@ __device__ int tile_edge(const InstDev &in, const Ctrl &cr, const int32_t *r) {
   return 32;
 }
 
-__device__ TileGeo tile_geo(const InstDev &in, const Ctrl &cr, const int32_t *r, int b) {
-  return tile_geo_e(in, cr, r, b, tile_edge(in, cr, r));
-}
+
 
 __device__ __forceinline__ void tile_rows(const InstDev &in, const TileGeo &g, int b, int64_t t,
                                           int64_t &r0, int &nr) {
@@ -299,7 +297,7 @@ __device__ void stage_meta(const InstDev &in, int b, int64_t r0, int nr, int64_t
   const int wl = b, wr = in.d - b - 2;
   for (int x = tid; x < BM; x += NT) {
     if (x < nr) {
-      const int64_t a = r0 + x, p = a / nb0, i = a - p * nb0;
+      const uint32_t a = (uint32_t)(r0 + x), p = a / (uint32_t)nb0, i = a - p * (uint32_t)nb0;
       sm.lrow[x] = L.lin[p] + i * in.stride[b];
       if (hil) {
         sm.srow[x] = L.sum[p] + (int)i;
@@ -311,7 +309,7 @@ __device__ void stage_meta(const InstDev &in, int b, int64_t r0, int nr, int64_t
   }
   for (int x = tid; x < BN; x += NT) {
     if (x < nc) {
-      const int64_t c = c0 + x, q = c / nb1, j = c - q * nb1;
+      const uint32_t c = (uint32_t)(c0 + x), q = c / (uint32_t)nb1, j = c - q * (uint32_t)nb1;
       sm.lcol[x] = j * in.stride[b + 1] + Rset.lin[q];
       if (hil) {
         sm.scol[x] = (int)j + Rset.sum[q];
@@ -627,12 +625,13 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
     if (st != ST_SCREEN) continue;
     int32_t r[TTC_MAXD];
     for (int b = 0; b < in.nb; ++b) r[b] = *(volatile const int32_t *)&cr.r[b];
+    const int te = tile_edge(in, cr, r);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       // bookkeeping of this screen, from the ranks it uses
       Ctrl &cw = *in.ctrl;
       int64_t entries = 0, fmas = 0;
       for (int b = 0; b < in.nb; ++b) {
-        const TileGeo g = tile_geo(in, cr, r, b);
+        const TileGeo g = tile_geo_e(in, cr, r, b, te);
         cw.ntiles[b] = (int32_t)(g.nrt * g.nct);
         entries += g.rows * g.cols;
         fmas += g.rows * g.cols * r[b];
@@ -643,7 +642,7 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
       cw.screened = 1;
     }
     for (int b = 0; b < in.nb; ++b) {
-      const TileGeo g = tile_geo(in, cr, r, b);
+      const TileGeo g = tile_geo_e(in, cr, r, b, te);
       const int64_t nt = g.nrt * g.nct;
       int64_t first = base + ((blockIdx.x - base) % G + G) % G;
       for (int64_t t = first; t < base + nt; t += G) {
@@ -1517,12 +1516,13 @@ __device__ void phase_refine(const RunArgs &ra, PhaseSmem &sm) {
     if (!*(volatile const int32_t *)&cr.screened) continue;
     int32_t r[TTC_MAXD];
     for (int b = 0; b < in.nb; ++b) r[b] = *(volatile const int32_t *)&cr.r[b];
+    const int te = tile_edge(in, cr, r);
     for (int b = 0; b < in.nb; ++b) {
       if (!*(volatile const int32_t *)&cr.pending[b]) continue;
       const int64_t cnt = *(volatile const int32_t *)&cr.nrefine_bond[b];
       const int32_t *list = in.refine_list + 2 * in.bond[b].cand_base;
       Cand *out = in.refine_cand + in.bond[b].cand_base;
-      const TileGeo g = tile_geo(in, cr, r, b);
+      const TileGeo g = tile_geo_e(in, cr, r, b, te);
       for (int64_t t = base + ((blockIdx.x - base) % G + G) % G; t < base + cnt; t += G) {
         const int64_t li = t - base;
         const int64_t tile = list[2 * li + 1];
