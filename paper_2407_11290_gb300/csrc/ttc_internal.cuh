@@ -60,6 +60,12 @@ struct Ctrl {
   int32_t best_row[TTC_MAXD], best_col[TTC_MAXD];
   double eps, tau, xrms, den, err;
   int64_t sweeps, entries, refinements, tiles_refined;
+  // tile schedule of the next screen (written by the instance's owner CTA
+  // whenever its ranks change, read by every CTA): tile edge, and per bond
+  // the superblock rows / columns and row / column tile counts
+  int32_t plan_te;
+  int32_t plan_rows[TTC_MAXD], plan_cols[TTC_MAXD];
+  int32_t plan_nrt[TTC_MAXD], plan_nct[TTC_MAXD];
   int32_t screened;          // screened in this sweep (set by the screen, cleared by decide)
   int32_t pad2;
   int32_t pending[TTC_MAXD]; // mixed forms: bond merged, waiting for the refinement

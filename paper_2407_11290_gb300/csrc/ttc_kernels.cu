@@ -170,60 +170,70 @@ __device__ bool grid_barrier(const RunArgs &ra, int where) {
 // (columns) are cut into BM (BN) chunks; with one, mode b (b+1) is split into
 // grid[b] (grid[b+1]) balanced pieces and no tile crosses a piece.
 
-struct TileGeo {
-  int64_t nrt, nct;        // row tiles, column tiles
-  int64_t rows, cols;
-  int32_t pr, pc;          // pieces (0 = none)
-  int64_t rtpb, ctpb;      // tiles per block of n_b rows / n_{b+1} columns
-  int32_t te;              // tile edge (64, or 32 for small sweeps)
+// Balanced split of n indices into C pieces: the first rem = n mod C pieces
+// hold q + 1 = n / C + 1 indices, the others q.  Tiles never cross a piece.
+struct Pieces {
+  int32_t q, rem, tq1, tq0, tpb;  // tiles per piece of size q+1 / q, tiles per block
 };
 
-__device__ __forceinline__ int64_t piece_tiles(int64_t n, int32_t C, int64_t T) {
-  int64_t s = 0;
-  for (int32_t k = 0; k < C; ++k) {
-    const int64_t lo = n * k / C, hi = n * (k + 1) / C;
-    s += (hi - lo + T - 1) / T;
-  }
-  return s;
+__device__ __forceinline__ Pieces make_pieces(int32_t n, int32_t C, int32_t te) {
+  Pieces P;
+  P.q = n / C;
+  P.rem = n - P.q * C;
+  P.tq1 = (P.q + 1 + te - 1) / te;
+  P.tq0 = (P.q + te - 1) / te;
+  P.tpb = P.rem * P.tq1 + (C - P.rem) * P.tq0;
+  return P;
 }
 
-__device__ __forceinline__ void piece_locate(int64_t n, int32_t C, int64_t T, int64_t t,
-                                             int64_t &start, int64_t &len) {
-  for (int32_t k = 0; k < C; ++k) {
-    const int64_t lo = n * k / C, hi = n * (k + 1) / C;
-    const int64_t nt = (hi - lo + T - 1) / T;
-    if (t < nt) {
-      start = lo + t * T;
-      len = min(T, hi - start);
-      return;
-    }
-    t -= nt;
+// tile t of one block: start within the block and length
+__device__ __forceinline__ void piece_tile(const Pieces &P, int32_t t, int32_t te, int32_t &start,
+                                           int32_t &len) {
+  int32_t k, tin, size;
+  if (t < P.rem * P.tq1) {
+    k = t / P.tq1;
+    tin = t - k * P.tq1;
+    size = P.q + 1;
+  } else {
+    const int32_t u = t - P.rem * P.tq1;
+    const int32_t kk = u / P.tq0;
+    k = P.rem + kk;
+    tin = u - kk * P.tq0;
+    size = P.q;
   }
-  start = 0;
-  len = 0;
+  start = k * P.q + min(k, P.rem) + tin * te;
+  len = min(te, size - tin * te);
 }
+
+// Tile geometry of bond b for edge te, from the ranks r (no subtensor grid:
+// rows / columns cut into te-chunks; grid: pieces of mode b / b+1 per block)
+struct TileGeo {
+  int32_t nrt, nct;        // row tiles, column tiles
+  int32_t rows, cols;
+  int32_t te;
+  int32_t pr, pc;          // pieces (0 = none)
+  Pieces P, Q;             // row / column pieces
+};
 
 __device__ TileGeo tile_geo_e(const InstDev &in, const Ctrl &cr, const int32_t *r, int b, int te) {
   TileGeo g;
   g.te = te;
-  g.rows = rows_of(in, r, b);
-  g.cols = cols_of(in, r, b);
+  g.rows = (int32_t)rows_of(in, r, b);
+  g.cols = (int32_t)cols_of(in, r, b);
   g.pr = cr.grid[b];
   g.pc = cr.grid[b + 1];
-  const int64_t nrb = b == 0 ? 1 : r[b - 1];
-  const int64_t ncb = b == in.nb - 1 ? 1 : r[b + 1];
+  const int32_t nrb = b == 0 ? 1 : r[b - 1];
+  const int32_t ncb = b == in.nb - 1 ? 1 : r[b + 1];
   if (g.pr > 0) {
-    g.rtpb = piece_tiles(in.n[b], g.pr, te);
-    g.nrt = nrb * g.rtpb;
+    g.P = make_pieces((int32_t)in.n[b], g.pr, te);
+    g.nrt = nrb * g.P.tpb;
   } else {
-    g.rtpb = 0;
     g.nrt = (g.rows + te - 1) / te;
   }
   if (g.pc > 0) {
-    g.ctpb = piece_tiles(in.n[b + 1], g.pc, te);
-    g.nct = ncb * g.ctpb;
+    g.Q = make_pieces((int32_t)in.n[b + 1], g.pc, te);
+    g.nct = ncb * g.Q.tpb;
   } else {
-    g.ctpb = 0;
     g.nct = (g.cols + te - 1) / te;
   }
   return g;
@@ -233,51 +243,76 @@ __device__ TileGeo tile_geo_e(const InstDev &in, const Ctrl &cr, const int32_t *
 // under a quarter wave of them on this grid while the contraction is deep
 // (rank >= 24): then 32 x 32 tiles put four times the CTAs to work.  At
 // small ranks the per-tile overhead dominates and 64 x 64 stays faster
-// (measured on the 6D Hilbert workloads).  A pure function of the ranks and
-// the grid, so every phase agrees.
-__device__ int tile_edge(const InstDev &in, const Ctrl &cr, const int32_t *r) {
+// (measured on the 6D Hilbert workloads).
+__device__ int tile_edge(const InstDev &in, const Ctrl &cr, const int32_t *r, int grid) {
   int64_t t64 = 0;
   int kmax = 0;
   for (int b = 0; b < in.nb; ++b) {
     const TileGeo g = tile_geo_e(in, cr, r, b, 64);
-    t64 += g.nrt * g.nct;
+    t64 += (int64_t)g.nrt * g.nct;
     kmax = max(kmax, (int)r[b]);
   }
-  if (4 * t64 >= (int64_t)gridDim.x || kmax < 24) return 64;
+  if (4 * t64 >= (int64_t)grid || kmax < 24) return 64;
   for (int b = 0; b < in.nb; ++b) {
     const TileGeo g = tile_geo_e(in, cr, r, b, 32);
-    if (g.nrt * g.nct > in.bond[b].cand_cap) return 64;
+    if ((int64_t)g.nrt * g.nct > in.bond[b].cand_cap) return 64;
   }
   return 32;
 }
 
-
-
-__device__ __forceinline__ void tile_rows(const InstDev &in, const TileGeo &g, int b, int64_t t,
-                                          int64_t &r0, int &nr) {
-  if (g.pr > 0) {
-    const int64_t p = t / g.rtpb;
-    int64_t s, len;
-    piece_locate(in.n[b], g.pr, g.te, t - p * g.rtpb, s, len);
-    r0 = p * in.n[b] + s;
-    nr = (int)len;
-  } else {
-    r0 = t * g.te;
-    nr = (int)min((int64_t)g.te, g.rows - r0);
+// the tile plan of the next screen at ranks r (owner CTA, one thread)
+__device__ void write_plan(const InstDev &in, Ctrl &cr, const int32_t *r, int grid) {
+  const int te = tile_edge(in, cr, r, grid);
+  cr.plan_te = te;
+  for (int b = 0; b < in.nb; ++b) {
+    const TileGeo g = tile_geo_e(in, cr, r, b, te);
+    cr.plan_rows[b] = g.rows;
+    cr.plan_cols[b] = g.cols;
+    cr.plan_nrt[b] = g.nrt;
+    cr.plan_nct[b] = g.nct;
   }
 }
 
-__device__ __forceinline__ void tile_cols(const InstDev &in, const TileGeo &g, int b, int64_t t,
+// geometry of bond b as planned (cheap: no tile counting)
+__device__ __forceinline__ TileGeo planned_geo(const InstDev &in, const Ctrl &cr, int b) {
+  TileGeo g;
+  g.te = *(volatile const int32_t *)&cr.plan_te;
+  g.rows = *(volatile const int32_t *)&cr.plan_rows[b];
+  g.cols = *(volatile const int32_t *)&cr.plan_cols[b];
+  g.nrt = *(volatile const int32_t *)&cr.plan_nrt[b];
+  g.nct = *(volatile const int32_t *)&cr.plan_nct[b];
+  g.pr = cr.grid[b];
+  g.pc = cr.grid[b + 1];
+  if (g.pr > 0) g.P = make_pieces((int32_t)in.n[b], g.pr, g.te);
+  if (g.pc > 0) g.Q = make_pieces((int32_t)in.n[b + 1], g.pc, g.te);
+  return g;
+}
+
+__device__ __forceinline__ void tile_rows(const InstDev &in, const TileGeo &g, int b, int32_t t,
+                                          int64_t &r0, int &nr) {
+  if (g.pr > 0) {
+    const int32_t p = t / g.P.tpb;
+    int32_t st, len;
+    piece_tile(g.P, t - p * g.P.tpb, g.te, st, len);
+    r0 = (int64_t)p * in.n[b] + st;
+    nr = len;
+  } else {
+    r0 = (int64_t)t * g.te;
+    nr = min(g.te, g.rows - t * g.te);
+  }
+}
+
+__device__ __forceinline__ void tile_cols(const InstDev &in, const TileGeo &g, int b, int32_t t,
                                           int64_t &c0, int &nc) {
   if (g.pc > 0) {
-    const int64_t q = t / g.ctpb;
-    int64_t s, len;
-    piece_locate(in.n[b + 1], g.pc, g.te, t - q * g.ctpb, s, len);
-    c0 = q * in.n[b + 1] + s;
-    nc = (int)len;
+    const int32_t q = t / g.Q.tpb;
+    int32_t st, len;
+    piece_tile(g.Q, t - q * g.Q.tpb, g.te, st, len);
+    c0 = (int64_t)q * in.n[b + 1] + st;
+    nc = len;
   } else {
-    c0 = t * g.te;
-    nc = (int)min((int64_t)g.te, g.cols - c0);
+    c0 = (int64_t)t * g.te;
+    nc = min(g.te, g.cols - t * g.te);
   }
 }
 
@@ -616,8 +651,9 @@ __device__ __forceinline__ void screen_tile_mixed(const InstDev &in, int b, int 
 // phase: screen.  Tiles of every (instance, bond) pair that needs a screen
 // are numbered consecutively; CTA g takes tiles g, g + G, ...
 __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
-  const int64_t G = gridDim.x;
+  const int32_t G = gridDim.x;
   int64_t base = 0;
+  int32_t boff = 0;  // base mod G
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = *ra.insts[ii];
     const Ctrl &cr = *in.ctrl;
@@ -625,16 +661,15 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
     if (st != ST_SCREEN) continue;
     int32_t r[TTC_MAXD];
     for (int b = 0; b < in.nb; ++b) r[b] = *(volatile const int32_t *)&cr.r[b];
-    const int te = tile_edge(in, cr, r);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      // bookkeeping of this screen, from the ranks it uses
+      // bookkeeping of this screen
       Ctrl &cw = *in.ctrl;
       int64_t entries = 0, fmas = 0;
       for (int b = 0; b < in.nb; ++b) {
-        const TileGeo g = tile_geo_e(in, cr, r, b, te);
-        cw.ntiles[b] = (int32_t)(g.nrt * g.nct);
-        entries += g.rows * g.cols;
-        fmas += g.rows * g.cols * r[b];
+        cw.ntiles[b] = cw.plan_nrt[b] * cw.plan_nct[b];
+        const int64_t e = (int64_t)cw.plan_rows[b] * cw.plan_cols[b];
+        entries += e;
+        fmas += e * r[b];
       }
       cw.sweeps += 1;
       cw.entries += entries;
@@ -642,12 +677,10 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
       cw.screened = 1;
     }
     for (int b = 0; b < in.nb; ++b) {
-      const TileGeo g = tile_geo_e(in, cr, r, b, te);
-      const int64_t nt = g.nrt * g.nct;
-      int64_t first = base + ((blockIdx.x - base) % G + G) % G;
-      for (int64_t t = first; t < base + nt; t += G) {
-        const int64_t lt = t - base;
-        const int64_t tr = lt / g.nct, tc = lt - tr * g.nct;
+      const TileGeo g = planned_geo(in, cr, b);
+      const int32_t nt = g.nrt * g.nct;
+      for (int32_t lt = ((int32_t)blockIdx.x - boff + G) % G; lt < nt; lt += G) {
+        const int32_t tr = lt / g.nct, tc = lt - tr * g.nct;
         int64_t r0, c0;
         int nr, nc;
         tile_rows(in, g, b, tr, r0, nr);
@@ -663,6 +696,7 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
                            sm.s);
       }
       base += nt;
+      boff = (int32_t)((boff + nt) % G);
     }
   }
 }
@@ -1061,7 +1095,13 @@ __device__ void update_row(const InstDev &in, int b, int64_t a, int z) {
   putT(in, B, a + (int64_t)z * ld, -w);
 }
 
+// first item >= base that thread gt of NTOT takes when items are dealt
+// round-robin (32-bit arithmetic while the counts allow)
 __device__ __forceinline__ int64_t first_item(int64_t base, int64_t gt, int64_t NTOT) {
+  if (base < ((int64_t)1 << 31) && NTOT < ((int64_t)1 << 31)) {
+    const int32_t n = (int32_t)NTOT;
+    return base + (((int32_t)gt - (int32_t)base % n) % n + n) % n;
+  }
   return base + ((gt - base) % NTOT + NTOT) % NTOT;
 }
 
@@ -1297,8 +1337,10 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
       nadd += ad[b];
     }
     const bool screened = *(volatile const int32_t *)&cr.screened != 0;
-    if (nadd == 0 && screened && blockIdx.x == ii % gridDim.x && threadIdx.x == 0)
-      in.ctrl->state = ST_VERIFY;
+    if (blockIdx.x == ii % gridDim.x && threadIdx.x == 0) {
+      if (nadd == 0 && screened) in.ctrl->state = ST_VERIFY;
+      if (nadd > 0) write_plan(in, *in.ctrl, rn, gridDim.x);  // next screen's tiles
+    }
     if (nadd > 0) {
       // C first: the replays are the longest items
       for (int b = 1; b < in.nb; ++b) {
@@ -1463,6 +1505,7 @@ __device__ void phase_init2(const RunArgs &ra, PhaseSmem &sm) {
         cr.add[b] = 0;
       }
       if (cr.state != ST_DONE) {
+        write_plan(in, cr, cr.r, gridDim.x);
         // the pivot entry of every superblock is X(start)
         const double delta = 1.0 / __dsub_rn(xs0, 0.0);
         if (!isfinite(delta)) {
@@ -1516,17 +1559,16 @@ __device__ void phase_refine(const RunArgs &ra, PhaseSmem &sm) {
     if (!*(volatile const int32_t *)&cr.screened) continue;
     int32_t r[TTC_MAXD];
     for (int b = 0; b < in.nb; ++b) r[b] = *(volatile const int32_t *)&cr.r[b];
-    const int te = tile_edge(in, cr, r);
     for (int b = 0; b < in.nb; ++b) {
       if (!*(volatile const int32_t *)&cr.pending[b]) continue;
       const int64_t cnt = *(volatile const int32_t *)&cr.nrefine_bond[b];
       const int32_t *list = in.refine_list + 2 * in.bond[b].cand_base;
       Cand *out = in.refine_cand + in.bond[b].cand_base;
-      const TileGeo g = tile_geo_e(in, cr, r, b, te);
+      const TileGeo g = planned_geo(in, cr, b);
       for (int64_t t = base + ((blockIdx.x - base) % G + G) % G; t < base + cnt; t += G) {
         const int64_t li = t - base;
-        const int64_t tile = list[2 * li + 1];
-        const int64_t tr = tile / g.nct, tc = tile - tr * g.nct;
+        const int32_t tile = list[2 * li + 1];
+        const int32_t tr = tile / g.nct, tc = tile - tr * g.nct;
         int64_t r0, c0;
         int nr, nc;
         tile_rows(in, g, b, tr, r0, nr);
@@ -1690,12 +1732,8 @@ __global__ void k_core(const InstDev *inp, int m, double *dst) {
 size_t phase_smem_bytes() { return sizeof(PhaseSmem); }
 
 static int64_t host_piece_tiles(int64_t n, int32_t C, int64_t T) {
-  int64_t s = 0;
-  for (int32_t k = 0; k < C; ++k) {
-    const int64_t lo = n * k / C, hi = n * (k + 1) / C;
-    s += (hi - lo + T - 1) / T;
-  }
-  return s;
+  const int64_t q = n / C, rem = n - q * C;  // the balanced split of make_pieces
+  return rem * ((q + 1 + T - 1) / T) + (C - rem) * ((q + T - 1) / T);
 }
 
 int64_t host_tiles(int64_t n_b, int64_t n_b1, int64_t rl, int64_t rr, int32_t pr, int32_t pc) {

@@ -301,6 +301,31 @@ def test_mixed_small_cases(tt, prec):
         assert_same(g, o)
 
 
+def test_maxwellian_batch_recipe_small(tt):
+    """The batch recipe's instances (uneven d, n, amplitudes) run in one
+    launch equal their single runs; the smallest also matches the oracle."""
+    ws = W.maxwellian_batch(3)
+    for w in ws:
+        w["n"] = [min(v, 12) for v in w["n"]]
+    singles = []
+    for w in ws:
+        a = tt.TTCross(w["n"], w["gen"], max_rank=24, nsamples=20000)
+        a.run(1e-5)
+        a.sync(allow=(tt.OK, tt.NOT_CONVERGED))
+        singles.append(a)
+    batch = [tt.TTCross(w["n"], w["gen"], max_rank=24, nsamples=20000) for w in ws]
+    tt.run_batch(batch, 1e-5)
+    for a, b in zip(singles, batch):
+        b.sync(allow=(tt.OK, tt.NOT_CONVERGED))
+        assert list(a.ranks()) == list(b.ranks())
+        for k in range(1, a.d + 1):
+            np.testing.assert_array_equal(a.core(k), b.core(k))
+    w = ws[0]
+    if singles[0].stats()["refinements"] == 0 and singles[0].stats()["status"] == tt.OK:
+        o, ties = replay_with_resync(singles[0], w, 1e-5, 24, 20000)
+        assert list(singles[0].ranks()[1:-1]) == list(o.ranks())
+
+
 def test_mixed_host_stepped_and_batch(tt):
     w = W.hilbert(5, 20)
     a = tt.TTCross(w["n"], w["gen"], max_rank=32, nsamples=30000, precision="split")
