@@ -201,6 +201,27 @@ def bench_gpu(args, rank, world, local):
         e2e.append((time.perf_counter() - t0) * 1e3)
         d2h = sum(c.nbytes for c in cores)
 
+    # the FP64 and mixed (float-float screen, certified FP64 pivots) forms
+    # side by side on this workload and on the 6D n=256 one (device time of
+    # the persistent kernel, best of 3)
+    forms = {}
+    if rank == 0 and not args.no_forms:
+        for wname in dict.fromkeys([args.workload, "hilbert6d_n256"]):
+            wc = workloads.CONFIGS[wname]
+            for prec in ("fp64", "split"):
+                f = ttcross.TTCross(wc["n"], wc["gen"], max_rank=wc["max_rank"],
+                                    nsamples=wc["nsamples"], precision=prec)
+                best = None
+                for _ in range(3):
+                    f.run(wc["eps"], subtensor_grid=wc["grid"], stream=stream)
+                    f.sync()
+                    fs = f.stats()
+                    best = fs["device_ms"] if best is None else min(best, fs["device_ms"])
+                forms[f"{wname}/{prec}"] = {"ms": best, "err": fs["err"],
+                                            "tiles_refined": fs["tiles_refined"],
+                                            "ranks": [int(x) for x in f.ranks()]}
+                f.close()
+
     # roofline of the dominant kernel (the persistent cross kernel): its
     # algorithmic FP64 FMAs (screen + error) over its measured duration
     fma64, _ = ttcross.probe_fma_peak(True)
@@ -233,6 +254,7 @@ def bench_gpu(args, rank, world, local):
                      "kernel": "k_persistent", "kernel_ms": kms,
                      "algorithmic_fma": algo_fma},
         "clocks": clocks,
+        "forms": forms,
     }
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -315,6 +337,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "split", "auto"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP64 vs mixed comparison runs")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["hilbert3d_n32", "hilbert6d_n64", "hilbert6d_n256", "maxwellian6d_n64",
                              "maxwellian_batch"])

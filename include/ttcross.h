@@ -111,6 +111,8 @@ typedef struct {
   int64_t refinements;       /* tau reductions */
   int64_t tiles_refined;     /* mixed forms: screen tiles whose error bound could hide
                                 the FP64 argmax and were re-screened in FP64 */
+  int64_t unscreened_slots;  /* self-check: candidate slots a merge read that no screen
+                                wrote in the same sweep (always 0) */
   int64_t screen_fmas;       /* algorithmic FMAs of the screens: sum over sweeps and
                                 bonds of r_k * |superblock_k| */
   int64_t error_fmas;        /* algorithmic FMAs of the sampled-error evaluations */

@@ -117,6 +117,9 @@ ttc_status ensure_cands(ttc_handle *h, const int32_t *grid) {
   const size_t bytes = (sizeof(Cand) + sizeof(MCand) + 2 * sizeof(int32_t) + sizeof(Cand)) *
                        (size_t)total;
   CU(cudaMalloc(&h->cand, bytes));
+  // all bits set: an unwritten slot reads as row -1 with a NaN key, which the
+  // merges count (ttc_stats.unscreened_slots) instead of trusting
+  CU(cudaMemset(h->cand, 0xFF, bytes));
   h->cand_cap = total;
   char *base = reinterpret_cast<char *>(h->cand);
   h->hi.mcand = reinterpret_cast<MCand *>(base + sizeof(Cand) * total);
@@ -679,6 +682,7 @@ ttc_status ttcross_get_stats(ttc_handle *h, ttc_stats *out) {
   out->entries_screened = c.entries;
   out->refinements = c.refinements;
   out->tiles_refined = c.tiles_refined;
+  out->unscreened_slots = c.unscreened;
   out->screen_fmas = c.screen_fmas;
   out->error_fmas = c.error_fmas;
   out->tau = c.tau;

@@ -60,6 +60,7 @@ struct Ctrl {
   int32_t best_row[TTC_MAXD], best_col[TTC_MAXD];
   double eps, tau, xrms, den, err;
   int64_t sweeps, entries, refinements, tiles_refined;
+  int64_t unscreened;        // candidate slots read by a merge that no screen wrote
   // tile schedule of the next screen (written by the instance's owner CTA
   // whenever its ranks change, read by every CTA): tile edge, and per bond
   // the superblock rows / columns and row / column tile counts

@@ -239,38 +239,50 @@ __device__ TileGeo tile_geo_e(const InstDev &in, const Ctrl &cr, const int32_t *
   return g;
 }
 
-// Tile autotuner: 64 x 64 tiles, unless the instance's superblocks give
-// under a quarter wave of them on this grid while the contraction is deep
-// (rank >= 24): then 32 x 32 tiles put four times the CTAs to work.  At
-// small ranks the per-tile overhead dominates and 64 x 64 stays faster
-// (measured on the 6D Hilbert workloads).
-__device__ int tile_edge(const InstDev &in, const Ctrl &cr, const int32_t *r, int grid) {
+// Tile autotuner (in write_plan_warp): 64 x 64 tiles, unless the instance's
+// superblocks give under a quarter wave of them on this grid while the
+// contraction is deep (rank >= 24): then 32 x 32 tiles put four times the
+// CTAs to work.  At small ranks the per-tile overhead dominates and 64 x 64
+// stays faster (measured on the 6D Hilbert workloads).
+// the tile plan of the next screen at ranks r, computed by one warp of the
+// owner CTA (lane b handles bond b)
+__device__ void write_plan_warp(const InstDev &in, Ctrl &cr, const int32_t *r, int grid) {
+  const int lane = threadIdx.x & 31;
+  const bool act = lane < in.nb;
+  TileGeo g64;
   int64_t t64 = 0;
   int kmax = 0;
-  for (int b = 0; b < in.nb; ++b) {
-    const TileGeo g = tile_geo_e(in, cr, r, b, 64);
-    t64 += (int64_t)g.nrt * g.nct;
-    kmax = max(kmax, (int)r[b]);
+  if (act) {
+    g64 = tile_geo_e(in, cr, r, lane, 64);
+    t64 = (int64_t)g64.nrt * g64.nct;
+    kmax = r[lane];
   }
-  if (4 * t64 >= (int64_t)grid || kmax < 24) return 64;
-  for (int b = 0; b < in.nb; ++b) {
-    const TileGeo g = tile_geo_e(in, cr, r, b, 32);
-    if ((int64_t)g.nrt * g.nct > in.bond[b].cand_cap) return 64;
+  for (int off = 16; off > 0; off >>= 1) {
+    t64 += __shfl_xor_sync(0xffffffffu, t64, off);
+    kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, off));
   }
-  return 32;
-}
-
-// the tile plan of the next screen at ranks r (owner CTA, one thread)
-__device__ void write_plan(const InstDev &in, Ctrl &cr, const int32_t *r, int grid) {
-  const int te = tile_edge(in, cr, r, grid);
-  cr.plan_te = te;
-  for (int b = 0; b < in.nb; ++b) {
-    const TileGeo g = tile_geo_e(in, cr, r, b, te);
-    cr.plan_rows[b] = g.rows;
-    cr.plan_cols[b] = g.cols;
-    cr.plan_nrt[b] = g.nrt;
-    cr.plan_nct[b] = g.nct;
+  int te = 64;
+  TileGeo g = g64;
+  if (4 * t64 < (int64_t)grid && kmax >= 24) {
+    // 32 x 32 tiles when the candidate slots of every bond allow them
+    int ok = 1;
+    if (act) {
+      g = tile_geo_e(in, cr, r, lane, 32);
+      ok = (int64_t)g.nrt * g.nct <= in.bond[lane].cand_cap;
+    }
+    if (__all_sync(0xffffffffu, ok)) {
+      te = 32;
+    } else {
+      g = g64;
+    }
   }
+  if (act) {
+    cr.plan_rows[lane] = g.rows;
+    cr.plan_cols[lane] = g.cols;
+    cr.plan_nrt[lane] = g.nrt;
+    cr.plan_nct[lane] = g.nct;
+  }
+  if (lane == 0) cr.plan_te = te;
 }
 
 // geometry of bond b as planned (cheap: no tile counting)
@@ -815,10 +827,13 @@ __device__ void merge_bond_fp64(const InstDev &in, Ctrl &cr, int b, DecideSmem &
   const int64_t nt = cr.ntiles[b];
   KeyBest best{0ull, LLONG_MAX, -1, -1};
   const Cand *cand = in.cand + in.bond[b].cand_base;
+  int bad = 0;
   for (int64_t t = threadIdx.x; t < nt; t += NT) {
     KeyBest o{cand[t].key, cand[t].lin, cand[t].row, cand[t].col};
+    bad += o.row < 0;
     kb_take(best, o);
   }
+  if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
   best = block_best(best, sm.rk, sm.rl, sm.rr, sm.rc);
   if (threadIdx.x == 0) {
     cr.best_key[b] = best.key;
@@ -842,8 +857,13 @@ __device__ void merge_bond_mixed(const InstDev &in, Ctrl &cr, int b, DecideSmem 
   // one pass: every thread keeps its k best tiles, the block merges them
   KeyBest loc[TOPK_MAX];
   for (int j = 0; j < k; ++j) loc[j] = KeyBest{0ull, LLONG_MAX, -1, -1};
+  int bad = 0;
   for (int64_t t = threadIdx.x; t < nt; t += NT) {
     const float v = mc[t].v;
+    if (mc[t].row < 0 && !(v == v)) {  // never written: count, do not use
+      ++bad;
+      continue;
+    }
     KeyBest o{(v == v) ? (uint64_t)__float_as_uint(v) : 0xFFFFFFFFull, mc[t].lin, 0, (int32_t)t};
     for (int j = 0; j < k; ++j) {
       if (loc[j].row < 0 || key_better(o.key, o.lin, loc[j].key, loc[j].lin)) {
@@ -854,6 +874,7 @@ __device__ void merge_bond_mixed(const InstDev &in, Ctrl &cr, int b, DecideSmem 
       }
     }
   }
+  if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
   for (int j = 0; j < k; ++j) {
     // the block's j-th best: the best head among the threads' lists
     KeyBest head = loc[0];
@@ -897,6 +918,7 @@ __device__ void merge_bond_mixed(const InstDev &in, Ctrl &cr, int b, DecideSmem 
     const MCand &c = mc[t];
     bool taken = false;
     for (int q = 0; q < k; ++q) taken |= sm.sel[q] == (int32_t)t;
+    if (c.row < 0 && !(c.v == c.v)) continue;  // never written (counted above)
     const double top = taken ? (double)c.rest : fmax((double)c.v, (double)c.rest);
     const double U = top * g + c.eabs;
     if (!(U == U) || (strict ? U > thr : U >= thr)) {
@@ -1022,10 +1044,13 @@ __device__ void phase_decide2(const RunArgs &ra, PhaseSmem &sm) {
     const int32_t cnt = cr.nrefine_bond[b];
     const Cand *rc = in.refine_cand + in.bond[b].cand_base;
     KeyBest best{cr.best_key[b], cr.best_lin[b], cr.best_row[b], cr.best_col[b]};
+    int bad = 0;
     for (int32_t t = threadIdx.x; t < cnt; t += NT) {
       KeyBest o{rc[t].key, rc[t].lin, rc[t].row, rc[t].col};
+      bad += o.row < 0;
       kb_take(best, o);
     }
+    if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
     best = block_best(best, d.rk, d.rl, d.rr, d.rc);
     if (threadIdx.x == 0) {
       cr.best_key[b] = best.key;
@@ -1337,9 +1362,9 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
       nadd += ad[b];
     }
     const bool screened = *(volatile const int32_t *)&cr.screened != 0;
-    if (blockIdx.x == ii % gridDim.x && threadIdx.x == 0) {
-      if (nadd == 0 && screened) in.ctrl->state = ST_VERIFY;
-      if (nadd > 0) write_plan(in, *in.ctrl, rn, gridDim.x);  // next screen's tiles
+    if (blockIdx.x == ii % gridDim.x && threadIdx.x < 32) {
+      if (nadd == 0 && screened && threadIdx.x == 0) in.ctrl->state = ST_VERIFY;
+      if (nadd > 0) write_plan_warp(in, *in.ctrl, rn, gridDim.x);  // next screen's tiles
     }
     if (nadd > 0) {
       // C first: the replays are the longest items
@@ -1505,7 +1530,6 @@ __device__ void phase_init2(const RunArgs &ra, PhaseSmem &sm) {
         cr.add[b] = 0;
       }
       if (cr.state != ST_DONE) {
-        write_plan(in, cr, cr.r, gridDim.x);
         // the pivot entry of every superblock is X(start)
         const double delta = 1.0 / __dsub_rn(xs0, 0.0);
         if (!isfinite(delta)) {
@@ -1518,6 +1542,8 @@ __device__ void phase_init2(const RunArgs &ra, PhaseSmem &sm) {
         }
       }
     }
+    __syncthreads();
+    if (threadIdx.x < 32 && cr.state != ST_DONE) write_plan_warp(in, cr, cr.r, gridDim.x);
     __syncthreads();
   }
 }

@@ -62,6 +62,7 @@ class Options(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("sweeps", C.c_int64), ("entries_screened", C.c_int64),
                 ("refinements", C.c_int64), ("tiles_refined", C.c_int64),
+                ("unscreened_slots", C.c_int64),
                 ("screen_fmas", C.c_int64), ("error_fmas", C.c_int64),
                 ("tau", C.c_double), ("x_rms", C.c_double), ("err", C.c_double),
                 ("device_ms", C.c_double), ("phase_ms", C.c_double * 6),

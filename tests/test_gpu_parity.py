@@ -34,6 +34,7 @@ def run_both(tt, w, eps, max_rank, nsamples, grid=None, **kw):
 
 def assert_same(g, o, cores=True):
     d = o.d
+    assert g.stats()["unscreened_slots"] == 0
     r = g.ranks()
     assert list(r[1:-1]) == list(o.ranks())
     for k in range(1, d):
@@ -282,6 +283,7 @@ def test_mixed_config1_pivots_equal_oracle(tt, prec):
     assert_same(g, o)
     st = g.stats()
     assert abs(st["err"] - ost["err"]) <= 1e-12
+    assert st["unscreened_slots"] == 0
     print(f"{prec}: tiles refined in FP64 {st['tiles_refined']}, sweeps {st['sweeps']}")
 
 
