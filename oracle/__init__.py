@@ -79,6 +79,11 @@ def lib():
             L.orc_residual.restype = C.c_double
             L.orc_residual.argtypes = [P, C.c_int, C.c_int64, C.c_int64]
             L.orc_apply.argtypes = [P, i32p, i32p, i32p]
+            L.orc_set_stored.argtypes = [P, C.c_int]
+            L.orc_stored_residual.restype = C.c_double
+            L.orc_stored_residual.argtypes = [P, C.c_int, C.c_int64, C.c_int64]
+            L.orc_E.argtypes = [P, C.c_int, f64p]
+            L.orc_stored_extent.argtypes = [P, C.c_int, i64p, i64p]
             L.orc_run.argtypes = [P, C.c_double, C.c_int64, C.c_uint64, C.c_int, C.POINTER(Stats)]
             L.orc_sampled_error.argtypes = [P, C.c_int64, C.c_uint64, f64p]
             L.orc_sample_rms.argtypes = [P, C.c_int64, C.c_uint64, f64p]
@@ -110,7 +115,7 @@ class Oracle:
     "vmin":..., "vmax":...}``.
     """
 
-    def __init__(self, n, gen, max_rank, nthreads: int = 1):
+    def __init__(self, n, gen, max_rank, nthreads: int = 1, stored: bool = False):
         L = lib()
         self.n = np.ascontiguousarray(n, dtype=np.int64)
         self.d = int(self.n.size)
@@ -141,6 +146,9 @@ class Oracle:
         if not self._h:
             raise ValueError("orc_create rejected the arguments")
         self._L = L
+        self.stored = bool(stored)
+        if stored and L.orc_set_stored(self._h, 1):
+            raise MemoryError("orc_set_stored: no memory for the stored residuals")
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -185,6 +193,19 @@ class Oracle:
 
     def residual(self, b, a, c) -> float:
         return float(self._L.orc_residual(self._h, int(b), int(a), int(c)))
+
+    def stored_residual(self, b, a, c) -> float:
+        """Stored-residual form: the kept E(a, c) of bond b (NaN if none)."""
+        return float(self._L.orc_stored_residual(self._h, int(b), int(a), int(c)))
+
+    def stored_block(self, b) -> np.ndarray:
+        """Stored-residual form: E of bond b over the superblock of the last
+        screen, [rows, cols]."""
+        rows, cols = C.c_int64(), C.c_int64()
+        self._L.orc_stored_extent(self._h, int(b), C.byref(rows), C.byref(cols))
+        out = np.zeros((rows.value, cols.value))
+        self._L.orc_E(self._h, int(b), _p(out, C.c_double))
+        return out
 
     def apply(self, add, row, col) -> int:
         add = np.ascontiguousarray(add, dtype=np.int32)

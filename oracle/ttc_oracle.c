@@ -49,6 +49,11 @@ struct orc_state {
   double *hdelta[ORC_MAXD];
   double *hpiv[ORC_MAXD]; /* [cap][cap]: row z = T(a_z, 0..z-1) before step z */
   double *hc[ORC_MAXD];   /* [cap][cap]: row z = A(a_t, c_z), t < z */
+  /* stored-residual form (eq. aca_approx_E): E[b] [rows_cap][cols_cap], valid
+     on rows < st_rows[b] and columns < st_cols[b] */
+  int stored;
+  double *E[ORC_MAXD];
+  int64_t st_rows[ORC_MAXD], st_cols[ORC_MAXD];
   int initialized;
 };
 
@@ -222,9 +227,22 @@ void orc_destroy(orc_state *s) {
     free(s->I[b]); free(s->J[b]); free(s->prow[b]); free(s->pcol[b]);
     free(s->T[b]); free(s->R[b]); free(s->U[b]);
     free(s->hdelta[b]); free(s->hpiv[b]); free(s->hc[b]);
+    free(s->E[b]);
   }
   free(s->tt);
   free(s);
+}
+
+int orc_set_stored(orc_state *s, int on) {
+  if (!on) { s->stored = 0; return ORC_OK; }
+  for (int b = 0; b < s->d - 1; ++b) {
+    if (s->E[b]) continue;
+    s->E[b] = (double *)calloc((size_t)(s->rows_cap[b] * s->cols_cap[b]), sizeof(double));
+    if (!s->E[b]) return ORC_ERR_OOM;
+  }
+  s->stored = 1;
+  for (int b = 0; b < s->d - 1; ++b) s->st_rows[b] = s->st_cols[b] = 0;
+  return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -272,6 +290,7 @@ int orc_init_at(orc_state *s, const int32_t *start) {
     s->hdelta[b][0] = delta;
     s->U[b][0] = delta;
     for (int64_t a = 0; a < rows; ++a) replay_row(s, b, a, 1);
+    s->st_rows[b] = s->st_cols[b] = 0; /* nothing stored yet */
   }
   s->initialized = 1;
   return ORC_OK;
@@ -305,13 +324,23 @@ static best_t screen_rows(const orc_state *s, int b, int64_t a0, int64_t a1) {
   int32_t idx[ORC_MAXD];
   for (int64_t a = a0; a < a1; ++a) {
     const double *Ta = s->T[b] + a * cap;
+    double *Ea = s->stored ? s->E[b] + a * s->cols_cap[b] : NULL;
     for (int64_t c = 0; c < cols; ++c) {
       sb_index(s, b, a, c, idx);
-      double A = orc_entry(s, idx);
-      double e = A - chain(Ta, 1, s->R[b] + c, s->cols_cap[b], K);
+      double e;
+      if (Ea && a < s->st_rows[b] && c < s->st_cols[b]) {
+        /* stored form: the residual kept from the last screen, already
+           carried through the rank-one steps since (eq. aca_approx_E) */
+        e = Ea[c];
+      } else {
+        /* an entry seen for the first time: E = A - T R */
+        double A = orc_entry(s, idx);
+        e = A - chain(Ta, 1, s->R[b] + c, s->cols_cap[b], K);
+        if (Ea) Ea[c] = e;
+        if (fabs(A) > bt.maxabs) bt.maxabs = fabs(A);
+      }
       if (!isfinite(e)) { bt.bad = 1; continue; }
       double v = fabs(e);
-      if (fabs(A) > bt.maxabs) bt.maxabs = fabs(A);
       int64_t lin = lin_index(s, idx);
       if (better(v, lin, &bt)) { bt.v = v; bt.lin = lin; bt.a = a; bt.c = c; }
     }
@@ -322,6 +351,11 @@ static best_t screen_rows(const orc_state *s, int b, int64_t a0, int64_t a1) {
 double orc_residual(const orc_state *s, int b, int64_t a, int64_t c) {
   return sb_entry(s, b, a, c) -
          chain(s->T[b] + a * s->maxr[b], 1, s->R[b] + c, s->cols_cap[b], s->r[b]);
+}
+
+double orc_stored_residual(const orc_state *s, int b, int64_t a, int64_t c) {
+  if (!s->stored || a >= s->st_rows[b] || c >= s->st_cols[b]) return NAN;
+  return s->E[b][a * s->cols_cap[b] + c];
 }
 
 int orc_screen(orc_state *s, double *best, int64_t *lin, int32_t *row,
@@ -355,6 +389,7 @@ int orc_screen(orc_state *s, double *best, int64_t *lin, int32_t *row,
     bt.maxabs = mx;
     bt.bad = bd;
     bad |= bt.bad;
+    if (s->stored) { s->st_rows[b] = rows; s->st_cols[b] = cols_of(s, b); }
     best[b] = bt.v; lin[b] = bt.lin;
     row[b] = (int32_t)bt.a; col[b] = (int32_t)bt.c;
     maxabs[b] = bt.maxabs;
@@ -376,6 +411,33 @@ int orc_apply(orc_state *s, const int32_t *add, const int32_t *row,
     if (add[b] && (row[b] < 0 || row[b] >= rows_of(s, b) || col[b] < 0 ||
                    col[b] >= cols_of(s, b)))
       return ORC_ERR_INVALID_ARG;
+  }
+  /* (0) stored form, eq. aca_approx_E on the sweep-start superblock:
+     E <- E - E(:,c*) E(a*,:) / E(a*,c*), entry by entry
+       E(a,c) = fma(w_a, E(a*,c), E(a,c)),  w_a = -(E(a,c*) / E(a*,c*))
+     (w_{a*} = -1 exactly, so row a* becomes exactly zero). */
+  if (s->stored) {
+    for (int b = 0; b < d - 1; ++b) {
+      if (!add[b]) continue;
+      int64_t rows = s->st_rows[b], cols = s->st_cols[b], ld = s->cols_cap[b];
+      if (rows != rows_of(s, b) || cols != cols_of(s, b)) return ORC_ERR_INVALID_ARG;
+      double *E = s->E[b];
+      int64_t as = row[b], cs = col[b];
+      double piv = E[as * ld + cs];
+      double *erow = (double *)malloc(sizeof(double) * cols);
+      double *w = (double *)malloc(sizeof(double) * rows);
+      if (!erow || !w) { free(erow); free(w); return ORC_ERR_OOM; }
+      for (int64_t c = 0; c < cols; ++c) erow[c] = E[as * ld + c];
+      for (int64_t a = 0; a < rows; ++a) w[a] = -(E[a * ld + cs] / piv);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(s->nthreads) schedule(static)
+#endif
+      for (int64_t a = 0; a < rows; ++a)
+        for (int64_t c = 0; c < cols; ++c)
+          E[a * ld + c] = fma(w[a], erow[c], E[a * ld + c]);
+      free(erow);
+      free(w);
+    }
   }
   /* (1) pivot step on the sweep-start superblocks */
   for (int b = 0; b < d - 1; ++b) {
@@ -720,4 +782,14 @@ void orc_U(const orc_state *s, int b, double *out) {
   int64_t cap = s->maxr[b];
   for (int t = 0; t < s->r[b]; ++t)
     for (int u = 0; u < s->r[b]; ++u) out[t * s->r[b] + u] = s->U[b][t * cap + u];
+}
+void orc_E(const orc_state *s, int b, double *out) {
+  int64_t rows = s->st_rows[b], cols = s->st_cols[b];
+  for (int64_t a = 0; a < rows; ++a)
+    for (int64_t c = 0; c < cols; ++c)
+      out[a * cols + c] = s->stored ? s->E[b][a * s->cols_cap[b] + c] : NAN;
+}
+void orc_stored_extent(const orc_state *s, int b, int64_t *rows, int64_t *cols) {
+  *rows = s->stored ? s->st_rows[b] : 0;
+  *cols = s->stored ? s->st_cols[b] : 0;
 }

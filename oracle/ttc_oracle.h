@@ -29,6 +29,7 @@
  *     every row a: s=chain(T(a,:),cz)-A(a,c*); w=delta*s;
  *       T(a,t)=fma(w,Tp[t],T(a,t)) (t<z); T(a,z)=-w
  *   ties in |E| go to the lowest column-major linear index of the entry.
+ *   stored-residual form: see orc_set_stored.
  */
 #ifndef TTC_ORACLE_H
 #define TTC_ORACLE_H
@@ -100,6 +101,23 @@ int orc_screen(orc_state *s, double *best, int64_t *lin, int32_t *row,
    of bond b, as the screen computes it. */
 double orc_residual(const orc_state *s, int b, int64_t a, int64_t c);
 
+/* Stored-residual form (eq. aca_approx_E, Sec. 3.1.1): on = 1 keeps every
+   bond's residual E over its superblock and updates it by rank-one steps
+   instead of recomputing A - T R.  Contract:
+     - an entry entering a superblock (first screen, or rows / columns added
+       by a neighbour's pivot) gets E = A - chain(T(a,:), R(:,c)) with the
+       current T, R, as in the recompute form;
+     - when bond b appends pivot (a*, c*), every entry of the sweep-start
+       superblock becomes E(a,c) = fma(w_a, E(a*,c), E(a,c)) with
+       w_a = -(E(a,c*) / E(a*,c*)) (row a* becomes exactly zero);
+     - the screen is the argmax of the stored |E| (same tie rule); T, U, R
+       and the cores are updated exactly as in the recompute form.
+   Call after orc_create and before the first screen (orc_run re-initialises
+   the stored extents).  Allocates rows_cap x cols_cap doubles per bond. */
+int orc_set_stored(orc_state *s, int on);
+/* Stored E(a,c) of bond b (NaN outside the stored extent or when off). */
+double orc_stored_residual(const orc_state *s, int b, int64_t a, int64_t c);
+
 /* Append pivot (row[b], col[b]) to every bond b with add[b] != 0 (row/col are
    superblock coordinates of the sweep-start superblock), update T, R, U and
    the history, then extend the neighbouring superblocks. */
@@ -145,6 +163,10 @@ void orc_pivot_coords(const orc_state *s, int b, int32_t *prow, int32_t *pcol);
 void orc_T(const orc_state *s, int b, double *out);
 void orc_R(const orc_state *s, int b, double *out);
 void orc_U(const orc_state *s, int b, double *out);
+/* stored form: E_b over its stored extent [st_rows][st_cols] (the superblock
+   of the last screen), row-major */
+void orc_E(const orc_state *s, int b, double *out);
+void orc_stored_extent(const orc_state *s, int b, int64_t *rows, int64_t *cols);
 /* core m as [s_{m-1}][n_m][s_m] row-major */
 void orc_core(const orc_state *s, int m, double *out);
 int64_t orc_core_size(const orc_state *s, int m);
