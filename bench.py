@@ -153,7 +153,8 @@ def bench_gpu(args, rank, world, local):
     cfg = workloads.CONFIGS[args.workload]
     stream = torch.cuda.Stream()
     tc = ttcross.TTCross(cfg["n"], cfg["gen"], max_rank=cfg["max_rank"], nsamples=cfg["nsamples"],
-                         precision=args.precision, host_loop=args.host_loop)
+                         precision=args.precision, host_loop=args.host_loop,
+                         residual=args.residual)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def one_step():
@@ -201,25 +202,38 @@ def bench_gpu(args, rank, world, local):
         e2e.append((time.perf_counter() - t0) * 1e3)
         d2h = sum(c.nbytes for c in cores)
 
-    # the FP64 and mixed (float-float screen, certified FP64 pivots) forms
-    # side by side on this workload and on the 6D n=256 one (device time of
-    # the persistent kernel, best of 3)
+    # the forms side by side on this workload and on the 6D n=256 one (device
+    # time of the persistent kernel, best of 3): FP64 recompute, mixed
+    # (float-float screen, certified FP64 pivots) and FP64 stored residual
     forms = {}
     if rank == 0 and not args.no_forms:
         for wname in dict.fromkeys([args.workload, "hilbert6d_n256"]):
             wc = workloads.CONFIGS[wname]
-            for prec in ("fp64", "split"):
+            for prec, resid in (("fp64", "recompute"), ("split", "recompute"),
+                                ("fp64", "stored")):
                 f = ttcross.TTCross(wc["n"], wc["gen"], max_rank=wc["max_rank"],
-                                    nsamples=wc["nsamples"], precision=prec)
+                                    nsamples=wc["nsamples"], precision=prec, residual=resid)
                 best = None
-                for _ in range(3):
+                key = f"{wname}/{prec}" + ("/stored" if resid == "stored" else "")
+                failed = None
+                for rep in range(3):
                     f.run(wc["eps"], subtensor_grid=wc["grid"], stream=stream)
-                    f.sync()
+                    rc = f._L.ttcross_sync(f.handle)
                     fs = f.stats()
+                    if rc not in (ttcross.OK, ttcross.NOT_CONVERGED):
+                        failed = {"status": ttcross.STATUS_NAMES.get(rc, rc), "rep": rep,
+                                  "sweeps": fs["sweeps"], "unscreened": fs["unscreened_slots"],
+                                  "ranks": [int(x) for x in f.ranks()]}
+                        break
                     best = fs["device_ms"] if best is None else min(best, fs["device_ms"])
-                forms[f"{wname}/{prec}"] = {"ms": best, "err": fs["err"],
-                                            "tiles_refined": fs["tiles_refined"],
-                                            "ranks": [int(x) for x in f.ranks()]}
+                if failed is not None:
+                    forms[key] = {"failed": failed}
+                    f.close()
+                    continue
+                forms[key] = {"ms": best, "err": fs["err"], "tiles_refined": fs["tiles_refined"],
+                              "entries_fresh": fs["entries_fresh"],
+                              "stored_bytes": fs["stored_bytes"], "phase_ms": fs["phase_ms"],
+                              "ranks": [int(x) for x in f.ranks()]}
                 f.close()
 
     # roofline of the dominant kernel (the persistent cross kernel): its
@@ -237,7 +251,8 @@ def bench_gpu(args, rank, world, local):
         "config": {"workload": args.workload, "d": len(cfg["n"]), "n": cfg["n"][0],
                    "eps": cfg["eps"], "max_rank": cfg["max_rank"], "grid": cfg["grid"],
                    "nsamples": cfg["nsamples"],
-                   "precision": args.precision, "l2": "flushed between steps (512 MB write)",
+                   "precision": args.precision, "residual": args.residual,
+                   "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "min_ms": min(step_ms), "median_ms": statistics.median(step_ms),
         "entries_screened": st["entries_screened"],
@@ -336,6 +351,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "split", "auto"])
+    ap.add_argument("--residual", default="recompute", choices=["recompute", "stored"],
+                    help="screen form: A - T R every sweep, or the stored residual")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP64 vs mixed comparison runs")

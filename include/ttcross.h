@@ -90,6 +90,18 @@ typedef enum {
   TTC_PREC_AUTO = 3   /* FP32 for eps >= 1e-7 (of the entries' rms), else SPLIT */
 } ttc_precision;
 
+typedef enum {
+  TTC_RESIDUAL_RECOMPUTE = 0, /* every screen forms E = A - T_k R_k afresh (Alg. 1) */
+  TTC_RESIDUAL_STORED = 1     /* eq. aca_approx_E: E_k is kept in device memory and
+                                 carried through each pivot's rank-one step
+                                 E <- E - E(:,j*) E(i*,:) / E(i*,j*); only entries
+                                 that enter a superblock are formed as A - T R.
+                                 FP64 only.  Needs 8 * rows_cap * cols_cap bytes per
+                                 bond (rows_cap = cap_{k-1} n_k, cols_cap = n_{k+1}
+                                 cap_{k+1}); pivots follow the stored values, so they
+                                 may differ from the recompute form's at near-ties. */
+} ttc_residual;
+
 typedef struct {
   int32_t max_rank;         /* rank capacity of every bond (default 64, <= 128) */
   const int32_t *bond_max_rank; /* nullable host array of d-1 per-bond rank caps
@@ -103,6 +115,7 @@ typedef struct {
                                (default); 1: host-stepped phases (debugging) */
   int32_t grid_ctas;        /* persistent CTAs (0 = one wave at full occupancy) */
   double wait_limit_s;      /* limit of every device-side wait, seconds (default 2.0) */
+  int32_t residual;         /* ttc_residual (default TTC_RESIDUAL_RECOMPUTE) */
 } ttc_options;
 
 typedef struct {
@@ -124,6 +137,9 @@ typedef struct {
                                 decide, update, error verification, FP64 refinement) */
   int32_t status;            /* ttc_status of the last run */
   int32_t device_error_where;/* for TTC_ERR_DEVICE_TIMEOUT: the wait that gave up */
+  int64_t entries_fresh;     /* screened entries formed as A - T R (all of them in the
+                                recompute form; the rest were carried in storage) */
+  int64_t stored_bytes;      /* stored form: bytes of E the screens read and wrote */
 } ttc_stats;
 
 typedef struct ttc_handle ttc_handle;

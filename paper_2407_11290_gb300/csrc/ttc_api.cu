@@ -70,6 +70,8 @@ struct ttc_handle {
   Ctrl h_ctrl{};
   void *pool = nullptr;
   size_t pool_bytes = 0;
+  void *estore = nullptr;       // stored-residual form: E, ew, erow of every bond
+  size_t estore_bytes = 0;
   Cand *cand = nullptr;
   int64_t cand_cap = 0;
   int64_t bond_cand_cap[TTC_MAXB] = {};
@@ -135,6 +137,10 @@ ttc_status ensure_cands(ttc_handle *h, const int32_t *grid) {
   }
   h->hi.cand = h->cand;
   CU(cudaMemcpy(h->d_inst, &h->hi, sizeof(InstDev), cudaMemcpyHostToDevice));
+  // the memset and the copy ran on the legacy stream, which does not order
+  // against the caller's (possibly non-blocking) stream, and a pageable copy
+  // may return before its DMA lands: finish both before any launch
+  CU(cudaDeviceSynchronize());
   return TTC_OK;
 }
 
@@ -225,6 +231,7 @@ ttc_status ttcross_default_options(ttc_options *opt) {
   opt->host_loop = 0;
   opt->grid_ctas = 0;
   opt->wait_limit_s = 2.0;
+  opt->residual = TTC_RESIDUAL_RECOMPUTE;
   return TTC_OK;
 }
 
@@ -249,6 +256,10 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     return fail(TTC_ERR_INVALID_ARG, "wait_limit_s must be in (0, 600]");
   if (o.grid_ctas < 0 || o.grid_ctas > GRID_CAP)
     return fail(TTC_ERR_INVALID_ARG, "grid_ctas outside [0,%d]", GRID_CAP);
+  if (o.residual != TTC_RESIDUAL_RECOMPUTE && o.residual != TTC_RESIDUAL_STORED)
+    return fail(TTC_ERR_INVALID_ARG, "unknown residual form %d", o.residual);
+  if (o.residual == TTC_RESIDUAL_STORED && o.precision != TTC_PREC_FP64)
+    return fail(TTC_ERR_INVALID_ARG, "the stored residual form is FP64 only");
   int64_t total = 1;
   bool overflow = false;
   int64_t hsum = 0;
@@ -478,9 +489,42 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
   auto cleanup = [&](ttc_status s) {
     cudaFree(h->pool);
     if (h->cand) cudaFree(h->cand);
+    if (h->estore) cudaFree(h->estore);
     delete h;
     return s;
   };
+  if (o.residual == TTC_RESIDUAL_STORED) {
+    // E [ldT][ldR], ew [ldT], erow [ldR] per bond, in one allocation of its own
+    // (it dominates the footprint: 8 B per superblock entry at the rank caps)
+    Carver ev;
+    for (int pass = 0; pass < 2; ++pass) {
+      ev.base = static_cast<char *>(h->estore);
+      ev.off = 0;
+      for (int b = 0; b < d - 1; ++b) {
+        BondDev &B = I.bond[b];
+        double *E = ev.take<double>((size_t)(B.ldT * B.ldR));
+        double *ew = ev.take<double>((size_t)B.ldT);
+        double *er = ev.take<double>((size_t)B.ldR);
+        if (pass == 1) {
+          B.E = E;
+          B.ew = ew;
+          B.erow = er;
+        }
+      }
+      if (pass == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && ev.off > fr)
+          return cleanup(fail(TTC_ERR_OOM, "stored residuals need %zu bytes, %zu free", ev.off, fr));
+        h->estore_bytes = ev.off;
+        cudaError_t e = cudaMalloc(&h->estore, ev.off);
+        if (e != cudaSuccess)
+          return cleanup(fail(e == cudaErrorMemoryAllocation ? TTC_ERR_OOM : TTC_ERR_CUDA,
+                              "cudaMalloc(%zu) of the stored residuals failed: %s", ev.off,
+                              cudaGetErrorString(e)));
+      }
+    }
+    I.stored = 1;
+  }
   if (cudaMemset(h->pool, 0, h->pool_bytes) != cudaSuccess)
     return cleanup(fail(TTC_ERR_CUDA, "cudaMemset failed"));
   if (gen->kind == TTC_GEN_HILBERT) {
@@ -516,6 +560,10 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
         cudaDeviceSynchronize() != cudaSuccess)
       return cleanup(fail(TTC_ERR_CUDA, "Maxwellian tables failed"));
   }
+  // every setup copy above is on the legacy stream: complete them before the
+  // caller launches on a stream that does not order against it
+  if (cudaDeviceSynchronize() != cudaSuccess)
+    return cleanup(fail(TTC_ERR_CUDA, "setup did not complete"));
   if (cudaEventCreate(&h->ev0) == cudaSuccess && cudaEventCreate(&h->ev1) == cudaSuccess)
     h->events_ok = true;
   if (!bcaps.empty()) {
@@ -689,6 +737,8 @@ ttc_status ttcross_get_stats(ttc_handle *h, ttc_stats *out) {
   out->x_rms = c.xrms;
   out->err = c.err;
   out->status = s;
+  out->entries_fresh = c.entries_fresh;
+  out->stored_bytes = c.stored_bytes;
   float ms = 0.f;
   if (h->events_ok && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) out->device_ms = ms;
   Barrier bar;
@@ -707,6 +757,7 @@ ttc_status ttcross_destroy(ttc_handle *h) {
     cudaEventDestroy(h->ev1);
   }
   if (h->cand) cudaFree(h->cand);
+  if (h->estore) cudaFree(h->estore);
   if (h->pool) cudaFree(h->pool);
   delete h;
   return TTC_OK;

@@ -10,6 +10,9 @@
 //     U  [R_b][R_b]  P_k^{-1} (bordered Sherman-Morrison, Sec. 3.1.1)
 //     hpiv/hc [R_b][R_b], delta[R_b]: pivot history replayed by Alg. 4
 //     I, J: pivot multi-indices + column-major linear index + index sum
+//     E  [ldT][ldR]  FP64, stored-residual form only: the residual of every
+//        superblock entry, row-major (eq. aca_approx_E); ew [ldT] and
+//        erow [ldR] hold the rank-one step of the last pivot
 //   ldT = cap(R_{b-1}) * n_b and ldR = n_{b+1} * cap(R_{b+1}), so rows and
 //   columns that enter the superblock later are appended, never moved.
 #pragma once
@@ -41,6 +44,7 @@ struct BondDev {
   double *T, *R, *U, *hpiv, *hc, *delta;
   float *Thi, *Tlo, *Rhi, *Rlo;
   int32_t *prow, *pcol;  // pivot superblock coordinates, insertion order
+  double *E, *ew, *erow; // stored-residual form (null otherwise)
   SetDev I, J;
   int64_t cand_base;     // first candidate slot of this bond
   int64_t cand_cap;      // candidate slots of this bond
@@ -75,6 +79,14 @@ struct Ctrl {
   int32_t max_refine;
   int32_t grid[TTC_MAXD];  // subtensor pieces per mode (0 = library tiles)
   int32_t pad;
+  // stored-residual form, per bond: the stored extent (superblock rows /
+  // columns as of the last screen) and whether the rank-one step of the last
+  // pivot (ew, erow) is still to be applied by the next screen
+  int32_t st_rows[TTC_MAXD], st_cols[TTC_MAXD];
+  int32_t e_pend[TTC_MAXD];
+  int32_t pad3;
+  int64_t entries_fresh;     // entries evaluated as A - T R (the rest carried)
+  int64_t stored_bytes;      // bytes of E read and written by the screens
 };
 
 struct InstDev {
@@ -96,6 +108,7 @@ struct InstDev {
   int64_t mx_stride[TTC_MAXD];
   int32_t prec;
   int32_t topk;
+  int32_t stored;                    // stored-residual screen (FP64 only)
   BondDev bond[TTC_MAXB];
   SetDev empty;                      // I_{<=0} / J_{>d}: one empty multi-index
   double *xs;                        // X at the error samples

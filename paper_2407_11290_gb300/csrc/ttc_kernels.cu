@@ -263,7 +263,7 @@ __device__ void write_plan_warp(const InstDev &in, Ctrl &cr, const int32_t *r, i
   }
   int te = 64;
   TileGeo g = g64;
-  if (4 * t64 < (int64_t)grid && kmax >= 24) {
+  if (!in.stored && 4 * t64 < (int64_t)grid && kmax >= 24) {
     // 32 x 32 tiles when the candidate slots of every bond allow them
     int ok = 1;
     if (act) {
@@ -377,16 +377,15 @@ __device__ __forceinline__ double tile_entry(const InstDev &in, const ScreenSmem
   return gen_full(in, idx);
 }
 
-template <bool HIL, int TE>
-__device__ __noinline__ void screen_tile_fp64_t(const InstDev &in, int b, int K, int64_t r0, int nr,
-                                                int64_t c0, int nc, Cand *out, ScreenSmem &sm) {
-  constexpr int U = TE / 16;  // entries per thread and dimension
-  const BondDev &B = in.bond[b];
+// acc[u][v] = chain(T(r0 + ty + 16u, :), R(:, c0 + tx + 16v)) over t < K, the
+// contract's serial FMA order, T / R staged through shared memory in 32-deep
+// chunks (the first chunk's barrier also publishes the tile metadata)
+template <int TE>
+__device__ __forceinline__ void tile_chain_fp64(const BondDev &B, int K, int64_t r0, int nr,
+                                                int64_t c0, int nc, double (&acc)[TE / 16][TE / 16],
+                                                ScreenSmem &sm) {
+  constexpr int U = TE / 16;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int wl = b, wr = in.d - b - 2;
-  __syncthreads();
-  stage_meta(in, b, r0, nr, c0, nc, sm);
-  double acc[U][U];
 #pragma unroll
   for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -415,6 +414,19 @@ __device__ __noinline__ void screen_tile_fp64_t(const InstDev &in, int b, int K,
         for (int v = 0; v < U; ++v) acc[u][v] = __fma_rn(tv[u], rv[v], acc[u][v]);
     }
   }
+}
+
+template <bool HIL, int TE>
+__device__ __noinline__ void screen_tile_fp64_t(const InstDev &in, int b, int K, int64_t r0, int nr,
+                                                int64_t c0, int nc, Cand *out, ScreenSmem &sm) {
+  constexpr int U = TE / 16;  // entries per thread and dimension
+  const BondDev &B = in.bond[b];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int wl = b, wr = in.d - b - 2;
+  __syncthreads();
+  stage_meta(in, b, r0, nr, c0, nc, sm);
+  double acc[U][U];
+  tile_chain_fp64<TE>(B, K, r0, nr, c0, nc, acc, sm);
   KeyBest best{0ull, LLONG_MAX, -1, -1};
 #pragma unroll
   for (int u = 0; u < U; ++u) {
@@ -460,6 +472,137 @@ __device__ __forceinline__ void screen_tile_fp64(const InstDev &in, int b, int K
       screen_tile_fp64_t<true, 64>(in, b, K, r0, nr, c0, nc, out, sm);
     else
       screen_tile_fp64_t<false, 64>(in, b, K, r0, nr, c0, nc, out, sm);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stored-residual screen of one tile (eq. aca_approx_E).  Entries inside the
+// stored extent (row < sr and column < sc) are read from E and, when the bond
+// appended a pivot in the last sweep (pend), carried through its rank-one
+// step E(a,c) = fma(ew[a], erow[c], E(a,c)) with ew[a] = -(E(a,c*) / E(a*,c*))
+// and erow = E(a*, :).  Entries outside it have just entered the superblock
+// and get A - chain(T(a,:), R(:,c)) with the current factors.  Both are written
+// back to E; the tile's best |E| is kept as in the FP64 screen.
+template <bool HIL, int TE>
+__device__ __noinline__ void screen_tile_stored_t(const InstDev &in, int b, int K, int64_t r0,
+                                                  int nr, int64_t c0, int nc, int32_t sr,
+                                                  int32_t sc, int pend, Cand *out,
+                                                  ScreenSmem &sm) {
+  constexpr int U = TE / 16;
+  const BondDev &B = in.bond[b];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int wl = b, wr = in.d - b - 2;
+  const int64_t ld = B.ldR;
+  __syncthreads();
+  stage_meta(in, b, r0, nr, c0, nc, sm);
+  const bool carried = r0 + nr <= sr && c0 + nc <= sc;
+  double ev[U][U];
+  if (carried) {
+    // streaming tile: all loads first, then the rank-one step and the stores
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int rr = ty + 16 * u;
+#pragma unroll
+      for (int v = 0; v < U; ++v) {
+        const int cc = tx + 16 * v;
+        ev[u][v] = (rr < nr && cc < nc) ? B.E[(r0 + rr) * ld + c0 + cc] : 0.0;
+      }
+    }
+    if (pend) {
+      double wa[U], er[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) wa[u] = ty + 16 * u < nr ? B.ew[r0 + ty + 16 * u] : 0.0;
+#pragma unroll
+      for (int v = 0; v < U; ++v) er[v] = tx + 16 * v < nc ? B.erow[c0 + tx + 16 * v] : 0.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int rr = ty + 16 * u;
+#pragma unroll
+        for (int v = 0; v < U; ++v) {
+          const int cc = tx + 16 * v;
+          if (rr < nr && cc < nc) {
+            ev[u][v] = __fma_rn(wa[u], er[v], ev[u][v]);
+            B.E[(r0 + rr) * ld + c0 + cc] = ev[u][v];
+          }
+        }
+      }
+    }
+    __syncthreads();  // publishes the tile metadata
+  } else {
+    double acc[U][U];
+    tile_chain_fp64<TE>(B, K, r0, nr, c0, nc, acc, sm);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int rr = ty + 16 * u;
+      const int64_t a = r0 + rr;
+      const bool arow = rr < nr && a < sr;
+      const double wa = (pend && arow) ? B.ew[a] : 0.0;
+#pragma unroll
+      for (int v = 0; v < U; ++v) {
+        const int cc = tx + 16 * v;
+        const int64_t c = c0 + cc;
+        if (rr >= nr || cc >= nc) {
+          ev[u][v] = 0.0;
+          continue;
+        }
+        double e;
+        if (arow && c < sc) {
+          e = B.E[a * ld + c];
+          if (pend) e = __fma_rn(wa, B.erow[c], e);
+        } else {
+          const double A =
+              HIL ? in.hilb[sm.srow[rr] + sm.scol[cc]] : tile_entry(in, sm, wl, wr, rr, cc);
+          e = __dsub_rn(A, acc[u][v]);
+        }
+        B.E[a * ld + c] = e;
+        ev[u][v] = e;
+      }
+    }
+  }
+  KeyBest best{0ull, LLONG_MAX, -1, -1};
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int rr = ty + 16 * u;
+    if (rr >= nr) continue;
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+      const int cc = tx + 16 * v;
+      if (cc >= nc) continue;
+      const uint64_t k = abs_key(ev[u][v]);
+      if (best.row < 0 || k >= best.key) {
+        const int64_t l = sm.lrow[rr] + sm.lcol[cc];
+        if (best.row < 0 || k > best.key || l < best.lin) {
+          best.key = k;
+          best.lin = l;
+          best.row = (int32_t)(r0 + rr);
+          best.col = (int32_t)(c0 + cc);
+        }
+      }
+    }
+  }
+  best = block_best(best, sm.sk, sm.sl, sm.sr, sm.sc);
+  if (tid == 0) {
+    out->key = best.key;
+    out->lin = best.lin;
+    out->row = best.row;
+    out->col = best.col;
+  }
+}
+
+__device__ __forceinline__ void screen_tile_stored(const InstDev &in, int b, int K, int64_t r0,
+                                                   int nr, int64_t c0, int nc, int te, int32_t sr,
+                                                   int32_t sc, int pend, Cand *out,
+                                                   ScreenSmem &sm) {
+  if (te == 32) {
+    if (in.gen == 0)
+      screen_tile_stored_t<true, 32>(in, b, K, r0, nr, c0, nc, sr, sc, pend, out, sm);
+    else
+      screen_tile_stored_t<false, 32>(in, b, K, r0, nr, c0, nc, sr, sc, pend, out, sm);
+  } else {
+    if (in.gen == 0)
+      screen_tile_stored_t<true, 64>(in, b, K, r0, nr, c0, nc, sr, sc, pend, out, sm);
+    else
+      screen_tile_stored_t<false, 64>(in, b, K, r0, nr, c0, nc, sr, sc, pend, out, sm);
   }
 }
 
@@ -676,28 +819,48 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       // bookkeeping of this screen
       Ctrl &cw = *in.ctrl;
-      int64_t entries = 0, fmas = 0;
+      int64_t entries = 0, fmas = 0, fresh = 0, bytes = 0;
       for (int b = 0; b < in.nb; ++b) {
         cw.ntiles[b] = cw.plan_nrt[b] * cw.plan_nct[b];
         const int64_t e = (int64_t)cw.plan_rows[b] * cw.plan_cols[b];
         entries += e;
-        fmas += e * r[b];
+        if (in.stored) {
+          // carried entries cost one FMA when a rank-one step is pending
+          const int64_t kept = (int64_t)cw.st_rows[b] * cw.st_cols[b];
+          fresh += e - kept;
+          fmas += (e - kept) * r[b] + (cw.e_pend[b] ? kept : 0);
+          bytes += 8 * e + (cw.e_pend[b] ? 8 * kept : 0);
+        } else {
+          fresh += e;
+          fmas += e * r[b];
+        }
       }
       cw.sweeps += 1;
       cw.entries += entries;
+      cw.entries_fresh += fresh;
+      cw.stored_bytes += bytes;
       cw.screen_fmas += fmas;
       cw.screened = 1;
     }
     for (int b = 0; b < in.nb; ++b) {
       const TileGeo g = planned_geo(in, cr, b);
       const int32_t nt = g.nrt * g.nct;
+      int32_t sr = 0, sc = 0, pend = 0;
+      if (in.stored) {
+        sr = *(volatile const int32_t *)&cr.st_rows[b];
+        sc = *(volatile const int32_t *)&cr.st_cols[b];
+        pend = *(volatile const int32_t *)&cr.e_pend[b];
+      }
       for (int32_t lt = ((int32_t)blockIdx.x - boff + G) % G; lt < nt; lt += G) {
         const int32_t tr = lt / g.nct, tc = lt - tr * g.nct;
         int64_t r0, c0;
         int nr, nc;
         tile_rows(in, g, b, tr, r0, nr);
         tile_cols(in, g, b, tc, c0, nc);
-        if (in.prec == P_SPLIT)
+        if (in.stored)
+          screen_tile_stored(in, b, r[b], r0, nr, c0, nc, g.te, sr, sc, pend,
+                             in.cand + in.bond[b].cand_base + lt, sm.s);
+        else if (in.prec == P_SPLIT)
           screen_tile_mixed<true>(in, b, r[b], r0, nr, c0, nc, g.te,
                                   in.mcand + in.bond[b].cand_base + lt, sm.s);
         else if (in.prec == P_FP32)
@@ -796,6 +959,21 @@ __device__ void fail_instance(Ctrl &cr, int32_t status) {
   }
 }
 
+// stored-residual form: the rank-one step of eq. aca_approx_E for pivot
+// (a*, c*) of bond b, applied by the next screen to the stored extent:
+//   ew[a] = -(E(a,c*) / E(a*,c*)) (exactly -1 at a*), erow[c] = E(a*,c)
+// (block-wide; E holds this sweep's screen, so the extent is the screen's)
+__device__ void stored_step(const InstDev &in, Ctrl &cr, int b, int64_t as, int64_t cs) {
+  const BondDev &B = in.bond[b];
+  const int64_t ld = B.ldR;
+  const int32_t rows = cr.st_rows[b], cols = cr.st_cols[b];
+  const double piv = B.E[as * ld + cs];
+  for (int32_t a = threadIdx.x; a < rows; a += NT) B.ew[a] = -(B.E[a * ld + cs] / piv);
+  for (int32_t c = threadIdx.x; c < cols; c += NT) B.erow[c] = B.E[as * ld + c];
+  if (threadIdx.x == 0) cr.e_pend[b] = 1;
+  __syncthreads();
+}
+
 // stop test and pivot append for bond b on its merged best (block-wide): add
 // the pivot while the best |E| exceeds tau * rms(X) and the cap allows.  The
 // bond's own rank is the only rank this touches, so bonds decide in parallel.
@@ -813,6 +991,7 @@ __device__ void finalize_bond(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm
   const bool add = v > cr.tau * cr.xrms && v > 0.0 && cr.r[b] < cr.maxr[b];
   bool ok = true;
   if (add) ok = append_pivot(in, cr, b, row, col, sm);
+  if (add && ok && in.stored) stored_step(in, cr, b, row, col);
   if (!ok) fail_instance(cr, 4);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1026,6 +1205,16 @@ __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
     if (b < 0) {
       verify_instance(in, cr, sm.d);
     } else if (in.prec == P_FP64) {
+      if (in.stored) {
+        // the screen just stored every entry of the superblock and applied
+        // the pending rank-one step
+        if (threadIdx.x == 0) {
+          cr.st_rows[b] = cr.plan_rows[b];
+          cr.st_cols[b] = cr.plan_cols[b];
+          cr.e_pend[b] = 0;
+        }
+        __syncthreads();
+      }
       merge_bond_fp64(in, cr, b, sm.d);
       finalize_bond(in, cr, b, sm.d);
     } else {

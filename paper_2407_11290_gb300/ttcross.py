@@ -23,6 +23,8 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_OOM", 3: "ERR_ZERO_START"
 GEN_HILBERT, GEN_TT, GEN_MAXWELLIAN = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_SPLIT, PREC_AUTO = 0, 1, 2, 3
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "split": PREC_SPLIT, "auto": PREC_AUTO}
+RESIDUAL_RECOMPUTE, RESIDUAL_STORED = 0, 1
+RESIDUALS = {"recompute": RESIDUAL_RECOMPUTE, "stored": RESIDUAL_STORED}
 
 # every symbol include/ttcross.h declares
 ABI_SYMBOLS = ("ttcross_default_options", "ttcross_create", "ttcross_run", "ttcross_run_batch",
@@ -56,7 +58,8 @@ class Options(C.Structure):
                 ("topk", C.c_int32),
                 ("host_loop", C.c_int32),
                 ("grid_ctas", C.c_int32),
-                ("wait_limit_s", C.c_double)]
+                ("wait_limit_s", C.c_double),
+                ("residual", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -67,7 +70,8 @@ class Stats(C.Structure):
                 ("tau", C.c_double), ("x_rms", C.c_double), ("err", C.c_double),
                 ("device_ms", C.c_double), ("phase_ms", C.c_double * 6),
                 ("status", C.c_int32),
-                ("device_error_where", C.c_int32)]
+                ("device_error_where", C.c_int32),
+                ("entries_fresh", C.c_int64), ("stored_bytes", C.c_int64)]
 
 
 _lock = threading.Lock()
@@ -148,7 +152,8 @@ class TTCross:
 
     def __init__(self, n, gen, max_rank: int = 64, precision="fp64", nsamples: int = 10**6,
                  seed: int = 20240715, max_refine: int = 6, topk: int = 8, host_loop: bool = False,
-                 grid_ctas: int = 0, wait_limit_s: float = 2.0, bond_max_rank=None):
+                 grid_ctas: int = 0, wait_limit_s: float = 2.0, bond_max_rank=None,
+                 residual="recompute"):
         L = load_library()
         self._L = L
         self.n = np.ascontiguousarray(n, dtype=np.int64)
@@ -163,6 +168,7 @@ class TTCross:
         o.host_loop = 1 if host_loop else 0
         o.grid_ctas = int(grid_ctas)
         o.wait_limit_s = float(wait_limit_s)
+        o.residual = RESIDUALS[residual] if isinstance(residual, str) else int(residual)
         keep = []
         if bond_max_rank is not None:
             bm = _i32(bond_max_rank)

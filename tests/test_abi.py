@@ -32,6 +32,7 @@ def test_default_options_without_gpu():
     o = ttcross.default_options()
     assert o.max_rank == 64 and o.nsamples == 10**6 and o.seed == 20240715
     assert o.wait_limit_s == 2.0 and o.precision == ttcross.PREC_FP64
+    assert o.residual == ttcross.RESIDUAL_RECOMPUTE
 
 
 def test_create_fails_loudly_without_device():
@@ -52,3 +53,21 @@ def test_invalid_arguments_rejected_on_host():
     assert rc == ttcross.ERR_INVALID_ARG
     assert b"d=1" in L.ttcross_last_error_string()
     assert L.ttcross_run(None, 1e-3, 0, None, None) == ttcross.ERR_INVALID_ARG
+
+
+def test_stored_form_option_checked_on_host():
+    L = ttcross.load_library()
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 3)(8, 8, 8)
+    g = ttcross.Generator()
+    g.kind = ttcross.GEN_HILBERT
+    o = ttcross.default_options()
+    o.residual = 5
+    assert L.ttcross_create(3, n, ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)) == \
+        ttcross.ERR_INVALID_ARG
+    o.residual = ttcross.RESIDUAL_STORED
+    o.precision = ttcross.PREC_SPLIT
+    assert L.ttcross_create(3, n, ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)) == \
+        ttcross.ERR_INVALID_ARG
+    assert b"FP64 only" in L.ttcross_last_error_string()
+
