@@ -805,6 +805,93 @@ __device__ __forceinline__ void screen_tile_mixed(const InstDev &in, int b, int 
 // ---------------------------------------------------------------------------
 // phase: screen.  Tiles of every (instance, bond) pair that needs a screen
 // are numbered consecutively; CTA g takes tiles g, g + G, ...
+// Stored-residual instances instead hand out their tiles from a counter,
+// tiles new to a superblock (A - T R, r_k FMAs per entry) first and carried
+// ones (one load, one FMA, one store per entry) after, so that CTAs with a
+// costly tile take fewer cheap ones.  The decide phase after the screen
+// clears the counter.
+
+// carried region of bond b: row tiles < tr0 and column tiles < tc0 lie in
+// the stored extent (its rows / columns are whole prefix / suffix blocks)
+__device__ __forceinline__ void carried_tiles(const InstDev &in, const TileGeo &g, int b,
+                                              int32_t sr, int32_t sc, int32_t &tr0,
+                                              int32_t &tc0) {
+  tr0 = g.pr > 0 ? (sr / (int32_t)in.n[b]) * g.P.tpb : sr / g.te;
+  tc0 = g.pc > 0 ? (sc / (int32_t)in.n[b + 1]) * g.Q.tpb : sc / g.te;
+}
+
+__device__ void screen_stored_instance(const InstDev &in, const int32_t *r, PhaseSmem &sm) {
+  const Ctrl &cr = *in.ctrl;
+  int32_t *ctr = &in.ctrl->steal;
+  // per-bond geometry, stored extent and item counts, staged once
+  __shared__ TileGeo s_geo[TTC_MAXB];
+  __shared__ int32_t s_sr[TTC_MAXB], s_sc[TTC_MAXB], s_pend[TTC_MAXB];
+  __shared__ int32_t s_tr0[TTC_MAXB], s_tc0[TTC_MAXB];
+  __shared__ int32_t s_item;
+  __syncthreads();
+  if (threadIdx.x < in.nb) {
+    const int b = threadIdx.x;
+    const TileGeo g = planned_geo(in, cr, b);
+    const int32_t sr = *(volatile const int32_t *)&cr.st_rows[b];
+    const int32_t sc = *(volatile const int32_t *)&cr.st_cols[b];
+    int32_t tr0, tc0;
+    carried_tiles(in, g, b, sr, sc, tr0, tc0);
+    s_geo[b] = g;
+    s_sr[b] = sr;
+    s_sc[b] = sc;
+    s_pend[b] = *(volatile const int32_t *)&cr.e_pend[b];
+    s_tr0[b] = tr0;
+    s_tc0[b] = tc0;
+  }
+  __syncthreads();
+  int32_t nfresh = 0, ntot = 0;
+  for (int b = 0; b < in.nb; ++b) {
+    const int32_t nt = s_geo[b].nrt * s_geo[b].nct;
+    nfresh += nt - s_tr0[b] * s_tc0[b];
+    ntot += nt;
+  }
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
+    __syncthreads();
+    int32_t j = s_item;
+    __syncthreads();
+    if (j >= ntot) break;
+    // item j -> (bond, tile): fresh items of every bond, then carried ones
+    const bool fresh = j < nfresh;
+    if (!fresh) j -= nfresh;
+    for (int b = 0; b < in.nb; ++b) {
+      const TileGeo &g = s_geo[b];
+      const int32_t tr0 = s_tr0[b], tc0 = s_tc0[b];
+      const int32_t cnt = fresh ? g.nrt * g.nct - tr0 * tc0 : tr0 * tc0;
+      if (j >= cnt) {
+        j -= cnt;
+        continue;
+      }
+      int32_t tr, tc;
+      if (!fresh) {
+        tr = j / tc0;
+        tc = j - tr * tc0;
+      } else if (j < tr0 * (g.nct - tc0)) {
+        // new columns of the stored rows
+        tr = j / (g.nct - tc0);
+        tc = tc0 + (j - tr * (g.nct - tc0));
+      } else {
+        // new rows, every column
+        const int32_t u = j - tr0 * (g.nct - tc0);
+        tr = tr0 + u / g.nct;
+        tc = u - (tr - tr0) * g.nct;
+      }
+      int64_t r0, c0;
+      int nr, nc;
+      tile_rows(in, g, b, tr, r0, nr);
+      tile_cols(in, g, b, tc, c0, nc);
+      screen_tile_stored(in, b, r[b], r0, nr, c0, nc, g.te, s_sr[b], s_sc[b], s_pend[b],
+                         in.cand + in.bond[b].cand_base + tr * g.nct + tc, sm.s);
+      break;
+    }
+  }
+}
+
 __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
   const int32_t G = gridDim.x;
   int64_t base = 0;
@@ -842,25 +929,20 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
       cw.screen_fmas += fmas;
       cw.screened = 1;
     }
+    if (in.stored) {
+      screen_stored_instance(in, r, sm);
+      continue;
+    }
     for (int b = 0; b < in.nb; ++b) {
       const TileGeo g = planned_geo(in, cr, b);
       const int32_t nt = g.nrt * g.nct;
-      int32_t sr = 0, sc = 0, pend = 0;
-      if (in.stored) {
-        sr = *(volatile const int32_t *)&cr.st_rows[b];
-        sc = *(volatile const int32_t *)&cr.st_cols[b];
-        pend = *(volatile const int32_t *)&cr.e_pend[b];
-      }
       for (int32_t lt = ((int32_t)blockIdx.x - boff + G) % G; lt < nt; lt += G) {
         const int32_t tr = lt / g.nct, tc = lt - tr * g.nct;
         int64_t r0, c0;
         int nr, nc;
         tile_rows(in, g, b, tr, r0, nr);
         tile_cols(in, g, b, tc, c0, nc);
-        if (in.stored)
-          screen_tile_stored(in, b, r[b], r0, nr, c0, nc, g.te, sr, sc, pend,
-                             in.cand + in.bond[b].cand_base + lt, sm.s);
-        else if (in.prec == P_SPLIT)
+        if (in.prec == P_SPLIT)
           screen_tile_mixed<true>(in, b, r[b], r0, nr, c0, nc, g.te,
                                   in.mcand + in.bond[b].cand_base + lt, sm.s);
         else if (in.prec == P_FP32)
@@ -1212,6 +1294,7 @@ __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
           cr.st_rows[b] = cr.plan_rows[b];
           cr.st_cols[b] = cr.plan_cols[b];
           cr.e_pend[b] = 0;
+          if (b == 0) cr.steal = 0;  // tile counter of the next screen
         }
         __syncthreads();
       }

@@ -159,3 +159,20 @@ def test_stored_config4_scale_error_and_cost(tt):
         num += (x - v[0, 0]) ** 2
         den += x * x
     assert (num / den) ** 0.5 <= 10 * w["eps"]
+
+
+def test_stored_batch_equals_single(tt):
+    ws = [W.hilbert(3, 20), W.hilbert(4, 11), W.random_tt([6, 7, 8], [1, 2, 3, 1], seed=5)]
+    singles, batch = [], []
+    for w in ws:
+        a = tt.TTCross(w["n"], w["gen"], max_rank=16, nsamples=5000, residual="stored")
+        a.run(1e-9)
+        a.sync()
+        singles.append(a)
+        batch.append(tt.TTCross(w["n"], w["gen"], max_rank=16, nsamples=5000, residual="stored"))
+    tt.run_batch(batch, 1e-9)
+    for a, b in zip(singles, batch):
+        assert b.sync() == a.sync()
+        assert list(a.ranks()) == list(b.ranks())
+        for k in range(1, len(a.n) + 1):
+            np.testing.assert_array_equal(a.core(k), b.core(k))
