@@ -55,6 +55,8 @@ constexpr int TOPK_MAX = 16;
 
 struct DecideSmem {
   double ua[RCAP], bu[RCAP], brow[RCAP];
+  double hcs[RCAP], hps[RCAP];  // R(:, c*) and T(a*, :) of the pivot step
+  double apiv;                  // A(a*, c*)
   int32_t sel[TOPK_MAX];
   uint64_t skey[TOPK_MAX];
   int64_t slin[TOPK_MAX];
@@ -73,6 +75,24 @@ union __align__(16) PhaseSmem {
   DecideSmem d;
   double red[NT / 32];
 };
+
+// The descriptor of instance 0, copied into shared memory when a kernel
+// starts: every phase reads its fields all the time, and from global memory
+// each one is a dependent load at L2 latency.  It does not change during a
+// launch (the host writes it before launching).
+__shared__ InstDev s_inst0;
+
+__device__ void cache_inst0(const RunArgs &ra) {
+  static_assert(sizeof(InstDev) % 8 == 0, "InstDev copies as 8-byte words");
+  const unsigned long long *src = reinterpret_cast<const unsigned long long *>(ra.insts[0]);
+  unsigned long long *dst = reinterpret_cast<unsigned long long *>(&s_inst0);
+  for (int i = threadIdx.x; i < (int)(sizeof(InstDev) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+__device__ __forceinline__ const InstDev &inst(const RunArgs &ra, int ii) {
+  return ii == 0 ? s_inst0 : *ra.insts[ii];
+}
 
 // sampled-error split (defined with the error evaluation below)
 __device__ void choose_split(const InstDev &in, const int32_t *r, int &pL, int &pR);
@@ -897,7 +917,7 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
   int64_t base = 0;
   int32_t boff = 0;  // base mod G
   for (int ii = 0; ii < ra.count; ++ii) {
-    const InstDev &in = *ra.insts[ii];
+    const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
     const int st = *(volatile const int32_t *)&cr.state;
     if (st != ST_SCREEN) continue;
@@ -974,7 +994,8 @@ __device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int
   const int64_t q = cs / nb1, j = cs - q * nb1;
   const SetDev &L = left_set(in, b);
   const SetDev &Rset = right_set(in, b);
-  if (tid == 0) {
+  // warp 1 appends the index sets while warp 0 gathers the history
+  if (tid == 32) {
     const int wl = b, wj = in.d - 1 - b;
     for (int m = 0; m < wl; ++m) B.I.idx[(int64_t)z * (wl + 1) + m] = L.idx[p * wl + m];
     B.I.idx[(int64_t)z * (wl + 1) + wl] = (int32_t)i;
@@ -990,13 +1011,17 @@ __device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int
   double *hc = B.hc + (int64_t)z * cap;
   double *hp = B.hpiv + (int64_t)z * cap;
   for (int t = tid; t < z; t += NT) {
-    hc[t] = B.R[(int64_t)t * B.ldR + cs];
-    hp[t] = B.T[(int64_t)t * B.ldT + as];
+    const double c = B.R[(int64_t)t * B.ldR + cs], q = B.T[(int64_t)t * B.ldT + as];
+    hc[t] = c;
+    hp[t] = q;
+    sm.hcs[t] = c;
+    sm.hps[t] = q;
     sm.brow[t] = sb_entry(in, b, as, B.pcol[t]);
   }
+  if (tid == NT - 1) sm.apiv = sb_entry(in, b, as, cs);
   __syncthreads();
   if (tid == 0) {
-    const double piv = __dsub_rn(sb_entry(in, b, as, cs), chain(hp, 1, hc, 1, z));
+    const double piv = __dsub_rn(sm.apiv, chain(sm.hps, 1, sm.hcs, 1, z));
     const double delta = 1.0 / piv;
     sm.delta = delta;
     sm.flag = isfinite(delta) ? 1 : 0;
@@ -1007,7 +1032,7 @@ __device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int
   const double delta = sm.delta;
   double *U = B.U;
   for (int t = tid; t < z; t += NT) {
-    sm.ua[t] = chain(U + (int64_t)t * cap, 1, hc, 1, z);
+    sm.ua[t] = chain(U + (int64_t)t * cap, 1, sm.hcs, 1, z);
     sm.bu[t] = chain(sm.brow, 1, U + t, cap, z);
   }
   __syncthreads();
@@ -1264,7 +1289,7 @@ template <class F>
 __device__ void for_decide_items(const RunArgs &ra, bool second, F &&f) {
   int64_t j = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
-    const InstDev &in = *ra.insts[ii];
+    const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
     const int st = *(volatile const int32_t *)&cr.state;
     if (st == ST_DONE) continue;
@@ -1282,7 +1307,7 @@ __device__ void for_decide_items(const RunArgs &ra, bool second, F &&f) {
 
 __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
   for_decide_items(ra, false, [&](int ii, int b) {
-    const InstDev &in = *ra.insts[ii];
+    const InstDev &in = inst(ra, ii);
     Ctrl &cr = *in.ctrl;
     if (b < 0) {
       verify_instance(in, cr, sm.d);
@@ -1310,7 +1335,7 @@ __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
 // re-scored candidates; the best is the FP64 argmax of the screen.
 __device__ void phase_decide2(const RunArgs &ra, PhaseSmem &sm) {
   for_decide_items(ra, true, [&](int ii, int b) {
-    const InstDev &in = *ra.insts[ii];
+    const InstDev &in = inst(ra, ii);
     Ctrl &cr = *in.ctrl;
     DecideSmem &d = sm.d;
     const int32_t cnt = cr.nrefine_bond[b];
@@ -1362,14 +1387,32 @@ __device__ __forceinline__ void putR(const InstDev &in, const BondDev &B, int64_
   }
 }
 
+// A(a, c_z) for z < nz: superblock row a of bond b against the columns of
+// its first nz pivots, all issued before any is used (the replay and the row
+// update need them inside serial chains).  Hilbert: the entry is the table
+// value at the row's index sum plus the pivot's J_{>k} index sum.
+__device__ __forceinline__ void pivot_col_entries(const InstDev &in, int b, int64_t a, int z0,
+                                                  int nz, double *ent) {
+  const BondDev &B = in.bond[b];
+  if (in.gen == 0) {
+    const int64_t nb0 = in.n[b];
+    const int64_t p = a / nb0, i = a - p * nb0;
+    const int32_t rs = left_set(in, b).sum[p] + (int32_t)i;
+    for (int z = z0; z < nz; ++z) ent[z - z0] = in.hilb[rs + B.J.sum[z]];
+  } else {
+    for (int z = z0; z < nz; ++z) ent[z - z0] = sb_entry(in, b, a, B.pcol[z]);
+  }
+}
+
 __device__ void replay_row(const InstDev &in, int b, int64_t a, int nz) {
   const BondDev &B = in.bond[b];
-  double Tr[RCAP];
+  double Tr[RCAP], ent[RCAP];
   const int cap = B.cap;
+  pivot_col_entries(in, b, a, 0, nz, ent);
   for (int z = 0; z < nz; ++z) {
     const double *hc = B.hc + (int64_t)z * cap;
     const double *hp = B.hpiv + (int64_t)z * cap;
-    const double s = __dsub_rn(chain(Tr, 1, hc, 1, z), sb_entry(in, b, a, B.pcol[z]));
+    const double s = __dsub_rn(chain(Tr, 1, hc, 1, z), ent[z]);
     const double w = __dmul_rn(B.delta[z], s);
     for (int t = 0; t < z; ++t) Tr[t] = __fma_rn(w, hp[t], Tr[t]);
     Tr[z] = -w;
@@ -1384,9 +1427,11 @@ __device__ void update_row(const InstDev &in, int b, int64_t a, int z) {
   const double *hp = B.hpiv + (int64_t)z * cap;
   double *T = B.T + a;
   const int64_t ld = B.ldT;
+  double ent;
+  pivot_col_entries(in, b, a, z, z + 1, &ent);
   double acc = 0.0;
   for (int t = 0; t < z; ++t) acc = __fma_rn(T[t * ld], hc[t], acc);
-  const double s = __dsub_rn(acc, sb_entry(in, b, a, B.pcol[z]));
+  const double s = __dsub_rn(acc, ent);
   const double w = __dmul_rn(B.delta[z], s);
   for (int t = 0; t < z; ++t) putT(in, B, a + t * ld, __fma_rn(w, hp[t], T[t * ld]));
   putT(in, B, a + (int64_t)z * ld, -w);
@@ -1494,7 +1539,7 @@ __device__ void phase_tables(const RunArgs &ra) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t base = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
-    const InstDev &in = *ra.insts[ii];
+    const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
     if (*(volatile const int32_t *)&cr.state == ST_DONE) continue;
     if (!*(volatile const int32_t *)&cr.screened) continue;
@@ -1619,7 +1664,7 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
   const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
   int64_t base = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
-    const InstDev &in = *ra.insts[ii];
+    const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
     const int st = *(volatile const int32_t *)&cr.state;
     if (st == ST_DONE) continue;
@@ -1702,7 +1747,7 @@ __device__ void phase_init1(const RunArgs &ra, PhaseSmem &sm) {
   const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
   int64_t base = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
-    const InstDev &in = *ra.insts[ii];
+    const InstDev &in = inst(ra, ii);
     double part = 0.0;
     KeyBest best{0ull, LLONG_MAX, -1, -1};
     const int64_t ns = in.nsamples;
@@ -1742,7 +1787,7 @@ __device__ void phase_init1(const RunArgs &ra, PhaseSmem &sm) {
 
 __device__ void phase_init2(const RunArgs &ra, PhaseSmem &sm) {
   for (int ii = blockIdx.x; ii < ra.count; ii += gridDim.x) {
-    const InstDev &in = *ra.insts[ii];
+    const InstDev &in = inst(ra, ii);
     Ctrl &cr = *in.ctrl;
     double part = 0.0;
     KeyBest best{0ull, LLONG_MAX, -1, -1};
@@ -1825,7 +1870,7 @@ __device__ void phase_init3(const RunArgs &ra, PhaseSmem &sm) {
   const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
   int64_t base = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
-    const InstDev &in = *ra.insts[ii];
+    const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
     if (*(volatile const int32_t *)&cr.state == ST_DONE) continue;
     for (int b = 0; b < in.nb; ++b) {
@@ -1851,7 +1896,7 @@ __device__ void phase_refine(const RunArgs &ra, PhaseSmem &sm) {
   const int64_t G = gridDim.x;
   int64_t base = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
-    const InstDev &in = *ra.insts[ii];
+    const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
     if (*(volatile const int32_t *)&cr.state == ST_DONE) continue;
     if (!*(volatile const int32_t *)&cr.screened) continue;
@@ -1884,7 +1929,7 @@ __device__ bool all_done(const RunArgs &ra) {
   if (threadIdx.x == 0) {
     done = 1;
     for (int ii = 0; ii < ra.count; ++ii)
-      if (*(volatile const int32_t *)&ra.insts[ii]->ctrl->state != ST_DONE) done = 0;
+      if (*(volatile const int32_t *)&inst(ra, ii).ctrl->state != ST_DONE) done = 0;
   }
   __syncthreads();
   return done != 0;
@@ -1917,11 +1962,11 @@ __device__ bool any_verify(const RunArgs &ra) {
   if (threadIdx.x == 0) {
     hit = 0;
     for (int ii = 0; ii < ra.count; ++ii) {
-      const Ctrl &cr = *ra.insts[ii]->ctrl;
+      const Ctrl &cr = *inst(ra, ii).ctrl;
       if (*(volatile const int32_t *)&cr.state == ST_DONE) continue;
       if (!*(volatile const int32_t *)&cr.screened) continue;
       int nadd = 0;
-      for (int b = 0; b < ra.insts[ii]->nb; ++b) nadd += *(volatile const int32_t *)&cr.add[b];
+      for (int b = 0; b < inst(ra, ii).nb; ++b) nadd += *(volatile const int32_t *)&cr.add[b];
       if (nadd == 0) hit = 1;
     }
   }
@@ -1931,6 +1976,7 @@ __device__ bool any_verify(const RunArgs &ra) {
 
 __global__ void __launch_bounds__(NT, 2) k_persistent(RunArgs ra) {
   PhaseSmem &sm = *reinterpret_cast<PhaseSmem *>(dyn_smem);
+  cache_inst0(ra);
   PhaseClock clk;
   clk.start();
   phase_init1(ra, sm);
@@ -1972,28 +2018,39 @@ __global__ void __launch_bounds__(NT, 2) k_persistent(RunArgs ra) {
 }
 
 __global__ void __launch_bounds__(NT, 2) k_init1(RunArgs ra) {
+  cache_inst0(ra);
   phase_init1(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
 __global__ void __launch_bounds__(NT, 2) k_init2(RunArgs ra) {
+  cache_inst0(ra);
   phase_init2(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
 __global__ void __launch_bounds__(NT, 2) k_init3(RunArgs ra) {
+  cache_inst0(ra);
   phase_init3(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
 __global__ void __launch_bounds__(NT, 2) k_screen(RunArgs ra) {
+  cache_inst0(ra);
   phase_screen(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
 __global__ void __launch_bounds__(NT, 2) k_decide(RunArgs ra) {
+  cache_inst0(ra);
   phase_decide(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
 __global__ void __launch_bounds__(NT, 2) k_refine(RunArgs ra) {
+  cache_inst0(ra);
   phase_refine(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
 __global__ void __launch_bounds__(NT, 2) k_decide2(RunArgs ra) {
+  cache_inst0(ra);
   phase_decide2(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
-__global__ void __launch_bounds__(NT, 2) k_tables(RunArgs ra) { phase_tables(ra); }
+__global__ void __launch_bounds__(NT, 2) k_tables(RunArgs ra) {
+  cache_inst0(ra);
+  phase_tables(ra);
+}
 __global__ void __launch_bounds__(NT, 2) k_update(RunArgs ra) {
+  cache_inst0(ra);
   phase_update(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
 
