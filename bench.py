@@ -7,8 +7,12 @@ the 6D Hilbert tensor X = 1/(1 + i_1 + ... + i_6), n = 64 per mode
 error on 10^6 seeded random entries.  The tensor is a function of its
 indices, so the inputs are synthetic by construction.
 
+The screen keeps each bond's residual in device memory and carries it
+through every pivot's rank-one step (eq. aca_approx_E); ``--residual
+recompute`` forms A - T R afresh every sweep instead (Alg. 1).
+
 One JSON line on rank 0.  ``--impl reference`` times the CPU oracle (plain C,
-FP64, OpenMP over the host cores) on the same workload.  With ``--gpus N``
+FP64, OpenMP over the host cores) on the same workload and residual form.  With ``--gpus N``
 (under torchrun) every rank runs an independent replica: the path has no
 exchange step on one GPU.
 """
@@ -103,13 +107,15 @@ def measured_peaks():
     return None
 
 
-def cpu_oracle_time(cfg, threads: int, reps: int = 1):
-    """The oracle as it stands, on the host cores: full runs of the workload."""
+def cpu_oracle_time(cfg, threads: int, reps: int = 1, residual: str = "stored"):
+    """The oracle as it stands, on the host cores: full runs of the workload
+    in the same residual form as the GPU line."""
     import oracle
     times = []
     st = None
     for _ in range(reps):
-        o = oracle.Oracle(cfg["n"], cfg["gen"], cfg["max_rank"], nthreads=threads)
+        o = oracle.Oracle(cfg["n"], cfg["gen"], cfg["max_rank"], nthreads=threads,
+                          stored=residual == "stored")
         t0 = time.perf_counter()
         rc, st = o.run(cfg["eps"], nsamples=cfg["nsamples"])
         times.append((time.perf_counter() - t0) * 1e3)
@@ -123,8 +129,8 @@ def bench_reference(args, rank, world):
         return
     cfg = workloads.CONFIGS[args.workload]
     threads = os.cpu_count() or 1
-    warm, _ = cpu_oracle_time(cfg, threads, reps=args.warmup)
-    times, st = cpu_oracle_time(cfg, threads, reps=args.steps)
+    warm, _ = cpu_oracle_time(cfg, threads, reps=args.warmup, residual=args.residual)
+    times, st = cpu_oracle_time(cfg, threads, reps=args.steps, residual=args.residual)
     ms = sum(times) / len(times)
     line = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms",
@@ -133,7 +139,7 @@ def bench_reference(args, rank, world):
         "data": "synthetic (analytic tensor)",
         "config": {"workload": args.workload, "d": len(cfg["n"]), "n": cfg["n"][0],
                    "eps": cfg["eps"], "max_rank": cfg["max_rank"], "nsamples": cfg["nsamples"],
-                   "l2": "n/a (CPU)"},
+                   "residual": args.residual, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": ms, "unit": "ms", "cores": threads, "kind": "oracle",
                          "sample": f"{args.steps} full runs of the workload"},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -267,13 +273,15 @@ def bench_gpu(args, rank, world, local):
                      "frac": achieved / peak, "traffic": None,
                      "peak_source": "measured FP64 FMA loop on this GPU",
                      "kernel": "k_persistent", "kernel_ms": kms,
-                     "algorithmic_fma": algo_fma},
+                     "algorithmic_fma": algo_fma,
+                     "stored_bytes": st["stored_bytes"],
+                     "stored_gbs": st["stored_bytes"] / (kms * 1e-3) / 1e9},
         "clocks": clocks,
         "forms": forms,
     }
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        times, ost = cpu_oracle_time(cfg, threads, reps=1)
+        times, ost = cpu_oracle_time(cfg, threads, reps=1, residual=args.residual)
         line["cpu_baseline"] = {"value": times[0], "unit": "ms", "cores": threads,
                                 "kind": "oracle", "sample": "one full run of the workload",
                                 "err": ost["err"]}
@@ -351,8 +359,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "split", "auto"])
-    ap.add_argument("--residual", default="recompute", choices=["recompute", "stored"],
-                    help="screen form: A - T R every sweep, or the stored residual")
+    ap.add_argument("--residual", default="stored", choices=["recompute", "stored"],
+                    help="screen form: the stored residual of eq. aca_approx_E (default), or "
+                         "A - T R formed every sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP64 vs mixed comparison runs")

@@ -89,14 +89,20 @@ __device__ void maxwellian_table_entry(const InstDev &in, int64_t combo, double 
   *nh = -1.0 / __dmul_rn(2.0, T);
 }
 
+// TT cores or the Maxwellian: one out-of-line copy (each is long, and the
+// callers are many)
+__device__ __noinline__ double gen_other(const InstDev &in, const int32_t *idx) {
+  if (in.gen == 1) return gen_tt(in, idx);
+  return gen_maxwellian_tab(in, idx);
+}
+
 __device__ __forceinline__ double gen_full(const InstDev &in, const int32_t *idx) {
   if (in.gen == 0) {
     int s = 0;
     for (int m = 0; m < in.d; ++m) s += idx[m];
     return in.hilb[s];
   }
-  if (in.gen == 1) return gen_tt(in, idx);
-  return gen_maxwellian_tab(in, idx);
+  return gen_other(in, idx);
 }
 
 // Entry (a, c) of the superblock of bond b: rows a = p*n_b + i (p indexes

@@ -181,6 +181,12 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
+// Control words written by other CTAs earlier in the launch, read from L2:
+// the grid barrier's fence orders the writes before the read, and the L2
+// path skips this SM's L1 (which may hold a stale copy) without the
+// system-scope ordering a volatile access carries.
+__device__ __forceinline__ int32_t ld_cg(const int32_t &x) { return __ldcg(&x); }
+
 // key order: larger |E| first, then smaller linear index
 __device__ __forceinline__ bool key_better(uint64_t k1, int64_t l1, uint64_t k2, int64_t l2) {
   return k1 > k2 || (k1 == k2 && l1 < l2);
@@ -192,11 +198,25 @@ __device__ __forceinline__ uint64_t abs_key(double e) {
 // +Inf bit pattern: keys above it are NaN
 constexpr uint64_t KEY_INF = 0x7FF0000000000000ull;
 
-// The contract's dot product: acc = +0; acc = fma(x[t], y[t], acc), t = 0..K-1
+// The contract's dot product: acc = +0; acc = fma(x[t], y[t], acc), t = 0..K-1.
+// Operands are loaded eight pairs at a time before their FMAs, so a chain
+// over global memory waits for one round trip per eight terms, not per term;
+// the FMAs still run in the serial order t = 0, 1, ...
 __device__ __forceinline__ double chain(const double *x, int64_t sx, const double *y, int64_t sy,
                                         int K) {
   double acc = 0.0;
-  for (int t = 0; t < K; ++t) acc = __fma_rn(x[t * sx], y[t * sy], acc);
+  int t = 0;
+  for (; t + 8 <= K; t += 8) {
+    double xv[8], yv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      xv[k] = x[(t + k) * sx];
+      yv[k] = y[(t + k) * sy];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc = __fma_rn(xv[k], yv[k], acc);
+  }
+  for (; t < K; ++t) acc = __fma_rn(x[t * sx], y[t * sy], acc);
   return acc;
 }
 

@@ -29,6 +29,7 @@ namespace ttc {
 constexpr int NT = 256;  // threads per CTA
 constexpr int KC = 32;   // depth of the T / R chunks staged in shared memory
 
+
 struct ScreenSmem {
   union {
     struct {
@@ -70,9 +71,20 @@ struct DecideSmem {
   int32_t flag;
 };
 
+// pivot history of one bond for the replays (Alg. 4), packed triangles:
+// row z of hc / hpiv (z entries) at z (z - 1) / 2
+constexpr int HIST_SMEM = 2480;   // ranks up to 70
+struct ReplaySmem {
+  double hc[HIST_SMEM], hp[HIST_SMEM];
+  double delta[RCAP];
+  int32_t jsum[RCAP];     // Hilbert: index sums of the pivots' J_{>k} entries
+  int32_t lsum;           // Hilbert: index sum of the chunk's prefix
+};
+
 union __align__(16) PhaseSmem {
   ScreenSmem s;
   DecideSmem d;
+  ReplaySmem h;
   double red[NT / 32];
 };
 
@@ -308,11 +320,11 @@ __device__ void write_plan_warp(const InstDev &in, Ctrl &cr, const int32_t *r, i
 // geometry of bond b as planned (cheap: no tile counting)
 __device__ __forceinline__ TileGeo planned_geo(const InstDev &in, const Ctrl &cr, int b) {
   TileGeo g;
-  g.te = *(volatile const int32_t *)&cr.plan_te;
-  g.rows = *(volatile const int32_t *)&cr.plan_rows[b];
-  g.cols = *(volatile const int32_t *)&cr.plan_cols[b];
-  g.nrt = *(volatile const int32_t *)&cr.plan_nrt[b];
-  g.nct = *(volatile const int32_t *)&cr.plan_nct[b];
+  g.te = ld_cg(cr.plan_te);
+  g.rows = ld_cg(cr.plan_rows[b]);
+  g.cols = ld_cg(cr.plan_cols[b]);
+  g.nrt = ld_cg(cr.plan_nrt[b]);
+  g.nct = ld_cg(cr.plan_nct[b]);
   g.pr = cr.grid[b];
   g.pc = cr.grid[b + 1];
   if (g.pr > 0) g.P = make_pieces((int32_t)in.n[b], g.pr, g.te);
@@ -388,7 +400,7 @@ __device__ void stage_meta(const InstDev &in, int b, int64_t r0, int nr, int64_t
   }
 }
 
-__device__ __forceinline__ double tile_entry(const InstDev &in, const ScreenSmem &sm, int wl, int wr,
+__device__ __noinline__ double tile_entry(const InstDev &in, const ScreenSmem &sm, int wl, int wr,
                                              int rr, int cc) {
   if (in.gen == 0) return in.hilb[sm.srow[rr] + sm.scol[cc]];
   int32_t idx[TTC_MAXD];
@@ -822,6 +834,27 @@ __device__ __forceinline__ void screen_tile_mixed(const InstDev &in, int b, int 
   }
 }
 
+// state, screened, add[b] and r[b] of an instance, each word loaded by its
+// own thread (one L2 round trip instead of a chain of them)
+struct CtrlSnap {
+  int32_t state, screened;
+  int32_t add[TTC_MAXB], r[TTC_MAXB];
+};
+
+__device__ void snap_ctrl(const Ctrl &cr, int nb, CtrlSnap &out) {
+  __syncthreads();
+  const int k = threadIdx.x;
+  if (k == 0)
+    out.state = ld_cg(cr.state);
+  else if (k == 1)
+    out.screened = ld_cg(cr.screened);
+  else if (k < 2 + nb)
+    out.add[k - 2] = ld_cg(cr.add[k - 2]);
+  else if (k < 2 + 2 * nb)
+    out.r[k - 2 - nb] = ld_cg(cr.r[k - 2 - nb]);
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // phase: screen.  Tiles of every (instance, bond) pair that needs a screen
 // are numbered consecutively; CTA g takes tiles g, g + G, ...
@@ -852,14 +885,14 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
   if (threadIdx.x < in.nb) {
     const int b = threadIdx.x;
     const TileGeo g = planned_geo(in, cr, b);
-    const int32_t sr = *(volatile const int32_t *)&cr.st_rows[b];
-    const int32_t sc = *(volatile const int32_t *)&cr.st_cols[b];
+    const int32_t sr = ld_cg(cr.st_rows[b]);
+    const int32_t sc = ld_cg(cr.st_cols[b]);
     int32_t tr0, tc0;
     carried_tiles(in, g, b, sr, sc, tr0, tc0);
     s_geo[b] = g;
     s_sr[b] = sr;
     s_sc[b] = sc;
-    s_pend[b] = *(volatile const int32_t *)&cr.e_pend[b];
+    s_pend[b] = ld_cg(cr.e_pend[b]);
     s_tr0[b] = tr0;
     s_tc0[b] = tc0;
   }
@@ -913,16 +946,17 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
 }
 
 __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
+  __shared__ CtrlSnap snap;
   const int32_t G = gridDim.x;
   int64_t base = 0;
   int32_t boff = 0;  // base mod G
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
-    const int st = *(volatile const int32_t *)&cr.state;
-    if (st != ST_SCREEN) continue;
+    snap_ctrl(cr, in.nb, snap);
+    if (snap.state != ST_SCREEN) continue;
     int32_t r[TTC_MAXD];
-    for (int b = 0; b < in.nb; ++b) r[b] = *(volatile const int32_t *)&cr.r[b];
+    for (int b = 0; b < in.nb; ++b) r[b] = snap.r[b];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       // bookkeeping of this screen
       Ctrl &cw = *in.ctrl;
@@ -953,8 +987,13 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
       screen_stored_instance(in, r, sm);
       continue;
     }
+    // every bond's tile geometry, one bond per thread
+    __shared__ TileGeo s_pg[TTC_MAXB];
+    __syncthreads();
+    if (threadIdx.x < in.nb) s_pg[threadIdx.x] = planned_geo(in, cr, threadIdx.x);
+    __syncthreads();
     for (int b = 0; b < in.nb; ++b) {
-      const TileGeo g = planned_geo(in, cr, b);
+      const TileGeo &g = s_pg[b];
       const int32_t nt = g.nrt * g.nct;
       for (int32_t lt = ((int32_t)blockIdx.x - boff + G) % G; lt < nt; lt += G) {
         const int32_t tr = lt / g.nct, tc = lt - tr * g.nct;
@@ -1291,15 +1330,15 @@ __device__ void for_decide_items(const RunArgs &ra, bool second, F &&f) {
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
-    const int st = *(volatile const int32_t *)&cr.state;
+    const int st = ld_cg(cr.state);
     if (st == ST_DONE) continue;
     if (!second && st == ST_VERIFY) {
       if (j++ % gridDim.x == blockIdx.x) f(ii, -1);
       continue;
     }
-    if (!*(volatile const int32_t *)&cr.screened) continue;
+    if (!ld_cg(cr.screened)) continue;
     for (int b = 0; b < in.nb; ++b) {
-      if (second && !*(volatile const int32_t *)&cr.pending[b]) continue;
+      if (second && !ld_cg(cr.pending[b])) continue;
       if (j++ % gridDim.x == blockIdx.x) f(ii, b);
     }
   }
@@ -1404,20 +1443,80 @@ __device__ __forceinline__ void pivot_col_entries(const InstDev &in, int b, int6
   }
 }
 
-__device__ void replay_row(const InstDev &in, int b, int64_t a, int nz) {
+// Alg. 4 for row a of bond b: eq. aca_approx_T_sub for pivots 0..nz-1 in
+// insertion order.  The history (hc, hpiv rows, delta) comes from shared
+// memory when `packed` (triangles, row z at z (z - 1) / 2), else from the
+// bond's arrays (row z at z * cap).
+__device__ void replay_row(const InstDev &in, int b, int64_t a, int nz,
+                           const double *__restrict__ hcb, const double *__restrict__ hpb,
+                           const double *__restrict__ dl, bool packed,
+                           const int32_t *__restrict__ jsum = nullptr, int32_t rs = 0) {
   const BondDev &B = in.bond[b];
   double Tr[RCAP], ent[RCAP];
   const int cap = B.cap;
-  pivot_col_entries(in, b, a, 0, nz, ent);
+  if (jsum) {
+    // Hilbert, sums staged: independent table lookups
+#pragma unroll 8
+    for (int z = 0; z < nz; ++z) ent[z] = in.hilb[rs + jsum[z]];
+  } else {
+    pivot_col_entries(in, b, a, 0, nz, ent);
+  }
   for (int z = 0; z < nz; ++z) {
-    const double *hc = B.hc + (int64_t)z * cap;
-    const double *hp = B.hpiv + (int64_t)z * cap;
+    const int64_t o = packed ? (int64_t)z * (z - 1) / 2 : (int64_t)z * cap;
+    const double *hc = hcb + o;
+    const double *hp = hpb + o;
     const double s = __dsub_rn(chain(Tr, 1, hc, 1, z), ent[z]);
-    const double w = __dmul_rn(B.delta[z], s);
+    const double w = __dmul_rn(dl[z], s);
     for (int t = 0; t < z; ++t) Tr[t] = __fma_rn(w, hp[t], Tr[t]);
     Tr[z] = -w;
   }
   for (int t = 0; t < nz; ++t) putT(in, B, (int64_t)t * B.ldT + a, Tr[t]);
+}
+
+// the replays of the n_b rows that the new prefix of bond b-1 adds to bond b:
+// chunks of NT rows, one per CTA (chunk g goes to CTA (cbase + g) mod G), the
+// history staged in shared memory once per chunk
+__device__ int32_t replay_chunks(const InstDev &in, int b, int64_t p, int nz, int32_t &cbase,
+                                 PhaseSmem &sm) {
+  const BondDev &B = in.bond[b];
+  const int64_t nit = in.n[b];
+  const int32_t nch = (int32_t)((nit + NT - 1) / NT);
+  const int32_t G = gridDim.x;
+  const bool fits = (int64_t)nz * (nz - 1) / 2 <= HIST_SMEM;
+  for (int32_t ch = (int32_t)(((int64_t)blockIdx.x - cbase) % G + G) % G; ch < nch; ch += G) {
+    if (fits) {
+      __syncthreads();
+      // flat over the triangle: entry k is (z, t) with z (z - 1) / 2 <= k
+      const int tri = nz * (nz - 1) / 2;
+      for (int k = threadIdx.x; k < tri; k += NT) {
+        int z = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)k)) * 0.5f);
+        while (z * (z - 1) / 2 > k) --z;
+        while ((z + 1) * z / 2 <= k) ++z;
+        const int t = k - z * (z - 1) / 2;
+        sm.h.hc[k] = B.hc[(int64_t)z * B.cap + t];
+        sm.h.hp[k] = B.hpiv[(int64_t)z * B.cap + t];
+      }
+      for (int z = threadIdx.x; z < nz; z += NT) {
+        sm.h.delta[z] = B.delta[z];
+        sm.h.jsum[z] = B.J.sum[z];
+      }
+      if (threadIdx.x == 0) sm.h.lsum = left_set(in, b).sum[p];
+      __syncthreads();
+    }
+    const int64_t i = (int64_t)ch * NT + threadIdx.x;
+    if (i < nit) {
+      if (fits && in.gen == 0)
+        replay_row(in, b, p * nit + i, nz, sm.h.hc, sm.h.hp, sm.h.delta, true, sm.h.jsum,
+                   sm.h.lsum + (int32_t)i);
+      else if (fits)
+        replay_row(in, b, p * nit + i, nz, sm.h.hc, sm.h.hp, sm.h.delta, true);
+      else
+        replay_row(in, b, p * nit + i, nz, B.hc, B.hpiv, B.delta, false);
+    }
+  }
+  __syncthreads();  // the staged history is dead before shared memory is reused
+  cbase = (int32_t)(((int64_t)cbase + nch) % G);
+  return nch;
 }
 
 __device__ void update_row(const InstDev &in, int b, int64_t a, int z) {
@@ -1429,9 +1528,7 @@ __device__ void update_row(const InstDev &in, int b, int64_t a, int z) {
   const int64_t ld = B.ldT;
   double ent;
   pivot_col_entries(in, b, a, z, z + 1, &ent);
-  double acc = 0.0;
-  for (int t = 0; t < z; ++t) acc = __fma_rn(T[t * ld], hc[t], acc);
-  const double s = __dsub_rn(acc, ent);
+  const double s = __dsub_rn(chain(T, ld, hc, 1, z), ent);
   const double w = __dmul_rn(B.delta[z], s);
   for (int t = 0; t < z; ++t) putT(in, B, a + t * ld, __fma_rn(w, hp[t], T[t * ld]));
   putT(in, B, a + (int64_t)z * ld, -w);
@@ -1541,13 +1638,13 @@ __device__ void phase_tables(const RunArgs &ra) {
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
-    if (*(volatile const int32_t *)&cr.state == ST_DONE) continue;
-    if (!*(volatile const int32_t *)&cr.screened) continue;
+    if (ld_cg(cr.state) == ST_DONE) continue;
+    if (!ld_cg(cr.screened)) continue;
     int32_t r[TTC_MAXD];
     int nadd = 0;
     for (int b = 0; b < in.nb; ++b) {
-      r[b] = *(volatile const int32_t *)&cr.r[b];
-      nadd += *(volatile const int32_t *)&cr.add[b];
+      r[b] = ld_cg(cr.r[b]);
+      nadd += ld_cg(cr.add[b]);
     }
     if (nadd) continue;
     int pL, pR;
@@ -1660,39 +1757,41 @@ __device__ double sample_residual(const InstDev &in, const int32_t *r, int pL, i
 
 
 __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
+  __shared__ CtrlSnap snap;
   const int64_t NTOT = (int64_t)gridDim.x * NT;
   const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
   int64_t base = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
-    const int st = *(volatile const int32_t *)&cr.state;
-    if (st == ST_DONE) continue;
     // the work follows from the decisions (every CTA reads the same flags;
     // the state word is rewritten by the owner CTA during this phase)
+    snap_ctrl(cr, in.nb, snap);
+    const int st = snap.state;
+    if (st == ST_DONE) continue;
     int32_t ro[TTC_MAXD], rn[TTC_MAXD], ad[TTC_MAXD];
     int nadd = 0;
     for (int b = 0; b < in.nb; ++b) {
-      ad[b] = *(volatile const int32_t *)&cr.add[b];
-      rn[b] = *(volatile const int32_t *)&cr.r[b];
+      ad[b] = snap.add[b];
+      rn[b] = snap.r[b];
       ro[b] = rn[b] - ad[b];
       nadd += ad[b];
     }
-    const bool screened = *(volatile const int32_t *)&cr.screened != 0;
+    const bool screened = snap.screened != 0;
     if (blockIdx.x == ii % gridDim.x && threadIdx.x < 32) {
       if (nadd == 0 && screened && threadIdx.x == 0) in.ctrl->state = ST_VERIFY;
       if (nadd > 0) write_plan_warp(in, *in.ctrl, rn, gridDim.x);  // next screen's tiles
     }
     if (nadd > 0) {
-      // C first: the replays are the longest items
+      // C first: the replays are the longest items, a CTA per NT rows; the
+      // thread-dealt items start on the CTA after the last replay chunk
+      int32_t cbase = (int32_t)((base / NT) % gridDim.x);
+      int64_t nchunks = 0;
       for (int b = 1; b < in.nb; ++b) {
         if (!ad[b - 1]) continue;
-        const int64_t nit = in.n[b];
-        const int64_t p = ro[b - 1];
-        for (int64_t x = first_item(base, gt, NTOT); x < base + nit; x += NTOT)
-          replay_row(in, b, p * in.n[b] + (x - base), rn[b]);
-        base += nit;
+        nchunks += replay_chunks(in, b, ro[b - 1], rn[b], cbase, sm);
       }
+      base += nchunks * NT;
       for (int b = 0; b < in.nb; ++b) {
         const BondDev &B = in.bond[b];
         if (ad[b]) {
@@ -1701,9 +1800,8 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
           for (int64_t x = first_item(base, gt, NTOT); x < base + rows; x += NTOT)
             update_row(in, b, x - base, z);
           base += rows;
-          const int64_t as = B.prow[z];
           for (int64_t x = first_item(base, gt, NTOT); x < base + cols; x += NTOT)
-            putR(in, B, (int64_t)z * B.ldR + (x - base), sb_entry(in, b, as, x - base));
+            putR(in, B, (int64_t)z * B.ldR + (x - base), sb_entry(in, b, B.prow[z], x - base));
           base += cols;
         }
         if (b < in.nb - 1 && ad[b + 1]) {
@@ -1872,7 +1970,7 @@ __device__ void phase_init3(const RunArgs &ra, PhaseSmem &sm) {
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
-    if (*(volatile const int32_t *)&cr.state == ST_DONE) continue;
+    if (ld_cg(cr.state) == ST_DONE) continue;
     for (int b = 0; b < in.nb; ++b) {
       const BondDev &B = in.bond[b];
       const int64_t rows = in.n[b], cols = in.n[b + 1];
@@ -1898,13 +1996,13 @@ __device__ void phase_refine(const RunArgs &ra, PhaseSmem &sm) {
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
-    if (*(volatile const int32_t *)&cr.state == ST_DONE) continue;
-    if (!*(volatile const int32_t *)&cr.screened) continue;
+    if (ld_cg(cr.state) == ST_DONE) continue;
+    if (!ld_cg(cr.screened)) continue;
     int32_t r[TTC_MAXD];
-    for (int b = 0; b < in.nb; ++b) r[b] = *(volatile const int32_t *)&cr.r[b];
+    for (int b = 0; b < in.nb; ++b) r[b] = ld_cg(cr.r[b]);
     for (int b = 0; b < in.nb; ++b) {
-      if (!*(volatile const int32_t *)&cr.pending[b]) continue;
-      const int64_t cnt = *(volatile const int32_t *)&cr.nrefine_bond[b];
+      if (!ld_cg(cr.pending[b])) continue;
+      const int64_t cnt = ld_cg(cr.nrefine_bond[b]);
       const int32_t *list = in.refine_list + 2 * in.bond[b].cand_base;
       Cand *out = in.refine_cand + in.bond[b].cand_base;
       const TileGeo g = planned_geo(in, cr, b);
@@ -1929,7 +2027,7 @@ __device__ bool all_done(const RunArgs &ra) {
   if (threadIdx.x == 0) {
     done = 1;
     for (int ii = 0; ii < ra.count; ++ii)
-      if (*(volatile const int32_t *)&inst(ra, ii).ctrl->state != ST_DONE) done = 0;
+      if (ld_cg(inst(ra, ii).ctrl->state) != ST_DONE) done = 0;
   }
   __syncthreads();
   return done != 0;
@@ -1939,6 +2037,8 @@ __device__ bool all_done(const RunArgs &ra) {
 // kernels
 
 extern __shared__ __align__(16) unsigned char dyn_smem[];
+
+
 
 // CTA 0 accounts the time between barrier exits to the phase that ran
 struct PhaseClock {
@@ -1963,10 +2063,10 @@ __device__ bool any_verify(const RunArgs &ra) {
     hit = 0;
     for (int ii = 0; ii < ra.count; ++ii) {
       const Ctrl &cr = *inst(ra, ii).ctrl;
-      if (*(volatile const int32_t *)&cr.state == ST_DONE) continue;
-      if (!*(volatile const int32_t *)&cr.screened) continue;
+      if (ld_cg(cr.state) == ST_DONE) continue;
+      if (!ld_cg(cr.screened)) continue;
       int nadd = 0;
-      for (int b = 0; b < inst(ra, ii).nb; ++b) nadd += *(volatile const int32_t *)&cr.add[b];
+      for (int b = 0; b < inst(ra, ii).nb; ++b) nadd += ld_cg(cr.add[b]);
       if (nadd == 0) hit = 1;
     }
   }
@@ -2159,5 +2259,6 @@ cudaError_t launch_core(const InstDev *d_inst, int m, double *dst, cudaStream_t 
   k_core<<<152, 256, 0, s>>>(d_inst, m, dst);
   return cudaGetLastError();
 }
+
 
 }  // namespace ttc
