@@ -111,6 +111,10 @@ __device__ __noinline__ double sb_entry(const InstDev &in, int b, int64_t a, int
   const int64_t nb0 = in.n[b], nb1 = in.n[b + 1];
   const int64_t p = a / nb0, i = a - p * nb0;
   const int64_t q = c / nb1, j = c - q * nb1;
+  // outside every superblock this bond can have: no entry (NaN), no access
+  if (a < 0 || c < 0 || (b > 0 && p >= in.bond[b - 1].cap) ||
+      (b < in.nb - 1 && q >= in.bond[b + 1].cap))
+    return __longlong_as_double(0x7FF8000000000000ll);
   const SetDev &L = left_set(in, b);
   const SetDev &Rs = right_set(in, b);
   if (in.gen == 0) return in.hilb[L.sum[p] + (int)i + (int)j + Rs.sum[q]];

@@ -1091,6 +1091,7 @@ __device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int
 
 // FP64 residual of superblock entry (a, c) with the contract's chain
 __device__ double residual64(const InstDev &in, const Ctrl &cr, int b, int64_t a, int64_t c) {
+  if (a < 0 || c < 0) return __longlong_as_double(0x7FF8000000000000ll);  // no entry: NaN
   const BondDev &B = in.bond[b];
   double acc = 0.0;
   for (int t = 0; t < cr.r[b]; ++t)
@@ -1175,6 +1176,9 @@ __device__ void merge_bond_fp64(const InstDev &in, Ctrl &cr, int b, DecideSmem &
 // FP64 argmax, or an equal residual with a lower index) or exceeds theta
 // (otherwise: the tile could hold an entry that must become a pivot).
 __device__ void merge_bond_mixed(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
+  __syncthreads();
+  if (threadIdx.x == 0) sm.flag = 0;
+  __syncthreads();
   const int64_t nt = cr.ntiles[b];
   const MCand *mc = in.mcand + in.bond[b].cand_base;
   int32_t *list = in.refine_list + 2 * in.bond[b].cand_base;
@@ -1182,11 +1186,13 @@ __device__ void merge_bond_mixed(const InstDev &in, Ctrl &cr, int b, DecideSmem 
   // one pass: every thread keeps its k best tiles, the block merges them
   KeyBest loc[TOPK_MAX];
   for (int j = 0; j < k; ++j) loc[j] = KeyBest{0ull, LLONG_MAX, -1, -1};
-  int bad = 0;
+  int bad = 0, badtile = 0;
   for (int64_t t = threadIdx.x; t < nt; t += NT) {
     const float v = mc[t].v;
-    if (mc[t].row < 0 && !(v == v)) {  // never written: count, do not use
-      ++bad;
+    if (mc[t].row < 0) {
+      // never written (NaN sentinel): count, do not use; written without an
+      // entry (every residual of the tile non-finite): the instance fails
+      if (!(v == v)) ++bad; else ++badtile;
       continue;
     }
     KeyBest o{(v == v) ? (uint64_t)__float_as_uint(v) : 0xFFFFFFFFull, mc[t].lin, 0, (int32_t)t};
@@ -1200,6 +1206,7 @@ __device__ void merge_bond_mixed(const InstDev &in, Ctrl &cr, int b, DecideSmem 
     }
   }
   if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
+  if (badtile) atomicExch(&sm.flag, 1);
   for (int j = 0; j < k; ++j) {
     // the block's j-th best: the best head among the threads' lists
     KeyBest head = loc[0];
@@ -1211,6 +1218,18 @@ __device__ void merge_bond_mixed(const InstDev &in, Ctrl &cr, int b, DecideSmem 
       loc[k - 1] = KeyBest{0ull, LLONG_MAX, -1, -1};
     }
     __syncthreads();
+  }
+  if (sm.flag) {
+    // a tile without a finite residual: the FP64 screen would report it
+    fail_instance(cr, 4);  // TTC_ERR_NONFINITE
+    if (threadIdx.x == 0) {
+      cr.best_key[b] = KEY_INF + 1;
+      cr.best_row[b] = -1;
+      cr.nrefine_bond[b] = 0;
+      cr.pending[b] = 1;
+    }
+    __syncthreads();
+    return;
   }
   if (threadIdx.x < k) {
     const int32_t t = sm.sel[threadIdx.x];
