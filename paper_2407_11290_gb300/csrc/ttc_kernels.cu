@@ -1579,16 +1579,19 @@ __device__ __forceinline__ int64_t core_s(const InstDev &in, const int32_t *r, i
 
 // FMAs of the error evaluation with tables of pL / pR modes (the last table
 // level dominates; the chunked build adds its lower levels once per chunk)
+// (in FP32: a cost estimate, identical on every thread; FP64 operations are
+// long-latency on this GPU and every thread evaluates the choice)
 __device__ double split_cost(const InstDev &in, const int32_t *r, int pL, int pR) {
   const int d = in.d;
-  double NL = 1.0, NR = 1.0;
-  for (int m = 0; m < pL; ++m) NL *= (double)in.n[m];
-  for (int m = d - pR; m < d; ++m) NR *= (double)in.n[m];
-  const double tl = pL >= 2 ? NL * core_s(in, r, pL - 1) * core_s(in, r, pL) : 0.0;
-  const double tr = pR >= 2 ? NR * core_s(in, r, d - pR) * core_s(in, r, d - pR + 1) : 0.0;
-  double mid = (double)core_s(in, r, d - pR);
-  for (int m = pL; m < d - pR; ++m) mid += (double)core_s(in, r, m) * core_s(in, r, m + 1);
-  return tl + tr + (double)in.nsamples * mid;
+  float NL = 1.f, NR = 1.f;
+  for (int m = 0; m < pL; ++m) NL *= (float)in.n[m];
+  for (int m = d - pR; m < d; ++m) NR *= (float)in.n[m];
+  const float tl = pL >= 2 ? NL * (float)core_s(in, r, pL - 1) * (float)core_s(in, r, pL) : 0.f;
+  const float tr =
+      pR >= 2 ? NR * (float)core_s(in, r, d - pR) * (float)core_s(in, r, d - pR + 1) : 0.f;
+  float mid = (float)core_s(in, r, d - pR);
+  for (int m = pL; m < d - pR; ++m) mid += (float)core_s(in, r, m) * (float)core_s(in, r, m + 1);
+  return (double)(tl + tr + (float)in.nsamples * mid);
 }
 
 __device__ void choose_split(const InstDev &in, const int32_t *r, int &pL, int &pR) {
@@ -1596,14 +1599,14 @@ __device__ void choose_split(const InstDev &in, const int32_t *r, int &pL, int &
   double best = 1e300;
   pL = 1;
   pR = 1;
-  double NL = 1.0;
+  float NL = 1.f;
   for (int a = 1; a < d; ++a) {
-    NL *= (double)in.n[a - 1];
-    if (a >= 2 && NL * core_s(in, r, a) > (double)in.tabL_cap) break;
-    double NR = 1.0;
+    NL *= (float)in.n[a - 1];
+    if (a >= 2 && NL * (float)core_s(in, r, a) > (float)in.tabL_cap) break;
+    float NR = 1.f;
     for (int c = 1; a + c <= d; ++c) {
-      NR *= (double)in.n[d - c];
-      if (c >= 2 && NR * core_s(in, r, d - c) > (double)in.tabR_cap) break;
+      NR *= (float)in.n[d - c];
+      if (c >= 2 && NR * (float)core_s(in, r, d - c) > (float)in.tabR_cap) break;
       const double cost = split_cost(in, r, a, c);
       if (cost < best) {
         best = cost;
@@ -1615,17 +1618,77 @@ __device__ void choose_split(const InstDev &in, const int32_t *r, int &pL, int &
 }
 
 // v (length s_m) <- v G_m(i) for a middle core 1 <= m <= d-2
+// dst[t] = src[t * s] for t < n, eight loads in flight (a plain copy loop
+// waits for each load before it issues the next)
+__device__ __forceinline__ void copy8(double *dst, const double *src, int64_t s, int n) {
+  int t = 0;
+  for (; t + 8 <= n; t += 8) {
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = src[(int64_t)(t + k) * s];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dst[t + k] = x[k];
+  }
+  for (; t < n; ++t) dst[t] = src[(int64_t)t * s];
+}
+
+// out[o] = sum_p x[p] * col_o[p * s] for o < n, col_o = base + o * so: four
+// outputs at a time, each its own serial FMA chain in p (so the FP64 pipe
+// has four independent chains to overlap instead of one)
+__device__ __forceinline__ void contract4(const double *x, int len, const double *base, int64_t so,
+                                          int64_t s, double *out, int n) {
+  int o = 0;
+  for (; o + 4 <= n; o += 4) {
+    const double *c0 = base + (int64_t)o * so, *c1 = c0 + so, *c2 = c1 + so, *c3 = c2 + so;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int p = 0;
+    for (; p + 4 <= len; p += 4) {
+      // 20 loads in flight, then the 16 FMAs in chain order
+      double xv[4], v0[4], v1[4], v2[4], v3[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t q = (int64_t)(p + k) * s;
+        xv[k] = x[p + k];
+        v0[k] = c0[q];
+        v1[k] = c1[q];
+        v2[k] = c2[q];
+        v3[k] = c3[q];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        a0 = __fma_rn(xv[k], v0[k], a0);
+        a1 = __fma_rn(xv[k], v1[k], a1);
+        a2 = __fma_rn(xv[k], v2[k], a2);
+        a3 = __fma_rn(xv[k], v3[k], a3);
+      }
+    }
+    for (; p < len; ++p) {
+      const double xp = x[p];
+      const int64_t q = (int64_t)p * s;
+      a0 = __fma_rn(xp, c0[q], a0);
+      a1 = __fma_rn(xp, c1[q], a1);
+      a2 = __fma_rn(xp, c2[q], a2);
+      a3 = __fma_rn(xp, c3[q], a3);
+    }
+    out[o] = a0;
+    out[o + 1] = a1;
+    out[o + 2] = a2;
+    out[o + 3] = a3;
+  }
+  for (; o < n; ++o) {
+    const double *c = base + (int64_t)o * so;
+    double a = 0.0;
+    for (int p = 0; p < len; ++p) a = __fma_rn(x[p], c[(int64_t)p * s], a);
+    out[o] = a;
+  }
+}
+
+// v (length s_m) <- v G_m(i) for a middle core 1 <= m <= d-2
 __device__ __forceinline__ int mul_core(const InstDev &in, const int32_t *r, int m, int64_t i,
                                         double *v, double *w) {
   const BondDev &B = in.bond[m];
   const int rl = (int)core_s(in, r, m), rr = (int)core_s(in, r, m + 1);
-  const int64_t nm = in.n[m];
-  for (int u = 0; u < rr; ++u) {
-    const double *col = B.T + (int64_t)u * B.ldT + i;
-    double acc = 0.0;
-    for (int p = 0; p < rl; ++p) acc = __fma_rn(v[p], col[p * nm], acc);
-    w[u] = acc;
-  }
+  contract4(v, rl, B.T + i, B.ldT, in.n[m], w, rr);
   for (int u = 0; u < rr; ++u) v[u] = w[u];
   return rr;
 }
@@ -1635,13 +1698,7 @@ __device__ __forceinline__ int mul_core_right(const InstDev &in, const int32_t *
                                               int64_t i, double *w, double *t) {
   const BondDev &B = in.bond[m];
   const int rl = (int)core_s(in, r, m), rr = (int)core_s(in, r, m + 1);
-  const int64_t nm = in.n[m];
-  for (int p = 0; p < rl; ++p) {
-    const double *row = B.T + (int64_t)p * nm + i;
-    double acc = 0.0;
-    for (int u = 0; u < rr; ++u) acc = __fma_rn(row[(int64_t)u * B.ldT], w[u], acc);
-    t[p] = acc;
-  }
+  contract4(w, rr, B.T + i, in.n[m], B.ldT, t, rl);
   for (int p = 0; p < rl; ++p) w[p] = t[p];
   return rl;
 }
@@ -1686,19 +1743,12 @@ __device__ void phase_tables(const RunArgs &ra) {
         }
         const BondDev &B0 = in.bond[0];
         int len = (int)core_s(in, r, 1);
-        for (int t = 0; t < len; ++t) v[t] = B0.T[(int64_t)t * B0.ldT + idx[0]];
+        copy8(v, B0.T + idx[0], B0.ldT, len);
         for (int m = 1; m < pL - 1; ++m) len = mul_core(in, r, m, idx[m], v, w);
         // last mode of the prefix: core pL-1 (a middle core, pL-1 <= d-2)
         const BondDev &B = in.bond[pL - 1];
-        for (int64_t i = ch * TAB_CHUNK; i < min(nl, (ch + 1) * TAB_CHUNK); ++i) {
-          double *out = in.tabL + (pre + i * np) * sl;
-          for (int u = 0; u < sl; ++u) {
-            const double *col = B.T + (int64_t)u * B.ldT + i;
-            double acc = 0.0;
-            for (int p = 0; p < len; ++p) acc = __fma_rn(v[p], col[p * nl], acc);
-            out[u] = acc;
-          }
-        }
+        for (int64_t i = ch * TAB_CHUNK; i < min(nl, (ch + 1) * TAB_CHUNK); ++i)
+          contract4(v, len, B.T + i, B.ldT, nl, in.tabL + (pre + i * np) * sl, (int)sl);
       }
       base += items;
     }
@@ -1719,18 +1769,11 @@ __device__ void phase_tables(const RunArgs &ra) {
         }
         const BondDev &BL = in.bond[d - 2];
         int len = (int)core_s(in, r, d - 1);
-        for (int t = 0; t < len; ++t) w[t] = BL.R[(int64_t)t * BL.ldR + idx[d - 1]];
+        copy8(w, BL.R + idx[d - 1], BL.ldR, len);
         for (int m = d - 2; m > mf; --m) len = mul_core_right(in, r, m, idx[m], w, v);
         const BondDev &B = in.bond[mf];
-        for (int64_t i = ch * TAB_CHUNK; i < min(nf, (ch + 1) * TAB_CHUNK); ++i) {
-          double *out = in.tabR + (i + nf * suf) * sr;
-          for (int p = 0; p < sr; ++p) {
-            const double *row = B.T + (int64_t)p * nf + i;
-            double acc = 0.0;
-            for (int u = 0; u < len; ++u) acc = __fma_rn(row[(int64_t)u * B.ldT], w[u], acc);
-            out[p] = acc;
-          }
-        }
+        for (int64_t i = ch * TAB_CHUNK; i < min(nf, (ch + 1) * TAB_CHUNK); ++i)
+          contract4(w, len, B.T + i, nf, B.ldT, in.tabR + (i + nf * suf) * sr, (int)sr);
       }
       base += items;
     }
@@ -1744,6 +1787,8 @@ __device__ double sample_residual(const InstDev &in, const int32_t *r, int pL, i
   double v[RCAP], w[RCAP];
   const int d = in.d;
   int len;
+  const double *src;   // the prefix vector in memory (stride sv)
+  int64_t sv;
   if (pL >= 2) {
     int64_t e = 0, st = 1;
     for (int m = 0; m < pL; ++m) {
@@ -1751,14 +1796,21 @@ __device__ double sample_residual(const InstDev &in, const int32_t *r, int pL, i
       st *= in.n[m];
     }
     len = (int)core_s(in, r, pL);
-    const double *src = in.tabL + e * len;
-    for (int t = 0; t < len; ++t) v[t] = src[t];
+    src = in.tabL + e * len;
+    sv = 1;
   } else {
     const BondDev &B0 = in.bond[0];
     len = (int)core_s(in, r, 1);
-    for (int t = 0; t < len; ++t) v[t] = B0.T[(int64_t)t * B0.ldT + idx[0]];
+    src = B0.T + idx[0];
+    sv = B0.ldT;
   }
-  for (int m = pL; m < d - pR; ++m) len = mul_core(in, r, m, idx[m], v, w);
+  if (pL + pR < d) {
+    // middle cores: the vector goes to local memory
+    copy8(v, src, sv, len);
+    for (int m = pL; m < d - pR; ++m) len = mul_core(in, r, m, idx[m], v, w);
+    src = v;
+    sv = 1;
+  }
   double xt;
   if (pR >= 2) {
     int64_t e = 0, st = 1;
@@ -1766,10 +1818,10 @@ __device__ double sample_residual(const InstDev &in, const int32_t *r, int pL, i
       e += idx[m] * st;
       st *= in.n[m];
     }
-    xt = chain(v, 1, in.tabR + e * len, 1, len);
+    xt = chain(src, sv, in.tabR + e * len, 1, len);
   } else {
     const BondDev &BL = in.bond[d - 2];
-    xt = chain(v, 1, BL.R + idx[d - 1], BL.ldR, len);
+    xt = chain(src, sv, BL.R + idx[d - 1], BL.ldR, len);
   }
   return __dsub_rn(in.xs[k], xt);
 }
