@@ -1070,9 +1070,12 @@ __device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int
   if (!sm.flag) return false;
   const double delta = sm.delta;
   double *U = B.U;
-  for (int t = tid; t < z; t += NT) {
-    sm.ua[t] = chain(U + (int64_t)t * cap, 1, sm.hcs, 1, z);
-    sm.bu[t] = chain(sm.brow, 1, U + t, cap, z);
+  // U a and b U side by side: lanes [0, z) take the rows, [z, 2z) the columns
+  for (int x = tid; x < 2 * z; x += NT) {
+    if (x < z)
+      sm.ua[x] = chain(U + (int64_t)x * cap, 1, sm.hcs, 1, z);
+    else
+      sm.bu[x - z] = chain(sm.brow, 1, U + (x - z), cap, z);
   }
   __syncthreads();
   for (int x = tid; x < z * z; x += NT) {
@@ -1107,18 +1110,12 @@ __device__ void fail_instance(Ctrl &cr, int32_t status) {
 }
 
 // stored-residual form: the rank-one step of eq. aca_approx_E for pivot
-// (a*, c*) of bond b, applied by the next screen to the stored extent:
-//   ew[a] = -(E(a,c*) / E(a*,c*)) (exactly -1 at a*), erow[c] = E(a*,c)
-// (block-wide; E holds this sweep's screen, so the extent is the screen's)
-__device__ void stored_step(const InstDev &in, Ctrl &cr, int b, int64_t as, int64_t cs) {
-  const BondDev &B = in.bond[b];
-  const int64_t ld = B.ldR;
-  const int32_t rows = cr.st_rows[b], cols = cr.st_cols[b];
-  const double piv = B.E[as * ld + cs];
-  for (int32_t a = threadIdx.x; a < rows; a += NT) B.ew[a] = -(B.E[a * ld + cs] / piv);
-  for (int32_t c = threadIdx.x; c < cols; c += NT) B.erow[c] = B.E[as * ld + c];
+// (a*, c*) of bond b is applied by the next screen to the stored extent:
+//   ew[a] = -(E(a,c*) / E(a*,c*)) (exactly -1 at a*), erow[c] = E(a*,c);
+// the decide phase only marks it pending, the update phase (every CTA, as
+// thread items) fills ew and erow from E, which the screen left unchanged
+__device__ void stored_step(Ctrl &cr, int b) {
   if (threadIdx.x == 0) cr.e_pend[b] = 1;
-  __syncthreads();
 }
 
 // stop test and pivot append for bond b on its merged best (block-wide): add
@@ -1138,7 +1135,7 @@ __device__ void finalize_bond(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm
   const bool add = v > cr.tau * cr.xrms && v > 0.0 && cr.r[b] < cr.maxr[b];
   bool ok = true;
   if (add) ok = append_pivot(in, cr, b, row, col, sm);
-  if (add && ok && in.stored) stored_step(in, cr, b, row, col);
+  if (add && ok && in.stored) stored_step(cr, b);
   if (!ok) fail_instance(cr, 4);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1865,6 +1862,18 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
       base += nchunks * NT;
       for (int b = 0; b < in.nb; ++b) {
         const BondDev &B = in.bond[b];
+        if (ad[b] && in.stored) {
+          // the pending rank-one step of the stored residual (from the
+          // sweep-start superblock, which E still holds)
+          const int64_t rows = rows_of(in, ro, b), cols = cols_of(in, ro, b);
+          const int64_t ld = B.ldR, as = B.prow[ro[b]], cs = B.pcol[ro[b]];
+          for (int64_t x = first_item(base, gt, NTOT); x < base + rows; x += NTOT)
+            B.ew[x - base] = -(B.E[(x - base) * ld + cs] / B.E[as * ld + cs]);
+          base += rows;
+          for (int64_t x = first_item(base, gt, NTOT); x < base + cols; x += NTOT)
+            B.erow[x - base] = B.E[as * ld + (x - base)];
+          base += cols;
+        }
         if (ad[b]) {
           const int z = ro[b];
           const int64_t rows = rows_of(in, ro, b), cols = cols_of(in, ro, b);
