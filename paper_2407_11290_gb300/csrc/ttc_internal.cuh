@@ -186,6 +186,13 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 // path skips this SM's L1 (which may hold a stale copy) without the
 // system-scope ordering a volatile access carries.
 __device__ __forceinline__ int32_t ld_cg(const int32_t &x) { return __ldcg(&x); }
+__device__ __forceinline__ int64_t ld_cg(const int64_t &x) {
+  return (int64_t)__ldcg(reinterpret_cast<const long long *>(&x));
+}
+__device__ __forceinline__ uint64_t ld_cg(const uint64_t &x) {
+  return (uint64_t)__ldcg(reinterpret_cast<const unsigned long long *>(&x));
+}
+__device__ __forceinline__ double ld_cg(const double &x) { return __ldcg(&x); }
 
 // key order: larger |E| first, then smaller linear index
 __device__ __forceinline__ bool key_better(uint64_t k1, int64_t l1, uint64_t k2, int64_t l2) {

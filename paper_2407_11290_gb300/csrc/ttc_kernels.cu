@@ -962,15 +962,16 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
       Ctrl &cw = *in.ctrl;
       int64_t entries = 0, fmas = 0, fresh = 0, bytes = 0;
       for (int b = 0; b < in.nb; ++b) {
-        cw.ntiles[b] = cw.plan_nrt[b] * cw.plan_nct[b];
-        const int64_t e = (int64_t)cw.plan_rows[b] * cw.plan_cols[b];
+        cw.ntiles[b] = ld_cg(cw.plan_nrt[b]) * ld_cg(cw.plan_nct[b]);
+        const int64_t e = (int64_t)ld_cg(cw.plan_rows[b]) * ld_cg(cw.plan_cols[b]);
         entries += e;
         if (in.stored) {
           // carried entries cost one FMA when a rank-one step is pending
-          const int64_t kept = (int64_t)cw.st_rows[b] * cw.st_cols[b];
+          const int64_t kept = (int64_t)ld_cg(cw.st_rows[b]) * ld_cg(cw.st_cols[b]);
+          const int32_t pend = ld_cg(cw.e_pend[b]);
           fresh += e - kept;
-          fmas += (e - kept) * r[b] + (cw.e_pend[b] ? kept : 0);
-          bytes += 8 * e + (cw.e_pend[b] ? 8 * kept : 0);
+          fmas += (e - kept) * r[b] + (pend ? kept : 0);
+          bytes += 8 * e + (pend ? 8 * kept : 0);
         } else {
           fresh += e;
           fmas += e * r[b];
@@ -1025,7 +1026,7 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
 __device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int64_t cs,
                              DecideSmem &sm) {
   const BondDev &B = in.bond[b];
-  const int z = cr.r[b];
+  const int z = ld_cg(cr.r[b]);
   const int cap = B.cap;
   const int tid = threadIdx.x;
   const int64_t nb0 = in.n[b], nb1 = in.n[b + 1];
@@ -1097,7 +1098,8 @@ __device__ double residual64(const InstDev &in, const Ctrl &cr, int b, int64_t a
   if (a < 0 || c < 0) return __longlong_as_double(0x7FF8000000000000ll);  // no entry: NaN
   const BondDev &B = in.bond[b];
   double acc = 0.0;
-  for (int t = 0; t < cr.r[b]; ++t)
+  const int K = ld_cg(cr.r[b]);
+  for (int t = 0; t < K; ++t)
     acc = __fma_rn(B.T[(int64_t)t * B.ldT + a], B.R[(int64_t)t * B.ldR + c], acc);
   return __dsub_rn(sb_entry(in, b, a, c), acc);
 }
@@ -1122,8 +1124,8 @@ __device__ void stored_step(Ctrl &cr, int b) {
 // the pivot while the best |E| exceeds tau * rms(X) and the cap allows.  The
 // bond's own rank is the only rank this touches, so bonds decide in parallel.
 __device__ void finalize_bond(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
-  const uint64_t key = cr.best_key[b];
-  const int32_t row = cr.best_row[b], col = cr.best_col[b];
+  const uint64_t key = ld_cg(cr.best_key[b]);
+  const int32_t row = ld_cg(cr.best_row[b]), col = ld_cg(cr.best_col[b]);
   __syncthreads();
   if (key > KEY_INF || row < 0) {
     fail_instance(cr, 4);  // TTC_ERR_NONFINITE
@@ -1132,7 +1134,8 @@ __device__ void finalize_bond(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm
     return;
   }
   const double v = __longlong_as_double((long long)key);
-  const bool add = v > cr.tau * cr.xrms && v > 0.0 && cr.r[b] < cr.maxr[b];
+  const int32_t rb = ld_cg(cr.r[b]);
+  const bool add = v > ld_cg(cr.tau) * ld_cg(cr.xrms) && v > 0.0 && rb < ld_cg(cr.maxr[b]);
   bool ok = true;
   if (add) ok = append_pivot(in, cr, b, row, col, sm);
   if (add && ok && in.stored) stored_step(cr, b);
@@ -1140,14 +1143,14 @@ __device__ void finalize_bond(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm
   __syncthreads();
   if (threadIdx.x == 0) {
     cr.add[b] = (add && ok) ? 1 : 0;
-    cr.r[b] += (add && ok) ? 1 : 0;
+    cr.r[b] = rb + ((add && ok) ? 1 : 0);
   }
   __syncthreads();
 }
 
 // FP64 form: merge the tile candidates of bond b (the Allgather of Alg. 3)
 __device__ void merge_bond_fp64(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
-  const int64_t nt = cr.ntiles[b];
+  const int64_t nt = ld_cg(cr.ntiles[b]);
   KeyBest best{0ull, LLONG_MAX, -1, -1};
   const Cand *cand = in.cand + in.bond[b].cand_base;
   int bad = 0;
@@ -1176,7 +1179,7 @@ __device__ void merge_bond_mixed(const InstDev &in, Ctrl &cr, int b, DecideSmem 
   __syncthreads();
   if (threadIdx.x == 0) sm.flag = 0;
   __syncthreads();
-  const int64_t nt = cr.ntiles[b];
+  const int64_t nt = ld_cg(cr.ntiles[b]);
   const MCand *mc = in.mcand + in.bond[b].cand_base;
   int32_t *list = in.refine_list + 2 * in.bond[b].cand_base;
   const int k = (int)min((int64_t)min(in.topk, TOPK_MAX), nt);
@@ -1251,7 +1254,7 @@ __device__ void merge_bond_mixed(const InstDev &in, Ctrl &cr, int b, DecideSmem 
     kb_take(vb, o);
   }
   const double vstar = __longlong_as_double((long long)(vb.key > KEY_INF ? KEY_INF : vb.key));
-  const double theta = cr.tau * cr.xrms;
+  const double theta = ld_cg(cr.tau) * ld_cg(cr.xrms);
   const bool strict = !(vstar > theta);
   const double thr = strict ? theta : vstar;
   const double g = 1.0 + 4.0 * 5.9604644775390625e-8;
@@ -1288,11 +1291,13 @@ __device__ void verify_instance(const InstDev &in, Ctrl &cr, DecideSmem &sm) {
   const double num = block_sum(part, sm.red);
   if (threadIdx.x == 0) {
     cr.screened = 0;
-    const double err = sqrt(num / cr.den);
+    const double err = sqrt(num / ld_cg(cr.den));
     cr.err = err;
     int pL, pR;
-    choose_split(in, cr.r, pL, pR);
-    cr.error_fmas += (int64_t)split_cost(in, cr.r, pL, pR);
+    int32_t rr[TTC_MAXD];
+    for (int b = 0; b < in.nb; ++b) rr[b] = ld_cg(cr.r[b]);
+    choose_split(in, rr, pL, pR);
+    cr.error_fmas += (int64_t)split_cost(in, rr, pL, pR);
     for (int b = 0; b < in.nb; ++b) cr.add[b] = 0;
     sm.flag = 0;
     if (!isfinite(err)) {
@@ -1312,14 +1317,14 @@ __device__ void verify_instance(const InstDev &in, Ctrl &cr, DecideSmem &sm) {
     if (threadIdx.x == 0) {
       bool capped = true;
       for (int b = 0; b < in.nb; ++b)
-        if (cr.r[b] < cr.maxr[b]) capped = false;
-      if (capped || cr.refinements >= cr.max_refine) {
+        if (ld_cg(cr.r[b]) < ld_cg(cr.maxr[b])) capped = false;
+      if (capped || ld_cg(cr.refinements) >= ld_cg(cr.max_refine)) {
         cr.status = 7;  // TTC_NOT_CONVERGED
         cr.state = ST_DONE;
         sm.flag = 0;
       } else {
-        cr.tau = cr.tau / 10.0;
-        cr.refinements += 1;
+        cr.tau = ld_cg(cr.tau) / 10.0;
+        cr.refinements = ld_cg(cr.refinements) + 1;
         cr.state = ST_SCREEN;
         // the mixed forms certified their bests only against the old
         // threshold: they screen again
@@ -1371,8 +1376,8 @@ __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
         // the screen just stored every entry of the superblock and applied
         // the pending rank-one step
         if (threadIdx.x == 0) {
-          cr.st_rows[b] = cr.plan_rows[b];
-          cr.st_cols[b] = cr.plan_cols[b];
+          cr.st_rows[b] = ld_cg(cr.plan_rows[b]);
+          cr.st_cols[b] = ld_cg(cr.plan_cols[b]);
           cr.e_pend[b] = 0;
           if (b == 0) cr.steal = 0;  // tile counter of the next screen
         }
@@ -1393,9 +1398,10 @@ __device__ void phase_decide2(const RunArgs &ra, PhaseSmem &sm) {
     const InstDev &in = inst(ra, ii);
     Ctrl &cr = *in.ctrl;
     DecideSmem &d = sm.d;
-    const int32_t cnt = cr.nrefine_bond[b];
+    const int32_t cnt = ld_cg(cr.nrefine_bond[b]);
     const Cand *rc = in.refine_cand + in.bond[b].cand_base;
-    KeyBest best{cr.best_key[b], cr.best_lin[b], cr.best_row[b], cr.best_col[b]};
+    KeyBest best{ld_cg(cr.best_key[b]), ld_cg(cr.best_lin[b]), ld_cg(cr.best_row[b]),
+                 ld_cg(cr.best_col[b])};
     int bad = 0;
     for (int32_t t = threadIdx.x; t < cnt; t += NT) {
       KeyBest o{rc[t].key, rc[t].lin, rc[t].row, rc[t].col};
