@@ -103,6 +103,7 @@ ttc_status ensure_cands(ttc_handle *h, const int32_t *grid) {
     // 64 x 64 tiles at the rank caps, and room for the 32 x 32 tiles the
     // kernels switch to when a sweep has fewer than two waves of tiles
     need[b] = std::max<int64_t>(cand_need(h, b, grid), 8192);
+    if (h->hi.stored) need[b] *= 4;  // candidate slots per tile in the stored form
     if (need[b] > h->bond_cand_cap[b]) grow = true;
   }
   if (!grow && h->cand) return TTC_OK;

@@ -53,6 +53,9 @@ struct ScreenSmem {
 };
 
 constexpr int TOPK_MAX = 16;
+// stored-residual form: candidate slots per tile (the quarters of a fresh tile;
+// a carried tile uses the first and marks the rest empty, row -2)
+constexpr int STORED_SLOTS = 4;
 
 struct DecideSmem {
   double ua[RCAP], bu[RCAP], brow[RCAP];
@@ -293,9 +296,23 @@ __device__ void write_plan_warp(const InstDev &in, Ctrl &cr, const int32_t *r, i
     t64 += __shfl_xor_sync(0xffffffffu, t64, off);
     kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, off));
   }
+  // pieces of the subtensor grid at most 32 wide on every bond: a 64-wide
+  // tile would hold one piece and compute three quarters padding; 32 x 32
+  // tiles give the same tiles without it (FP64 forms)
+  int small = 1;
+  if (act) {
+    const int64_t pr = cr.grid[lane], pc = cr.grid[lane + 1];
+    const int64_t sr = pr > 0 ? (in.n[lane] + pr - 1) / pr : 64;
+    const int64_t sc = pc > 0 ? (in.n[lane + 1] + pc - 1) / pc : 64;
+    small = sr <= 32 && sc <= 32;
+  }
+  const bool pieces32 = __all_sync(0xffffffffu, small) && in.prec == P_FP64;
   int te = 64;
   TileGeo g = g64;
-  if (!in.stored && 4 * t64 < (int64_t)grid && kmax >= 24) {
+  if (pieces32) {
+    te = 32;
+    if (act) g = tile_geo_e(in, cr, r, lane, 32);
+  } else if (!in.stored && in.prec == P_FP64 && 4 * t64 < (int64_t)grid && kmax >= 24) {
     // 32 x 32 tiles when the candidate slots of every bond allow them
     int ok = 1;
     if (act) {
@@ -873,6 +890,38 @@ __device__ __forceinline__ void carried_tiles(const InstDev &in, const TileGeo &
   tc0 = g.pc > 0 ? (sc / (int32_t)in.n[b + 1]) * g.Q.tpb : sc / g.te;
 }
 
+// bookkeeping of a screen (one thread, from the CTA's staged geometry):
+// candidate slots per bond for the merge, and the statistics.  Stored form:
+// sr / sc / pend are the stored extents and pending steps, spt the slots per
+// tile; recompute form: sr = sc = null.
+__device__ void screen_bookkeeping(const InstDev &in, const int32_t *r, const TileGeo *geo,
+                                   const int32_t *sr, const int32_t *sc, const int32_t *pend,
+                                   int32_t spt) {
+  Ctrl &cw = *in.ctrl;
+  int64_t entries = 0, fmas = 0, fresh = 0, bytes = 0;
+  for (int b = 0; b < in.nb; ++b) {
+    cw.ntiles[b] = geo[b].nrt * geo[b].nct * spt;
+    const int64_t e = (int64_t)geo[b].rows * geo[b].cols;
+    entries += e;
+    if (sr) {
+      // carried entries cost one FMA when a rank-one step is pending
+      const int64_t kept = (int64_t)sr[b] * sc[b];
+      fresh += e - kept;
+      fmas += (e - kept) * r[b] + (pend[b] ? kept : 0);
+      bytes += 8 * e + (pend[b] ? 8 * kept : 0);
+    } else {
+      fresh += e;
+      fmas += e * r[b];
+    }
+  }
+  cw.sweeps += 1;
+  cw.entries += entries;
+  cw.entries_fresh += fresh;
+  cw.stored_bytes += bytes;
+  cw.screen_fmas += fmas;
+  cw.screened = 1;
+}
+
 __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, PhaseSmem &sm) {
   const Ctrl &cr = *in.ctrl;
   int32_t *ctr = &in.ctrl->steal;
@@ -897,21 +946,34 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
     s_tc0[b] = tc0;
   }
   __syncthreads();
-  int32_t nfresh = 0, ntot = 0;
+  // with fewer fresh tiles than CTAs, fresh tiles go out as quarters
+  // (32 x 32) so that their FP64 work spreads over four times as many CTAs;
+  // candidate slots are then STORED_SLOTS per tile, else one
+  int32_t nf = 0, ncar = 0;
   for (int b = 0; b < in.nb; ++b) {
-    const int32_t nt = s_geo[b].nrt * s_geo[b].nct;
-    nfresh += nt - s_tr0[b] * s_tc0[b];
-    ntot += nt;
+    const int32_t nt = s_geo[b].nrt * s_geo[b].nct, nc = s_tr0[b] * s_tc0[b];
+    nf += nt - nc;
+    ncar += nc;
   }
+  const bool quarters = s_geo[0].te == 64 && nf < (int32_t)gridDim.x;
+  const int32_t spt = quarters ? STORED_SLOTS : 1;  // slots per tile
+  const int32_t nfresh = spt * nf, ntot = nfresh + ncar;
+  if (blockIdx.x == 0 && threadIdx.x == 0) screen_bookkeeping(in, r, s_geo, s_sr, s_sc, s_pend, spt);
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
     __syncthreads();
     int32_t j = s_item;
     __syncthreads();
     if (j >= ntot) break;
-    // item j -> (bond, tile): fresh items of every bond, then carried ones
+    // item j -> (bond, tile): fresh quarters of every bond, then carried tiles
     const bool fresh = j < nfresh;
-    if (!fresh) j -= nfresh;
+    int32_t q = 0;
+    if (fresh) {
+      q = j % spt;
+      j /= spt;
+    } else {
+      j -= nfresh;
+    }
     for (int b = 0; b < in.nb; ++b) {
       const TileGeo &g = s_geo[b];
       const int32_t tr0 = s_tr0[b], tc0 = s_tc0[b];
@@ -938,8 +1000,22 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
       int nr, nc;
       tile_rows(in, g, b, tr, r0, nr);
       tile_cols(in, g, b, tc, c0, nc);
-      screen_tile_stored(in, b, r[b], r0, nr, c0, nc, g.te, s_sr[b], s_sc[b], s_pend[b],
-                         in.cand + in.bond[b].cand_base + tr * g.nct + tc, sm.s);
+      Cand *slot = in.cand + in.bond[b].cand_base + (int64_t)(tr * g.nct + tc) * spt;
+      if (fresh && quarters) {
+        // quarter q of the tile: rows / columns [32 qr, 32 qr + 32)
+        const int h = g.te / 2, qr = q >> 1, qc = q & 1;
+        const int nrq = min(h, nr - h * qr), ncq = min(h, nc - h * qc);
+        if (nrq > 0 && ncq > 0)
+          screen_tile_stored(in, b, r[b], r0 + h * qr, nrq, c0 + h * qc, ncq, h, s_sr[b],
+                             s_sc[b], s_pend[b], slot + q, sm.s);
+        else if (threadIdx.x == 0)
+          slot[q] = Cand{0ull, LLONG_MAX, -2, -2};  // an empty quarter
+      } else {
+        screen_tile_stored(in, b, r[b], r0, nr, c0, nc, g.te, s_sr[b], s_sc[b], s_pend[b],
+                           slot, sm.s);
+        if (threadIdx.x == 0)
+          for (int k = 1; k < spt; ++k) slot[k] = Cand{0ull, LLONG_MAX, -2, -2};
+      }
       break;
     }
   }
@@ -957,33 +1033,6 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
     if (snap.state != ST_SCREEN) continue;
     int32_t r[TTC_MAXD];
     for (int b = 0; b < in.nb; ++b) r[b] = snap.r[b];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      // bookkeeping of this screen
-      Ctrl &cw = *in.ctrl;
-      int64_t entries = 0, fmas = 0, fresh = 0, bytes = 0;
-      for (int b = 0; b < in.nb; ++b) {
-        cw.ntiles[b] = ld_cg(cw.plan_nrt[b]) * ld_cg(cw.plan_nct[b]);
-        const int64_t e = (int64_t)ld_cg(cw.plan_rows[b]) * ld_cg(cw.plan_cols[b]);
-        entries += e;
-        if (in.stored) {
-          // carried entries cost one FMA when a rank-one step is pending
-          const int64_t kept = (int64_t)ld_cg(cw.st_rows[b]) * ld_cg(cw.st_cols[b]);
-          const int32_t pend = ld_cg(cw.e_pend[b]);
-          fresh += e - kept;
-          fmas += (e - kept) * r[b] + (pend ? kept : 0);
-          bytes += 8 * e + (pend ? 8 * kept : 0);
-        } else {
-          fresh += e;
-          fmas += e * r[b];
-        }
-      }
-      cw.sweeps += 1;
-      cw.entries += entries;
-      cw.entries_fresh += fresh;
-      cw.stored_bytes += bytes;
-      cw.screen_fmas += fmas;
-      cw.screened = 1;
-    }
     if (in.stored) {
       screen_stored_instance(in, r, sm);
       continue;
@@ -993,6 +1042,8 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
     __syncthreads();
     if (threadIdx.x < in.nb) s_pg[threadIdx.x] = planned_geo(in, cr, threadIdx.x);
     __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+      screen_bookkeeping(in, r, s_pg, nullptr, nullptr, nullptr, 1);
     for (int b = 0; b < in.nb; ++b) {
       const TileGeo &g = s_pg[b];
       const int32_t nt = g.nrt * g.nct;
@@ -1156,7 +1207,7 @@ __device__ void merge_bond_fp64(const InstDev &in, Ctrl &cr, int b, DecideSmem &
   int bad = 0;
   for (int64_t t = threadIdx.x; t < nt; t += NT) {
     KeyBest o{cand[t].key, cand[t].lin, cand[t].row, cand[t].col};
-    bad += o.row < 0;
+    bad += o.row == -1;  // -2 marks a slot left empty on purpose
     kb_take(best, o);
   }
   if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
