@@ -103,7 +103,8 @@ typedef enum {
 } ttc_residual;
 
 typedef struct {
-  int32_t max_rank;         /* rank capacity of every bond (default 64, <= 128) */
+  int32_t max_rank;         /* rank capacity of every bond (default 64, <= 256); the
+                               superblock extents cap * n must stay below 2^31 */
   const int32_t *bond_max_rank; /* nullable host array of d-1 per-bond rank caps
                                (prescribed ranks, e.g. (15,17,18,17,15)); copied */
   int32_t precision;        /* ttc_precision (default TTC_PREC_FP64) */

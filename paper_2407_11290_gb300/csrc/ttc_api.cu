@@ -308,6 +308,15 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     }
     h->bond_cap[b] = cap;
   }
+  for (int b = 0; b < d - 1; ++b) {
+    // superblock rows / columns are 32-bit in the tile plan
+    const int64_t capL = b == 0 ? 1 : h->bond_cap[b - 1];
+    const int64_t capR = b == d - 2 ? 1 : h->bond_cap[b + 1];
+    if (capL * n[b] >= ((int64_t)1 << 31) || capR * n[b + 1] >= ((int64_t)1 << 31)) {
+      delete h;
+      return fail(TTC_ERR_INVALID_ARG, "bond %d: rank cap x mode size reaches 2^31", b + 1);
+    }
+  }
   h->opt.bond_max_rank = nullptr;
   std::vector<int32_t> bcaps;
   if (o.bond_max_rank) bcaps.assign(o.bond_max_rank, o.bond_max_rank + d - 1);

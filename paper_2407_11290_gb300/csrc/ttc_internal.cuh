@@ -25,7 +25,7 @@
 namespace ttc {
 
 constexpr int BM = 64, BN = 64;   // screen tile (superblock rows x columns)
-constexpr int RCAP = 128;         // largest rank capacity the kernels accept
+constexpr int RCAP = 256;         // largest rank capacity the kernels accept
 constexpr int GRID_CAP = 4096;    // largest persistent grid (partial-sum slots)
 
 enum State : int32_t { ST_SCREEN = 0, ST_UPDATE = 1, ST_VERIFY = 2, ST_DONE = 3 };

@@ -75,7 +75,7 @@ CONFIGS = {
                           nsamples=0, precision="fp64"),
     "hilbert6d_n64": dict(**hilbert(6, 64), eps=1e-8, max_rank=64, grid=[2] * 6,
                           nsamples=10**6, precision="fp64"),
-    "maxwellian6d_n64": dict(**maxwellian(3, 3, 64), eps=1e-6, max_rank=64,
+    "maxwellian6d_n64": dict(**maxwellian(3, 3, 64), eps=1e-6, max_rank=256,
                              grid=[4, 4, 4, 1, 1, 1], nsamples=10**6, precision="fp32"),
     "hilbert6d_n256": dict(**hilbert(6, 256), eps=1e-10, max_rank=128, grid=[4] * 6,
                            nsamples=10**6, precision="split"),

@@ -176,3 +176,30 @@ def test_stored_batch_equals_single(tt):
         assert list(a.ranks()) == list(b.ranks())
         for k in range(1, len(a.n) + 1):
             np.testing.assert_array_equal(a.core(k), b.core(k))
+
+
+def test_stored_maxwellian6d_reaches_eps_above_rank_128(tt):
+    """The 6D Maxwellian (3x + 3v, n = 64) needs ranks above 128 at eps = 1e-6:
+    the stored form reaches eps with rank cap 256; its error is cross-checked
+    at 2000 samples from the oracle's entries and a numpy contraction of the
+    GPU cores."""
+    w = W.CONFIGS["maxwellian6d_n64"]
+    g = tt.TTCross(w["n"], w["gen"], max_rank=w["max_rank"], nsamples=w["nsamples"],
+                   residual="stored")
+    g.run(w["eps"], subtensor_grid=w["grid"])
+    assert g.sync() == 0
+    st = g.stats()
+    assert st["err"] <= w["eps"]
+    assert max(g.ranks()) > 128
+    cores = g.cores()
+    idx = oracle.sample_indices(w["n"], 2000, seed=77)
+    o = oracle.Oracle(w["n"], w["gen"], 1)
+    num = den = 0.0
+    for s in idx:
+        x = o.entry(s)
+        v = cores[0][:, s[0], :]
+        for m in range(1, 6):
+            v = v @ cores[m][:, s[m], :]
+        num += (x - v[0, 0]) ** 2
+        den += x * x
+    assert (num / den) ** 0.5 <= 3 * w["eps"]
