@@ -160,7 +160,9 @@ def bench_gpu(args, rank, world, local):
     from paper_2407_11290_gb300 import ttcross, workloads
 
     torch.cuda.set_device(local)
-    cfg = workloads.CONFIGS[args.workload]
+    cfg = dict(workloads.CONFIGS[args.workload])
+    if args.max_rank > 0:
+        cfg["max_rank"] = args.max_rank
     stream = torch.cuda.Stream()
     tc = ttcross.TTCross(cfg["n"], cfg["gen"], max_rank=cfg["max_rank"], nsamples=cfg["nsamples"],
                          precision=args.precision, host_loop=args.host_loop,
@@ -377,6 +379,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["hilbert3d_n32", "hilbert6d_n64", "hilbert6d_n256", "maxwellian6d_n64",
                              "maxwellian_batch"])
+    ap.add_argument("--max-rank", type=int, default=0,
+                    help="rank cap instead of the workload's (0: the workload's); a smaller cap "
+                         "shrinks the stored residuals for profiling captures")
     ap.add_argument("--batch-count", type=int, default=256,
                     help="instances of the maxwellian_batch workload")
     ap.add_argument("--host-loop", action="store_true",

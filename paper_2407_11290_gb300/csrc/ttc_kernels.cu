@@ -965,14 +965,22 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
     int32_t j = s_item;
     __syncthreads();
     if (j >= ntot) break;
-    // item j -> (bond, tile): fresh quarters of every bond, then carried tiles
-    const bool fresh = j < nfresh;
+    // item j -> (bond, tile): fresh items (FP64-bound) and carried tiles
+    // (memory-bound) alternate, so the two CTAs of an SM tend to load
+    // different pipes; the longer list runs on alone at the end
+    const int32_t m = min(nfresh, ntot - nfresh);
+    bool fresh;
+    if (j < 2 * m) {
+      fresh = (j & 1) == 0;
+      j >>= 1;
+    } else {
+      fresh = nfresh > m;
+      j -= m;
+    }
     int32_t q = 0;
     if (fresh) {
       q = j % spt;
       j /= spt;
-    } else {
-      j -= nfresh;
     }
     for (int b = 0; b < in.nb; ++b) {
       const TileGeo &g = s_geo[b];
