@@ -67,6 +67,7 @@ struct ttc_handle {
   InstDev **d_list = nullptr;   // [1] = d_inst, for single runs
   Ctrl *d_ctrl = nullptr;
   Barrier *d_bar = nullptr;
+  int32_t *d_smid = nullptr;
   Ctrl h_ctrl{};
   void *pool = nullptr;
   size_t pool_bytes = 0;
@@ -173,6 +174,7 @@ ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, 
   ra.insts = d_list;
   ra.count = count;
   ra.bar = h0->d_bar;
+  ra.smid = h0->d_smid;
   ra.wait_ns = (int64_t)(h0->opt.wait_limit_s * 1e9);
   ra.persistent = h0->opt.host_loop ? 0 : 1;
   ra.mixed = 0;
@@ -399,6 +401,7 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     double *xs = cv.take<double>(ns);
     double *errp = cv.take<double>(GRID_CAP);
     Cand *spart = cv.take<Cand>(GRID_CAP);
+    int32_t *smid = cv.take<int32_t>(GRID_CAP);
     int32_t *eidx = cv.take<int32_t>(TTC_MAXD);
     int64_t *elin = cv.take<int64_t>(1);
     int32_t *esum = cv.take<int32_t>(1);
@@ -470,6 +473,7 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     } else {
       h->d_ctrl = ctrl;
       h->d_bar = bar;
+      h->d_smid = smid;
       h->d_inst = dinst;
       h->d_list = dlist;
       I.hilb = hilb;

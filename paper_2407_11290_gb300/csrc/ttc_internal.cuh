@@ -170,6 +170,7 @@ struct RunArgs {
   int64_t wait_ns;
   int32_t persistent;
   int32_t max_iters;     // sweep cap of the launch (sum of rank caps + refinements)
+  int32_t *smid;         // [grid] the SM each CTA of a persistent launch runs on
 };
 
 // ---------------------------------------------------------------------------

@@ -74,20 +74,27 @@ struct DecideSmem {
   int32_t flag;
 };
 
-// pivot history of one bond for the replays (Alg. 4), packed triangles:
-// row z of hc / hpiv (z entries) at z (z - 1) / 2
-constexpr int HIST_SMEM = 2480;   // ranks up to 70
+constexpr int SPREAD_MAXSM = 1024;
+struct SpreadSmem {
+  int32_t cnt[SPREAD_MAXSM];  // CTAs per SM id
+  int32_t k, place, bad;
+};
+
+// replays of up to 32 pivots (Alg. 4): the history triangles (row z at
+// z (z - 1) / 2) and delta, shared by the CTA's replay warps; after the
+// block reductions' words, which the CTA's other warps may be using meanwhile
+constexpr int LANE_NZ = 32;
 struct ReplaySmem {
-  double hc[HIST_SMEM], hp[HIST_SMEM];
-  double delta[RCAP];
-  int32_t jsum[RCAP];     // Hilbert: index sums of the pivots' J_{>k} entries
-  int32_t lsum;           // Hilbert: index sum of the chunk's prefix
+  double red_pad[NT / 32];
+  double hc[LANE_NZ * (LANE_NZ - 1) / 2], hp[LANE_NZ * (LANE_NZ - 1) / 2];
+  double delta[LANE_NZ];
 };
 
 union __align__(16) PhaseSmem {
   ScreenSmem s;
   DecideSmem d;
-  ReplaySmem h;
+  SpreadSmem sp;
+  ReplaySmem rp;
   double red[NT / 32];
 };
 
@@ -97,8 +104,16 @@ union __align__(16) PhaseSmem {
 // launch (the host writes it before launching).
 __shared__ InstDev s_inst0;
 
+// This CTA's place in the SM-spread order of the grid (the CTAs sorted by
+// their slot on their SM, then by SM): work dealt to places 0, 1, 2, ...
+// lands on distinct SMs before any SM gets a second share.  Latency-bound
+// items (pivot steps, replays) then do not queue for the FP64 pipe, which
+// is shared by the whole SM.  blockIdx.x until the order is known.
+__shared__ int32_t s_place;
+
 __device__ void cache_inst0(const RunArgs &ra) {
   static_assert(sizeof(InstDev) % 8 == 0, "InstDev copies as 8-byte words");
+  if (threadIdx.x == 0) s_place = blockIdx.x;
   const unsigned long long *src = reinterpret_cast<const unsigned long long *>(ra.insts[0]);
   unsigned long long *dst = reinterpret_cast<unsigned long long *>(&s_inst0);
   for (int i = threadIdx.x; i < (int)(sizeof(InstDev) / 8); i += blockDim.x) dst[i] = src[i];
@@ -1413,13 +1428,13 @@ __device__ void for_decide_items(const RunArgs &ra, bool second, F &&f) {
     const int st = ld_cg(cr.state);
     if (st == ST_DONE) continue;
     if (!second && st == ST_VERIFY) {
-      if (j++ % gridDim.x == blockIdx.x) f(ii, -1);
+      if (j++ % gridDim.x == s_place) f(ii, -1);
       continue;
     }
     if (!ld_cg(cr.screened)) continue;
     for (int b = 0; b < in.nb; ++b) {
       if (second && !ld_cg(cr.pending[b])) continue;
-      if (j++ % gridDim.x == blockIdx.x) f(ii, b);
+      if (j++ % gridDim.x == s_place) f(ii, b);
     }
   }
 }
@@ -1524,78 +1539,171 @@ __device__ __forceinline__ void pivot_col_entries(const InstDev &in, int b, int6
   }
 }
 
-// Alg. 4 for row a of bond b: eq. aca_approx_T_sub for pivots 0..nz-1 in
-// insertion order.  The history (hc, hpiv rows, delta) comes from shared
-// memory when `packed` (triangles, row z at z (z - 1) / 2), else from the
-// bond's arrays (row z at z * cap).
-__device__ void replay_row(const InstDev &in, int b, int64_t a, int nz,
-                           const double *__restrict__ hcb, const double *__restrict__ hpb,
-                           const double *__restrict__ dl, bool packed,
-                           const int32_t *__restrict__ jsum = nullptr, int32_t rs = 0) {
+// Alg. 4 for row a of bond b (eq. aca_approx_T_sub for pivots 0..nz-1 in
+// insertion order) by one warp: lane u keeps T(a, 32k + u), k < K, in
+// registers.  Step z runs the contract's chain over t < z on every lane from
+// broadcasts (the serial order is the contract's; the chain's FP64 latency
+// is the cost), then each lane updates its own entries - one instruction
+// per 32 entries.  A row per warp issues one FP64 instruction per chain
+// element; an SMSP's FP64 unit takes one warp instruction per ~64 cycles,
+// the latency of the chain itself.  History row z (hc, hpiv, delta) comes
+// from the triangles staged in shared memory (ST: row z at z (z - 1) / 2)
+// or from the bond's arrays (row z at z * cap), the next row loading
+// during this step when PF.
+template <int K, bool PF>
+__device__ __noinline__ void replay_row_warp(const InstDev &in, int b, int64_t a, int nz,
+                                             const ReplaySmem *st) {
   const BondDev &B = in.bond[b];
-  double Tr[RCAP], ent[RCAP];
-  const int cap = B.cap;
-  if (jsum) {
-    // Hilbert, sums staged: independent table lookups
-#pragma unroll 8
-    for (int z = 0; z < nz; ++z) ent[z] = in.hilb[rs + jsum[z]];
+  const int lane = threadIdx.x & 31;
+  const int64_t cap = B.cap;
+  constexpr unsigned FULL = 0xffffffffu;
+  const double *hcb = st ? st->hc : B.hc;
+  const double *hpb = st ? st->hp : B.hpiv;
+  const double *dlb = st ? st->delta : B.delta;
+  auto off = [&](int z) -> int64_t { return st ? (int64_t)z * (z - 1) / 2 : (int64_t)z * cap; };
+  double tr[K], en[K], hc[K], hp[K], hcn[K], hpn[K];
+  if (in.gen == 0) {
+    const int64_t nb0 = in.n[b];
+    const int64_t p = a / nb0, i = a - p * nb0;
+    const int32_t rs = left_set(in, b).sum[p] + (int32_t)i;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int t = 32 * k + lane;
+      en[k] = t < nz ? in.hilb[rs + B.J.sum[t]] : 0.0;
+    }
   } else {
-    pivot_col_entries(in, b, a, 0, nz, ent);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int t = 32 * k + lane;
+      en[k] = t < nz ? sb_entry(in, b, a, B.pcol[t]) : 0.0;
+    }
   }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    tr[k] = 0.0;
+    hcn[k] = 0.0;
+    hpn[k] = 0.0;
+  }
+  double dn = nz > 0 ? dlb[0] : 0.0;
   for (int z = 0; z < nz; ++z) {
-    const int64_t o = packed ? (int64_t)z * (z - 1) / 2 : (int64_t)z * cap;
-    const double *hc = hcb + o;
-    const double *hp = hpb + o;
-    const double s = __dsub_rn(chain(Tr, 1, hc, 1, z), ent[z]);
-    const double w = __dmul_rn(dl[z], s);
-    for (int t = 0; t < z; ++t) Tr[t] = __fma_rn(w, hp[t], Tr[t]);
-    Tr[z] = -w;
+    const double dz = dn;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int t = 32 * k + lane;
+      if (PF) {
+        hc[k] = hcn[k];
+        hp[k] = hpn[k];
+      } else {
+        hc[k] = t < z ? hcb[off(z) + t] : 0.0;
+        hp[k] = t < z ? hpb[off(z) + t] : 0.0;
+      }
+    }
+    if (z + 1 < nz) {
+      dn = dlb[z + 1];
+      if (PF) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int t = 32 * k + lane;
+          hcn[k] = t < z + 1 ? hcb[off(z + 1) + t] : 0.0;
+          hpn[k] = t < z + 1 ? hpb[off(z + 1) + t] : 0.0;
+        }
+      }
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (32 * k >= z) break;
+      const int lim = min(32, z - 32 * k);
+      for (int u = 0; u < lim; ++u)
+        acc = __fma_rn(__shfl_sync(FULL, tr[k], u), __shfl_sync(FULL, hc[k], u), acc);
+    }
+    double ez = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (k == (z >> 5)) ez = __shfl_sync(FULL, en[k], z & 31);
+    const double w = __dmul_rn(dz, __dsub_rn(acc, ez));
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int t = 32 * k + lane;
+      if (t < z)
+        tr[k] = __fma_rn(w, hp[k], tr[k]);
+      else if (t == z)
+        tr[k] = -w;
+    }
   }
-  for (int t = 0; t < nz; ++t) putT(in, B, (int64_t)t * B.ldT + a, Tr[t]);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int t = 32 * k + lane;
+    if (t < nz) putT(in, B, (int64_t)t * B.ldT + a, tr[k]);
+  }
+}
+
+// history of bond b (nz <= 32 pivots) into the triangles of shared memory by
+// the nw replay warps of the CTA (named barrier 1: the other warps are busy
+// elsewhere); every load is issued before the first store
+__device__ void stage_history(const BondDev &B, int nz, int nw, ReplaySmem &rs) {
+  constexpr int TRI = LANE_NZ * (LANE_NZ - 1) / 2;
+  constexpr int PER = (TRI + 31) / 32;
+  const int nthr = nw * 32;
+  const int64_t cap = B.cap;
+  const int tri = nz * (nz - 1) / 2;
+  double vc[PER], vp[PER];
+#pragma unroll
+  for (int m = 0; m < PER; ++m) {
+    const int k = threadIdx.x + nthr * m;
+    vc[m] = vp[m] = 0.0;
+    if (k < tri) {
+      int z = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)k)) * 0.5f);
+      while (z * (z - 1) / 2 > k) --z;
+      while ((z + 1) * z / 2 <= k) ++z;
+      const int64_t o = (int64_t)z * cap + (k - z * (z - 1) / 2);
+      vc[m] = B.hc[o];
+      vp[m] = B.hpiv[o];
+    }
+  }
+  const double dl = (int)threadIdx.x < nz ? B.delta[threadIdx.x] : 0.0;
+  asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");  // earlier readers are done
+#pragma unroll
+  for (int m = 0; m < PER; ++m) {
+    const int k = threadIdx.x + nthr * m;
+    if (k < tri) {
+      rs.hc[k] = vc[m];
+      rs.hp[k] = vp[m];
+    }
+  }
+  if ((int)threadIdx.x < nz) rs.delta[threadIdx.x] = dl;
+  asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
 }
 
 // the replays of the n_b rows that the new prefix of bond b-1 adds to bond b:
-// chunks of NT rows, one per CTA (chunk g goes to CTA (cbase + g) mod G), the
-// history staged in shared memory once per chunk
+// chunks of W <= 8 rows, a row per warp (warps 0..W-1; W <= 4 keeps one per
+// SMSP, the smallest W that gives every row a warp is taken), chunk
+// g to place (cbase + g) mod G, so that the first chunks land on distinct
+// SMs and the dependent FP64 chains run at their latency
 __device__ int32_t replay_chunks(const InstDev &in, int b, int64_t p, int nz, int32_t &cbase,
-                                 PhaseSmem &sm) {
+                                 int W, ReplaySmem &rs) {
   const BondDev &B = in.bond[b];
   const int64_t nit = in.n[b];
-  const int32_t nch = (int32_t)((nit + NT - 1) / NT);
   const int32_t G = gridDim.x;
-  const bool fits = (int64_t)nz * (nz - 1) / 2 <= HIST_SMEM;
-  for (int32_t ch = (int32_t)(((int64_t)blockIdx.x - cbase) % G + G) % G; ch < nch; ch += G) {
-    if (fits) {
-      __syncthreads();
-      // flat over the triangle: entry k is (z, t) with z (z - 1) / 2 <= k
-      const int tri = nz * (nz - 1) / 2;
-      for (int k = threadIdx.x; k < tri; k += NT) {
-        int z = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)k)) * 0.5f);
-        while (z * (z - 1) / 2 > k) --z;
-        while ((z + 1) * z / 2 <= k) ++z;
-        const int t = k - z * (z - 1) / 2;
-        sm.h.hc[k] = B.hc[(int64_t)z * B.cap + t];
-        sm.h.hp[k] = B.hpiv[(int64_t)z * B.cap + t];
+  const int32_t nch = (int32_t)((nit + W - 1) / W);
+  const int warp = threadIdx.x >> 5;
+  if (warp < W) {
+    for (int32_t ch = (int32_t)(((int64_t)s_place - cbase) % G + G) % G; ch < nch; ch += G) {
+      const int64_t i = (int64_t)ch * W + warp;
+      if (nz <= LANE_NZ) {
+        stage_history(B, nz, W, rs);
+        if (i < nit) replay_row_warp<1, true>(in, b, p * nit + i, nz, &rs);
+      } else if (i < nit) {
+        const int64_t a = p * nit + i;
+        if (nz <= 64)
+          replay_row_warp<2, true>(in, b, a, nz, nullptr);
+        else if (nz <= 128)
+          replay_row_warp<4, true>(in, b, a, nz, nullptr);
+        else
+          replay_row_warp<8, false>(in, b, a, nz, nullptr);
       }
-      for (int z = threadIdx.x; z < nz; z += NT) {
-        sm.h.delta[z] = B.delta[z];
-        sm.h.jsum[z] = B.J.sum[z];
-      }
-      if (threadIdx.x == 0) sm.h.lsum = left_set(in, b).sum[p];
-      __syncthreads();
-    }
-    const int64_t i = (int64_t)ch * NT + threadIdx.x;
-    if (i < nit) {
-      if (fits && in.gen == 0)
-        replay_row(in, b, p * nit + i, nz, sm.h.hc, sm.h.hp, sm.h.delta, true, sm.h.jsum,
-                   sm.h.lsum + (int32_t)i);
-      else if (fits)
-        replay_row(in, b, p * nit + i, nz, sm.h.hc, sm.h.hp, sm.h.delta, true);
-      else
-        replay_row(in, b, p * nit + i, nz, B.hc, B.hpiv, B.delta, false);
     }
   }
-  __syncthreads();  // the staged history is dead before shared memory is reused
   cbase = (int32_t)(((int64_t)cbase + nch) % G);
   return nch;
 }
@@ -1892,7 +2000,11 @@ __device__ double sample_residual(const InstDev &in, const int32_t *r, int pL, i
 __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
   __shared__ CtrlSnap snap;
   const int64_t NTOT = (int64_t)gridDim.x * NT;
-  const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
+  // items that each write their own outputs are dealt over the places; the
+  // error's samples by blockIdx, so that the partial sums (and their
+  // rounding) do not depend on where the CTAs run
+  const int64_t gt = (int64_t)s_place * NT + threadIdx.x;
+  const int64_t gs = (int64_t)blockIdx.x * NT + threadIdx.x;
   int64_t base = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = inst(ra, ii);
@@ -1916,13 +2028,16 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
       if (nadd > 0) write_plan_warp(in, *in.ctrl, rn, gridDim.x);  // next screen's tiles
     }
     if (nadd > 0) {
-      // C first: the replays are the longest items, a CTA per NT rows; the
-      // thread-dealt items start on the CTA after the last replay chunk
+      // C first: the replays are the longest items; the thread-dealt items
+      // start on the place after the last replay chunk
       int32_t cbase = (int32_t)((base / NT) % gridDim.x);
-      int64_t nchunks = 0;
+      int64_t nchunks = 0, rrows = 0;
+      for (int b = 1; b < in.nb; ++b)
+        if (ad[b - 1]) rrows += in.n[b];
+      const int W = (int)min((int64_t)(NT / 32), max((int64_t)1, (rrows + gridDim.x - 1) / gridDim.x));
       for (int b = 1; b < in.nb; ++b) {
         if (!ad[b - 1]) continue;
-        nchunks += replay_chunks(in, b, ro[b - 1], rn[b], cbase, sm);
+        nchunks += replay_chunks(in, b, ro[b - 1], rn[b], cbase, W, sm.rp);
       }
       base += nchunks * NT;
       for (int b = 0; b < in.nb; ++b) {
@@ -1966,7 +2081,7 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
       const int64_t ns = in.nsamples;
       int pL, pR;
       choose_split(in, rn, pL, pR);
-      for (int64_t x = first_item(base, gt, NTOT); x < base + ns; x += NTOT) {
+      for (int64_t x = first_item(base, gs, NTOT); x < base + ns; x += NTOT) {
         const double e = sample_residual(in, rn, pL, pR, x - base);
         part = __fma_rn(e, e, part);
       }
@@ -2219,13 +2334,59 @@ __device__ bool any_verify(const RunArgs &ra) {
   return hit != 0;
 }
 
+__device__ __forceinline__ int32_t sm_id() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return (int32_t)r;
+}
+
+// s_place from the table of SM ids (written by every CTA before a grid
+// barrier): with cnt[s] CTAs on SM s and this CTA the k-th on its SM sm,
+//   place = sum_s min(cnt[s], k) + #{s < sm : cnt[s] > k},
+// its rank when the CTAs are sorted by (k, SM) - a bijection onto [0, G).
+// Ids outside the table keep the identity order.
+__device__ void spread_order(const RunArgs &ra, PhaseSmem &sm) {
+  SpreadSmem &sp = sm.sp;
+  const int G = gridDim.x, me = sm_id();
+  for (int s = threadIdx.x; s < SPREAD_MAXSM; s += NT) sp.cnt[s] = 0;
+  if (threadIdx.x == 0) {
+    sp.k = 0;
+    sp.place = 0;
+    sp.bad = me >= SPREAD_MAXSM;
+  }
+  __syncthreads();
+  int k = 0;
+  for (int j = threadIdx.x; j < G; j += NT) {
+    const int s = ld_cg(ra.smid[j]);
+    if (s >= 0 && s < SPREAD_MAXSM)
+      atomicAdd(&sp.cnt[s], 1);
+    else
+      sp.bad = 1;
+    k += (j < (int)blockIdx.x && s == me);
+  }
+  if (k) atomicAdd(&sp.k, k);
+  __syncthreads();
+  const int kk = sp.k;
+  int part = 0;
+  for (int s = threadIdx.x; s < SPREAD_MAXSM; s += NT) {
+    const int c = sp.cnt[s];
+    part += min(c, kk) + (s < me && c > kk);
+  }
+  if (part) atomicAdd(&sp.place, part);
+  __syncthreads();
+  if (threadIdx.x == 0) s_place = sp.bad ? (int32_t)blockIdx.x : sp.place;
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(NT, 2) k_persistent(RunArgs ra) {
   PhaseSmem &sm = *reinterpret_cast<PhaseSmem *>(dyn_smem);
   cache_inst0(ra);
   PhaseClock clk;
   clk.start();
+  if (threadIdx.x == 0) ra.smid[blockIdx.x] = sm_id();
   phase_init1(ra, sm);
   if (!grid_barrier(ra, 1)) return;
+  spread_order(ra, sm);
   phase_init2(ra, sm);
   if (!grid_barrier(ra, 2)) return;
   phase_init3(ra, sm);
