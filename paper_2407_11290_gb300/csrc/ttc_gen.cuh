@@ -127,6 +127,18 @@ __device__ __noinline__ double sb_entry(const InstDev &in, int b, int64_t a, int
   return gen_full(in, idx);
 }
 
+// Coordinate m of error sample k, the value sample_index gives, computed
+// alone (no index array in local memory on the sample path).
+__device__ __forceinline__ int32_t sample_coord(const InstDev &in, int64_t k, int m) {
+  if (in.exhaustive) {
+    int64_t l = k;
+    for (int j = 0; j < m; ++j) l /= in.n[j];
+    return (int32_t)(l % in.n[m]);
+  }
+  const uint64_t x = splitmix64_at(in.seed, (uint64_t)(k * in.d + m));
+  return (int32_t)__umul64hi(x, (uint64_t)in.n[m]);
+}
+
 // Multi-index of error sample k (SplitMix64 counter form, sample-major,
 // mode-minor; index = floor(x * n / 2^64)), or entry k in column-major
 // order when the error runs over every entry.

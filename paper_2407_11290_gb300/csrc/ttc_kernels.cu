@@ -868,9 +868,13 @@ __device__ __forceinline__ void screen_tile_mixed(const InstDev &in, int b, int 
 
 // state, screened, add[b] and r[b] of an instance, each word loaded by its
 // own thread (one L2 round trip instead of a chain of them)
+// control words of an instance read once per phase by the CTA (shared
+// memory: per-thread copies would live in local memory, whose lines this
+// kernel's large stack frame keeps out of L1)
 struct CtrlSnap {
   int32_t state, screened;
   int32_t add[TTC_MAXB], r[TTC_MAXB];
+  int32_t old_r[TTC_MAXB];  // r - add: the ranks at the start of the sweep
 };
 
 __device__ void snap_ctrl(const Ctrl &cr, int nb, CtrlSnap &out) {
@@ -884,6 +888,8 @@ __device__ void snap_ctrl(const Ctrl &cr, int nb, CtrlSnap &out) {
     out.add[k - 2] = ld_cg(cr.add[k - 2]);
   else if (k < 2 + 2 * nb)
     out.r[k - 2 - nb] = ld_cg(cr.r[k - 2 - nb]);
+  __syncthreads();
+  if (k < nb) out.old_r[k] = out.r[k] - out.add[k];
   __syncthreads();
 }
 
@@ -1054,8 +1060,7 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
     const Ctrl &cr = *in.ctrl;
     snap_ctrl(cr, in.nb, snap);
     if (snap.state != ST_SCREEN) continue;
-    int32_t r[TTC_MAXD];
-    for (int b = 0; b < in.nb; ++b) r[b] = snap.r[b];
+    const int32_t *r = snap.r;
     if (in.stored) {
       screen_stored_instance(in, r, sm);
       continue;
@@ -1878,20 +1883,23 @@ constexpr int TAB_CHUNK = 8;  // last-mode indices per table work item
 // tables of the verifying instances: a work item is a prefix of pL-1 modes
 // (suffix of pR-1 modes) and a chunk of TAB_CHUNK values of the next mode
 __device__ void phase_tables(const RunArgs &ra) {
+  // items are dealt a warp's worth per CTA in turn (lane l of warp w of CTA
+  // c is number (w G + c) 32 + l): when there are fewer items than threads
+  // every SM still gets an equal share of this FP64-bound phase, and the
+  // lanes of a warp keep neighbouring items (the same core rows)
   const int64_t NTOT = (int64_t)gridDim.x * blockDim.x;
-  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gt = ((int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+  __shared__ CtrlSnap snap;
   int64_t base = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
-    if (ld_cg(cr.state) == ST_DONE) continue;
-    if (!ld_cg(cr.screened)) continue;
-    int32_t r[TTC_MAXD];
+    snap_ctrl(cr, in.nb, snap);
+    if (snap.state == ST_DONE) continue;
+    if (!snap.screened) continue;
+    const int32_t *r = snap.r;
     int nadd = 0;
-    for (int b = 0; b < in.nb; ++b) {
-      r[b] = ld_cg(cr.r[b]);
-      nadd += ld_cg(cr.add[b]);
-    }
+    for (int b = 0; b < in.nb; ++b) nadd += snap.add[b];
     if (nadd) continue;
     int pL, pR;
     choose_split(in, r, pL, pR);
@@ -1952,8 +1960,7 @@ __device__ void phase_tables(const RunArgs &ra) {
 
 // error of one sample: X(i) - X~(i), using the tables of (pL, pR)
 __device__ double sample_residual(const InstDev &in, const int32_t *r, int pL, int pR, int64_t k) {
-  int32_t idx[TTC_MAXD];
-  sample_index(in, k, idx);
+  const double xk = in.xs[k];
   double v[RCAP], w[RCAP];
   const int d = in.d;
   int len;
@@ -1962,7 +1969,7 @@ __device__ double sample_residual(const InstDev &in, const int32_t *r, int pL, i
   if (pL >= 2) {
     int64_t e = 0, st = 1;
     for (int m = 0; m < pL; ++m) {
-      e += idx[m] * st;
+      e += sample_coord(in, k, m) * st;
       st *= in.n[m];
     }
     len = (int)core_s(in, r, pL);
@@ -1971,13 +1978,13 @@ __device__ double sample_residual(const InstDev &in, const int32_t *r, int pL, i
   } else {
     const BondDev &B0 = in.bond[0];
     len = (int)core_s(in, r, 1);
-    src = B0.T + idx[0];
+    src = B0.T + sample_coord(in, k, 0);
     sv = B0.ldT;
   }
   if (pL + pR < d) {
     // middle cores: the vector goes to local memory
     copy8(v, src, sv, len);
-    for (int m = pL; m < d - pR; ++m) len = mul_core(in, r, m, idx[m], v, w);
+    for (int m = pL; m < d - pR; ++m) len = mul_core(in, r, m, sample_coord(in, k, m), v, w);
     src = v;
     sv = 1;
   }
@@ -1985,15 +1992,32 @@ __device__ double sample_residual(const InstDev &in, const int32_t *r, int pL, i
   if (pR >= 2) {
     int64_t e = 0, st = 1;
     for (int m = d - pR; m < d; ++m) {
-      e += idx[m] * st;
+      e += sample_coord(in, k, m) * st;
       st *= in.n[m];
     }
-    xt = chain(src, sv, in.tabR + e * len, 1, len);
+    const double *y = in.tabR + e * len;
+    if (len <= 16) {
+      // both rows in flight at once (a round trip to L2 each otherwise per
+      // eight entries), then the contract's chain
+      double xv[16], yv[16];
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        xv[t] = t < len ? src[t * sv] : 0.0;
+        yv[t] = t < len ? y[t] : 0.0;
+      }
+      double acc = 0.0;
+#pragma unroll
+      for (int t = 0; t < 16; ++t)
+        if (t < len) acc = __fma_rn(xv[t], yv[t], acc);
+      xt = acc;
+    } else {
+      xt = chain(src, sv, y, 1, len);
+    }
   } else {
     const BondDev &BL = in.bond[d - 2];
-    xt = chain(src, sv, BL.R + idx[d - 1], BL.ldR, len);
+    xt = chain(src, sv, BL.R + sample_coord(in, k, d - 1), BL.ldR, len);
   }
-  return __dsub_rn(in.xs[k], xt);
+  return __dsub_rn(xk, xt);
 }
 
 
@@ -2014,14 +2038,9 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
     snap_ctrl(cr, in.nb, snap);
     const int st = snap.state;
     if (st == ST_DONE) continue;
-    int32_t ro[TTC_MAXD], rn[TTC_MAXD], ad[TTC_MAXD];
+    const int32_t *ro = snap.old_r, *rn = snap.r, *ad = snap.add;
     int nadd = 0;
-    for (int b = 0; b < in.nb; ++b) {
-      ad[b] = snap.add[b];
-      rn[b] = snap.r[b];
-      ro[b] = rn[b] - ad[b];
-      nadd += ad[b];
-    }
+    for (int b = 0; b < in.nb; ++b) nadd += ad[b];
     const bool screened = snap.screened != 0;
     if (blockIdx.x == ii % gridDim.x && threadIdx.x < 32) {
       if (nadd == 0 && screened && threadIdx.x == 0) in.ctrl->state = ST_VERIFY;
