@@ -1693,7 +1693,8 @@ __device__ int32_t replay_chunks(const InstDev &in, int b, int64_t p, int nz, in
   const int32_t nch = (int32_t)((nit + W - 1) / W);
   const int warp = threadIdx.x >> 5;
   if (warp < W) {
-    for (int32_t ch = (int32_t)(((int64_t)s_place - cbase) % G + G) % G; ch < nch; ch += G) {
+    // places and cbase are in [0, G)
+    for (int32_t ch = (s_place - cbase + G) % G; ch < nch; ch += G) {
       const int64_t i = (int64_t)ch * W + warp;
       if (nz <= LANE_NZ) {
         stage_history(B, nz, W, rs);
@@ -2061,6 +2062,17 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
       base += nchunks * NT;
       for (int b = 0; b < in.nb; ++b) {
         const BondDev &B = in.bond[b];
+        // a thread with no item of this bond skips it whole: no load of the
+        // pivot's coordinates or entries reaches its path
+        {
+          const int64_t rc = ad[b] ? rows_of(in, ro, b) + cols_of(in, ro, b) : 0;
+          const int64_t tot = (in.stored ? 2 : 1) * rc +
+                              (b < in.nb - 1 && ad[b + 1] ? (int64_t)rn[b] * in.n[b + 1] : 0);
+          if (first_item(base, gt, NTOT) >= base + tot) {
+            base += tot;
+            continue;
+          }
+        }
         if (ad[b] && in.stored) {
           // the pending rank-one step of the stored residual (from the
           // sweep-start superblock, which E still holds)
