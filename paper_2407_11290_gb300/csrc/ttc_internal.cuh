@@ -88,7 +88,12 @@ struct Ctrl {
                              // (cleared by the decide phase after it)
   int64_t entries_fresh;     // entries evaluated as A - T R (the rest carried)
   int64_t stored_bytes;      // bytes of E read and written by the screens
+  int32_t dkind;             // work of the coming decide phases, fixed by the
+                             // screen phase: DK_BONDS, DK_VERIFY or DK_NONE
+  int32_t pad_dkind;
 };
+
+enum DecideKind { DK_NONE = 0, DK_BONDS = 1, DK_VERIFY = 2 };
 
 struct InstDev {
   int32_t d, nb;

@@ -57,9 +57,16 @@ constexpr int TOPK_MAX = 16;
 // a carried tile uses the first and marks the rest empty, row -2)
 constexpr int STORED_SLOTS = 4;
 
+constexpr int DEC_US = 32;  // pivot steps up to this rank stage U in shared memory
 struct DecideSmem {
   double ua[RCAP], bu[RCAP], brow[RCAP];
   double hcs[RCAP], hps[RCAP];  // R(:, c*) and T(a*, :) of the pivot step
+  double us[DEC_US * DEC_US];   // U before the step (z <= DEC_US)
+  int32_t key[RCAP];            // pivot t's column: index sum (Hilbert) or coordinate
+  int32_t lsum, rsum;           // index sums of the pivot's row part / column part
+  int64_t q_nt;                 // control words of the decide item
+  int32_t q_r, q_maxr, q_prow, q_pcol;
+  double q_tau, q_xrms;
   double apiv;                  // A(a*, c*)
   int32_t sel[TOPK_MAX];
   uint64_t skey[TOPK_MAX];
@@ -1059,6 +1066,9 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
     const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
     snap_ctrl(cr, in.nb, snap);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+      in.ctrl->dkind = snap.state == ST_SCREEN ? DK_BONDS : snap.state == ST_VERIFY ? DK_VERIFY
+                                                                                   : DK_NONE;
     if (snap.state != ST_SCREEN) continue;
     const int32_t *r = snap.r;
     if (in.stored) {
@@ -1102,10 +1112,9 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
 // (alpha*, i*), J_{>k} gets (j*, beta*) (eq. nestedpivots); the history of
 // step z keeps c_z = R(:, c*), T(a*, :) and delta; U = P^{-1} is bordered
 // by [[U + d U a b U, -d U a], [-d b U, d]] (Sec. 3.1.1).
-__device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int64_t cs,
+__device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int64_t cs, int z,
                              DecideSmem &sm) {
   const BondDev &B = in.bond[b];
-  const int z = ld_cg(cr.r[b]);
   const int cap = B.cap;
   const int tid = threadIdx.x;
   const int64_t nb0 = in.n[b], nb1 = in.n[b + 1];
@@ -1113,31 +1122,49 @@ __device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int
   const int64_t q = cs / nb1, j = cs - q * nb1;
   const SetDev &L = left_set(in, b);
   const SetDev &Rset = right_set(in, b);
-  // warp 1 appends the index sets while warp 0 gathers the history
-  if (tid == 32) {
+  const bool hil = in.gen == 0;
+  const bool ustage = z <= DEC_US;
+  // one round of independent loads: warp 1 appends the index sets (a lane
+  // per index), threads t < z gather the history (R(t, c*), T(a*, t)) and
+  // the pivot columns' index sums (Hilbert) or coordinates, the rest stage U
+  if (tid >= 32 && tid < 64) {
+    const int lane = tid - 32;
     const int wl = b, wj = in.d - 1 - b;
-    for (int m = 0; m < wl; ++m) B.I.idx[(int64_t)z * (wl + 1) + m] = L.idx[p * wl + m];
-    B.I.idx[(int64_t)z * (wl + 1) + wl] = (int32_t)i;
-    B.I.lin[z] = L.lin[p] + i * in.stride[b];
-    B.I.sum[z] = L.sum[p] + (int32_t)i;
-    B.J.idx[(int64_t)z * wj] = (int32_t)j;
-    for (int m = 0; m < wj - 1; ++m) B.J.idx[(int64_t)z * wj + 1 + m] = Rset.idx[q * (wj - 1) + m];
-    B.J.lin[z] = j * in.stride[b + 1] + Rset.lin[q];
-    B.J.sum[z] = (int32_t)j + Rset.sum[q];
-    B.prow[z] = (int32_t)as;
-    B.pcol[z] = (int32_t)cs;
+    if (lane < wl) B.I.idx[(int64_t)z * (wl + 1) + lane] = L.idx[p * wl + lane];
+    if (lane == wl) B.I.idx[(int64_t)z * (wl + 1) + wl] = (int32_t)i;
+    if (lane == 0) B.J.idx[(int64_t)z * wj] = (int32_t)j;
+    if (lane >= 1 && lane < wj) B.J.idx[(int64_t)z * wj + lane] = Rset.idx[q * (wj - 1) + lane - 1];
+    if (lane == 16) B.I.lin[z] = L.lin[p] + i * in.stride[b];
+    if (lane == 17) B.I.sum[z] = L.sum[p] + (int32_t)i;
+    if (lane == 18) B.J.lin[z] = j * in.stride[b + 1] + Rset.lin[q];
+    if (lane == 19) B.J.sum[z] = (int32_t)j + Rset.sum[q];
+    if (lane == 20) {
+      B.prow[z] = (int32_t)as;
+      B.pcol[z] = (int32_t)cs;
+    }
   }
   double *hc = B.hc + (int64_t)z * cap;
   double *hp = B.hpiv + (int64_t)z * cap;
   for (int t = tid; t < z; t += NT) {
-    const double c = B.R[(int64_t)t * B.ldR + cs], q = B.T[(int64_t)t * B.ldT + as];
+    const double c = B.R[(int64_t)t * B.ldR + cs], v = B.T[(int64_t)t * B.ldT + as];
+    sm.key[t] = hil ? B.J.sum[t] : B.pcol[t];
     hc[t] = c;
-    hp[t] = q;
+    hp[t] = v;
     sm.hcs[t] = c;
-    sm.hps[t] = q;
-    sm.brow[t] = sb_entry(in, b, as, B.pcol[t]);
+    sm.hps[t] = v;
   }
-  if (tid == NT - 1) sm.apiv = sb_entry(in, b, as, cs);
+  if (tid == NT - 1) sm.lsum = L.sum[p] + (int32_t)i;
+  if (tid == NT - 2) sm.rsum = Rset.sum[q] + (int32_t)j;
+  if (ustage)
+    for (int x = tid; x < z * z; x += NT) {
+      const int t = x / z, u = x - t * z;
+      sm.us[x] = B.U[(int64_t)t * cap + u];
+    }
+  __syncthreads();
+  // the pivot row's entries A(a*, c_t) and A(a*, c*)
+  for (int t = tid; t < z; t += NT)
+    sm.brow[t] = hil ? in.hilb[sm.lsum + sm.key[t]] : sb_entry(in, b, as, sm.key[t]);
+  if (tid == NT - 1) sm.apiv = hil ? in.hilb[sm.lsum + sm.rsum] : sb_entry(in, b, as, cs);
   __syncthreads();
   if (tid == 0) {
     const double piv = __dsub_rn(sm.apiv, chain(sm.hps, 1, sm.hcs, 1, z));
@@ -1150,18 +1177,20 @@ __device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int
   if (!sm.flag) return false;
   const double delta = sm.delta;
   double *U = B.U;
+  const double *Ur = ustage ? sm.us : U;
+  const int64_t ldu = ustage ? z : cap;
   // U a and b U side by side: lanes [0, z) take the rows, [z, 2z) the columns
   for (int x = tid; x < 2 * z; x += NT) {
     if (x < z)
-      sm.ua[x] = chain(U + (int64_t)x * cap, 1, sm.hcs, 1, z);
+      sm.ua[x] = chain(Ur + (int64_t)x * ldu, 1, sm.hcs, 1, z);
     else
-      sm.bu[x - z] = chain(sm.brow, 1, U + (x - z), cap, z);
+      sm.bu[x - z] = chain(sm.brow, 1, Ur + (x - z), ldu, z);
   }
   __syncthreads();
   for (int x = tid; x < z * z; x += NT) {
     const int t = x / z, u = x - t * z;
     const double du = __dmul_rn(delta, sm.ua[t]);
-    U[(int64_t)t * cap + u] = __fma_rn(du, sm.bu[u], U[(int64_t)t * cap + u]);
+    U[(int64_t)t * cap + u] = __fma_rn(du, sm.bu[u], Ur[(int64_t)t * ldu + u]);
   }
   for (int t = tid; t < z; t += NT) {
     U[(int64_t)t * cap + z] = -__dmul_rn(delta, sm.ua[t]);
@@ -1202,9 +1231,10 @@ __device__ void stored_step(Ctrl &cr, int b) {
 // stop test and pivot append for bond b on its merged best (block-wide): add
 // the pivot while the best |E| exceeds tau * rms(X) and the cap allows.  The
 // bond's own rank is the only rank this touches, so bonds decide in parallel.
-__device__ void finalize_bond(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
-  const uint64_t key = ld_cg(cr.best_key[b]);
-  const int32_t row = ld_cg(cr.best_row[b]), col = ld_cg(cr.best_col[b]);
+// The values come from the caller (every thread holds the same ones).
+__device__ void finalize_bond_v(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm, uint64_t key,
+                                int32_t row, int32_t col, int32_t rb, double tau, double xrms,
+                                int32_t maxr) {
   __syncthreads();
   if (key > KEY_INF || row < 0) {
     fail_instance(cr, 4);  // TTC_ERR_NONFINITE
@@ -1213,10 +1243,9 @@ __device__ void finalize_bond(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm
     return;
   }
   const double v = __longlong_as_double((long long)key);
-  const int32_t rb = ld_cg(cr.r[b]);
-  const bool add = v > ld_cg(cr.tau) * ld_cg(cr.xrms) && v > 0.0 && rb < ld_cg(cr.maxr[b]);
+  const bool add = v > tau * xrms && v > 0.0 && rb < maxr;
   bool ok = true;
-  if (add) ok = append_pivot(in, cr, b, row, col, sm);
+  if (add) ok = append_pivot(in, cr, b, row, col, rb, sm);
   if (add && ok && in.stored) stored_step(cr, b);
   if (!ok) fail_instance(cr, 4);
   __syncthreads();
@@ -1227,26 +1256,58 @@ __device__ void finalize_bond(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm
   __syncthreads();
 }
 
-// FP64 form: merge the tile candidates of bond b (the Allgather of Alg. 3)
-__device__ void merge_bond_fp64(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
-  const int64_t nt = ld_cg(cr.ntiles[b]);
+// the same with the best and the words read from the control block
+__device__ void finalize_bond(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
+  const uint64_t key = ld_cg(cr.best_key[b]);
+  const int32_t row = ld_cg(cr.best_row[b]), col = ld_cg(cr.best_col[b]);
+  finalize_bond_v(in, cr, b, sm, key, row, col, ld_cg(cr.r[b]), ld_cg(cr.tau), ld_cg(cr.xrms),
+                  ld_cg(cr.maxr[b]));
+}
+
+// FP64 decide item of bond b: the control words it needs in one round of
+// parallel loads, the merge of the tile candidates (the Allgather of Alg. 3),
+// then the stop test on the merged best as it stands
+__device__ void decide_bond_fp64(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
+  const int tid = threadIdx.x;
+  if (tid == 0) sm.q_nt = ld_cg(cr.ntiles[b]);
+  if (tid == 1) sm.q_r = ld_cg(cr.r[b]);
+  if (tid == 2) sm.q_tau = ld_cg(cr.tau);
+  if (tid == 3) sm.q_xrms = ld_cg(cr.xrms);
+  if (tid == 4) sm.q_maxr = ld_cg(cr.maxr[b]);
+  if (tid == 5 && in.stored) sm.q_prow = ld_cg(cr.plan_rows[b]);
+  if (tid == 6 && in.stored) sm.q_pcol = ld_cg(cr.plan_cols[b]);
+  __syncthreads();
+  if (in.stored && tid == 0) {
+    // the screen just stored every entry of the superblock and applied the
+    // pending rank-one step
+    cr.st_rows[b] = sm.q_prow;
+    cr.st_cols[b] = sm.q_pcol;
+    cr.e_pend[b] = 0;
+    if (b == 0) cr.steal = 0;  // tile counter of the next screen
+  }
+  const int64_t nt = sm.q_nt;
   KeyBest best{0ull, LLONG_MAX, -1, -1};
   const Cand *cand = in.cand + in.bond[b].cand_base;
   int bad = 0;
-  for (int64_t t = threadIdx.x; t < nt; t += NT) {
+  for (int64_t t = tid; t < nt; t += NT) {
     KeyBest o{cand[t].key, cand[t].lin, cand[t].row, cand[t].col};
     bad += o.row == -1;  // -2 marks a slot left empty on purpose
     kb_take(best, o);
   }
   if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
   best = block_best(best, sm.rk, sm.rl, sm.rr, sm.rc);
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     cr.best_key[b] = best.key;
     cr.best_lin[b] = best.lin;
     cr.best_row[b] = best.row;
     cr.best_col[b] = best.col;
+    sm.rk[0] = best.key;
+    sm.rr[0] = best.row;
+    sm.rc[0] = best.col;
   }
   __syncthreads();
+  finalize_bond_v(in, cr, b, sm, sm.rk[0], sm.rr[0], sm.rc[0], sm.q_r, sm.q_tau, sm.q_xrms,
+                  sm.q_maxr);
 }
 
 // mixed forms, part 1 for bond b: re-score the top-k tile bests in FP64,
@@ -1422,25 +1483,32 @@ __device__ void verify_instance(const InstDev &in, Ctrl &cr, DecideSmem &sm) {
   }
 }
 
-// decide work items: (instance, bond) for screened instances, (instance, -1)
-// for instances waiting for their verification; CTA g takes items g, g + G, ..
+// decide work items.  Every instance contributes nb + 1 items, numbered
+// alike by every CTA whatever the instance's state: item 0 the verification
+// (instance, -1), items 1..nb the bonds; place g takes items g, g + G, ...
+// Each item checks its own eligibility against the decide kind the screen
+// phase fixed.  The numbering must not depend on words that items rewrite
+// during the phase (state, screened, pending): a CTA that read them late
+// would number the items differently, and one bond would be decided twice.
 template <class F>
 __device__ void for_decide_items(const RunArgs &ra, bool second, F &&f) {
-  int64_t j = 0;
+  const int64_t G = gridDim.x;
+  int64_t first = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
-    const int st = ld_cg(cr.state);
-    if (st == ST_DONE) continue;
-    if (!second && st == ST_VERIFY) {
-      if (j++ % gridDim.x == s_place) f(ii, -1);
-      continue;
+    const int64_t end = first + in.nb + 1;
+    for (int64_t x = first + ((s_place - first) % G + G) % G; x < end; x += G) {
+      const int slot = (int)(x - first) - 1;
+      const int kind = ld_cg(cr.dkind);
+      if (slot < 0) {
+        if (!second && kind == DK_VERIFY) f(ii, -1);
+      } else if (kind == DK_BONDS && ld_cg(cr.state) != ST_DONE &&
+                 (!second || ld_cg(cr.pending[slot]))) {
+        f(ii, slot);
+      }
     }
-    if (!ld_cg(cr.screened)) continue;
-    for (int b = 0; b < in.nb; ++b) {
-      if (second && !ld_cg(cr.pending[b])) continue;
-      if (j++ % gridDim.x == s_place) f(ii, b);
-    }
+    first = end;
   }
 }
 
@@ -1451,19 +1519,7 @@ __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
     if (b < 0) {
       verify_instance(in, cr, sm.d);
     } else if (in.prec == P_FP64) {
-      if (in.stored) {
-        // the screen just stored every entry of the superblock and applied
-        // the pending rank-one step
-        if (threadIdx.x == 0) {
-          cr.st_rows[b] = ld_cg(cr.plan_rows[b]);
-          cr.st_cols[b] = ld_cg(cr.plan_cols[b]);
-          cr.e_pend[b] = 0;
-          if (b == 0) cr.steal = 0;  // tile counter of the next screen
-        }
-        __syncthreads();
-      }
-      merge_bond_fp64(in, cr, b, sm.d);
-      finalize_bond(in, cr, b, sm.d);
+      decide_bond_fp64(in, cr, b, sm.d);
     } else {
       merge_bond_mixed(in, cr, b, sm.d);
     }
@@ -1494,7 +1550,6 @@ __device__ void phase_decide2(const RunArgs &ra, PhaseSmem &sm) {
       cr.best_lin[b] = best.lin;
       cr.best_row[b] = best.row;
       cr.best_col[b] = best.col;
-      cr.pending[b] = 0;
     }
     __syncthreads();
     finalize_bond(in, cr, b, d);
