@@ -950,6 +950,79 @@ __device__ void screen_bookkeeping(const InstDev &in, const int32_t *r, const Ti
   cw.screened = 1;
 }
 
+// A carried 32-wide tile of bond b by one warp (lane = column): every load in
+// one round, the pending rank-one step E(a,c) = fma(ew[a], erow[c], E(a,c))
+// and its stores, then the tile's best |E| (ties: lowest linear index).  The
+// tile lies in one block (p, q) of the superblock, where the linear index is
+// L.lin[p] + R.lin[q] + i stride_b + j stride_{b+1}: the ties need no loads.
+// Eight tiles per CTA are in flight instead of one.
+__device__ __noinline__ void screen_carried_warp(const InstDev &in, int b, int64_t r0, int nr,
+                                                 int64_t c0, int nc, int pend, Cand *out,
+                                                 int spt) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const BondDev &B = in.bond[b];
+  const int lane = threadIdx.x & 31;
+  const int64_t ld = B.ldR;
+  const bool col_ok = lane < nc;
+  const int64_t nb0 = in.n[b], nb1 = in.n[b + 1];
+  const int64_t p = r0 / nb0, i0 = r0 - p * nb0;
+  const int64_t q = c0 / nb1, j0 = c0 - q * nb1;
+  double ev[32];
+#pragma unroll
+  for (int rr = 0; rr < 32; ++rr)
+    ev[rr] = (col_ok && rr < nr) ? B.E[(r0 + rr) * ld + c0 + lane] : 0.0;
+  const int64_t lp = lane == 0 ? left_set(in, b).lin[p] : 0;
+  const int64_t rq = lane == 1 ? right_set(in, b).lin[q] : 0;
+  if (pend) {
+    const double wa = lane < nr ? B.ew[r0 + lane] : 0.0;
+    const double er = col_ok ? B.erow[c0 + lane] : 0.0;
+#pragma unroll
+    for (int rr = 0; rr < 32; ++rr) {
+      const double w = __shfl_sync(FULL, wa, rr);
+      if (rr < nr && col_ok) {
+        ev[rr] = __fma_rn(w, er, ev[rr]);
+        B.E[(r0 + rr) * ld + c0 + lane] = ev[rr];
+      }
+    }
+  }
+  // the lane's best: rows in order, only a larger key replaces (in one
+  // column the earlier row has the lower linear index)
+  uint64_t bk = 0;
+  int brr = -1;
+#pragma unroll
+  for (int rr = 0; rr < 32; ++rr) {
+    if (rr < nr && col_ok) {
+      const uint64_t k = abs_key(ev[rr]);
+      if (brr < 0 || k > bk) {
+        bk = k;
+        brr = rr;
+      }
+    }
+  }
+  int64_t bl = brr >= 0 ? (i0 + brr) * in.stride[b] + (j0 + lane) * in.stride[b + 1] : LLONG_MAX;
+  int bcol = lane;
+  for (int off = 16; off > 0; off >>= 1) {
+    const uint64_t ok = __shfl_xor_sync(FULL, bk, off);
+    const int64_t ol = __shfl_xor_sync(FULL, bl, off);
+    const int orr = __shfl_xor_sync(FULL, brr, off);
+    const int oc = __shfl_xor_sync(FULL, bcol, off);
+    if (orr >= 0 && (brr < 0 || ok > bk || (ok == bk && ol < bl))) {
+      bk = ok;
+      bl = ol;
+      brr = orr;
+      bcol = oc;
+    }
+  }
+  const int64_t LP = __shfl_sync(FULL, lp, 0), RQ = __shfl_sync(FULL, rq, 1);
+  if (lane == 0) {
+    out->key = bk;
+    out->lin = LP + RQ + bl;
+    out->row = (int32_t)(r0 + brr);
+    out->col = (int32_t)(c0 + bcol);
+    for (int k = 1; k < spt; ++k) out[k] = Cand{0ull, LLONG_MAX, -2, -2};
+  }
+}
+
 __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, PhaseSmem &sm) {
   const Ctrl &cr = *in.ctrl;
   int32_t *ctr = &in.ctrl->steal;
@@ -957,6 +1030,7 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
   __shared__ TileGeo s_geo[TTC_MAXB];
   __shared__ int32_t s_sr[TTC_MAXB], s_sc[TTC_MAXB], s_pend[TTC_MAXB];
   __shared__ int32_t s_tr0[TTC_MAXB], s_tc0[TTC_MAXB];
+  __shared__ int32_t s_warp[TTC_MAXB];  // carried tiles go to single warps
   __shared__ int32_t s_item;
   __syncthreads();
   if (threadIdx.x < in.nb) {
@@ -972,23 +1046,29 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
     s_pend[b] = ld_cg(cr.e_pend[b]);
     s_tr0[b] = tr0;
     s_tc0[b] = tc0;
+    s_warp[b] = g.te == 32 && g.pr > 0 && g.pc > 0;
   }
   __syncthreads();
   // with fewer fresh tiles than CTAs, fresh tiles go out as quarters
   // (32 x 32) so that their FP64 work spreads over four times as many CTAs;
   // candidate slots are then STORED_SLOTS per tile, else one
-  int32_t nf = 0, ncar = 0;
+  int32_t nf = 0, ncar = 0, nwc = 0;
   for (int b = 0; b < in.nb; ++b) {
     const int32_t nt = s_geo[b].nrt * s_geo[b].nct, nc = s_tr0[b] * s_tc0[b];
     nf += nt - nc;
-    ncar += nc;
+    if (s_warp[b])
+      nwc += nc;
+    else
+      ncar += nc;
   }
   const bool quarters = s_geo[0].te == 64 && nf < (int32_t)gridDim.x;
   const int32_t spt = quarters ? STORED_SLOTS : 1;  // slots per tile
   const int32_t nfresh = spt * nf, ntot = nfresh + ncar;
   if (blockIdx.x == 0 && threadIdx.x == 0) screen_bookkeeping(in, r, s_geo, s_sr, s_sc, s_pend, spt);
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
+  // item s_place first, then items G, G + 1, ... from the counter (every CTA
+  // fetching at once from one address would queue at its L2 slice)
+  for (int32_t pass = 0;; ++pass) {
+    if (threadIdx.x == 0) s_item = pass == 0 ? s_place : (int32_t)gridDim.x + atomicAdd(ctr, 1);
     __syncthreads();
     int32_t j = s_item;
     __syncthreads();
@@ -1013,7 +1093,7 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
     for (int b = 0; b < in.nb; ++b) {
       const TileGeo &g = s_geo[b];
       const int32_t tr0 = s_tr0[b], tc0 = s_tc0[b];
-      const int32_t cnt = fresh ? g.nrt * g.nct - tr0 * tc0 : tr0 * tc0;
+      const int32_t cnt = fresh ? g.nrt * g.nct - tr0 * tc0 : (s_warp[b] ? 0 : tr0 * tc0);
       if (j >= cnt) {
         j -= cnt;
         continue;
@@ -1053,6 +1133,32 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
           for (int k = 1; k < spt; ++k) slot[k] = Cand{0ull, LLONG_MAX, -2, -2};
       }
       break;
+    }
+  }
+  // carried tiles of the warp bonds, a tile per warp, dealt statically (they
+  // cost alike): warp w of place s takes tiles s + G w, s + G (w + W), ...
+  // so that the first tiles land on distinct SMs
+  if (nwc > 0) {
+    const int32_t G = gridDim.x, nw = NT / 32;
+    for (int32_t j = s_place + G * (int32_t)(threadIdx.x >> 5); j < nwc; j += G * nw) {
+      int32_t k = j;
+      for (int b = 0; b < in.nb; ++b) {
+        if (!s_warp[b]) continue;
+        const TileGeo &g = s_geo[b];
+        const int32_t tc0 = s_tc0[b], cnt = s_tr0[b] * tc0;
+        if (k >= cnt) {
+          k -= cnt;
+          continue;
+        }
+        const int32_t tr = k / tc0, tc = k - tr * tc0;
+        int64_t r0, c0;
+        int nr, nc;
+        tile_rows(in, g, b, tr, r0, nr);
+        tile_cols(in, g, b, tc, c0, nc);
+        Cand *slot = in.cand + in.bond[b].cand_base + (int64_t)(tr * g.nct + tc) * spt;
+        screen_carried_warp(in, b, r0, nr, c0, nc, s_pend[b], slot, spt);
+        break;
+      }
     }
   }
 }
