@@ -1136,12 +1136,14 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
     }
   }
   // carried tiles of the warp bonds, a tile per warp, dealt statically (they
-  // cost alike): warp w of place s takes tiles s + G w, s + G (w + W), ...
-  // so that the first tiles land on distinct SMs
+  // cost alike) after the block items: warp slot x = s + G (w + W t) of place
+  // s, warp w takes tile x - ntot, so the first tiles land on distinct SMs
+  // that hold no block item
   if (nwc > 0) {
     const int32_t G = gridDim.x, nw = NT / 32;
-    for (int32_t j = s_place + G * (int32_t)(threadIdx.x >> 5); j < nwc; j += G * nw) {
-      int32_t k = j;
+    for (int32_t x = s_place + G * (int32_t)(threadIdx.x >> 5); x < ntot + nwc; x += G * nw) {
+      if (x < ntot) continue;
+      int32_t k = x - ntot;
       for (int b = 0; b < in.nb; ++b) {
         if (!s_warp[b]) continue;
         const TileGeo &g = s_geo[b];
@@ -1716,9 +1718,11 @@ __device__ __forceinline__ void pivot_col_entries(const InstDev &in, int b, int6
 // from the triangles staged in shared memory (ST: row z at z (z - 1) / 2)
 // or from the bond's arrays (row z at z * cap), the next row loading
 // during this step when PF.
+__device__ void stage_history(const BondDev &B, int nz, int nw, ReplaySmem &rs);
+
 template <int K, bool PF>
 __device__ __noinline__ void replay_row_warp(const InstDev &in, int b, int64_t a, int nz,
-                                             const ReplaySmem *st) {
+                                             ReplaySmem *st, bool valid, int nw) {
   const BondDev &B = in.bond[b];
   const int lane = threadIdx.x & 31;
   const int64_t cap = B.cap;
@@ -1744,6 +1748,10 @@ __device__ __noinline__ void replay_row_warp(const InstDev &in, int b, int64_t a
       en[k] = t < nz ? sb_entry(in, b, a, B.pcol[t]) : 0.0;
     }
   }
+  // the staging's round trip overlaps the entries'; every replay warp of
+  // the CTA takes part in it, rows past n_b included
+  if (st) stage_history(B, nz, nw, *st);
+  if (!valid) return;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     tr[k] = 0.0;
@@ -1858,16 +1866,15 @@ __device__ int32_t replay_chunks(const InstDev &in, int b, int64_t p, int nz, in
     for (int32_t ch = (s_place - cbase + G) % G; ch < nch; ch += G) {
       const int64_t i = (int64_t)ch * W + warp;
       if (nz <= LANE_NZ) {
-        stage_history(B, nz, W, rs);
-        if (i < nit) replay_row_warp<1, true>(in, b, p * nit + i, nz, &rs);
+        replay_row_warp<1, true>(in, b, p * nit + min(i, nit - 1), nz, &rs, i < nit, W);
       } else if (i < nit) {
         const int64_t a = p * nit + i;
         if (nz <= 64)
-          replay_row_warp<2, true>(in, b, a, nz, nullptr);
+          replay_row_warp<2, true>(in, b, a, nz, nullptr, true, W);
         else if (nz <= 128)
-          replay_row_warp<4, true>(in, b, a, nz, nullptr);
+          replay_row_warp<4, true>(in, b, a, nz, nullptr, true, W);
         else
-          replay_row_warp<8, false>(in, b, a, nz, nullptr);
+          replay_row_warp<8, false>(in, b, a, nz, nullptr, true, W);
       }
     }
   }
