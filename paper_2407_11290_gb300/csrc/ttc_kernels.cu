@@ -461,16 +461,27 @@ __device__ __forceinline__ void tile_chain_fp64(const BondDev &B, int K, int64_t
   for (int u = 0; u < U; ++u)
 #pragma unroll
     for (int v = 0; v < U; ++v) acc[u][v] = 0.0;
+  // a chunk's staging issues all its loads before the first store (one round
+  // trip to L2 instead of one per loop pass)
+  constexpr int PER = KC * TE / NT;
+  static_assert(KC * TE % NT == 0, "staging passes");
   for (int t0 = 0; t0 < K; t0 += KC) {
     const int kc = min(KC, K - t0);
-    __syncthreads();
-    for (int x = tid; x < kc * TE; x += NT) {
-      const int tt = x / TE, rr = x - tt * TE;
-      sm.op.d.Ts[tt][rr] = rr < nr ? B.T[(int64_t)(t0 + tt) * B.ldT + r0 + rr] : 0.0;
+    double tl[PER], rl[PER];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+      const int x = tid + NT * m, tt = x / TE, ee = x - tt * TE;
+      tl[m] = (tt < kc && ee < nr) ? B.T[(int64_t)(t0 + tt) * B.ldT + r0 + ee] : 0.0;
+      rl[m] = (tt < kc && ee < nc) ? B.R[(int64_t)(t0 + tt) * B.ldR + c0 + ee] : 0.0;
     }
-    for (int x = tid; x < kc * TE; x += NT) {
-      const int tt = x / TE, cc = x - tt * TE;
-      sm.op.d.Rs[tt][cc] = cc < nc ? B.R[(int64_t)(t0 + tt) * B.ldR + c0 + cc] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+      const int x = tid + NT * m, tt = x / TE, ee = x - tt * TE;
+      if (tt < kc) {
+        sm.op.d.Ts[tt][ee] = tl[m];
+        sm.op.d.Rs[tt][ee] = rl[m];
+      }
     }
     __syncthreads();
     for (int tt = 0; tt < kc; ++tt) {
@@ -1856,7 +1867,6 @@ __device__ void stage_history(const BondDev &B, int nz, int nw, ReplaySmem &rs) 
 // SMs and the dependent FP64 chains run at their latency
 __device__ int32_t replay_chunks(const InstDev &in, int b, int64_t p, int nz, int32_t &cbase,
                                  int W, ReplaySmem &rs) {
-  const BondDev &B = in.bond[b];
   const int64_t nit = in.n[b];
   const int32_t G = gridDim.x;
   const int32_t nch = (int32_t)((nit + W - 1) / W);
