@@ -151,7 +151,7 @@ struct Cand {            // one screen candidate (max |E| of a tile, or top-k)
 
 struct Barrier {
   unsigned int count;
-  unsigned int gen;
+  unsigned int gen;      // unused (the arrival count alone orders the barriers)
   int32_t abort;
   int32_t where;         // first wait that ran out
   int32_t overrun;       // the sweep cap was reached before every instance finished

@@ -117,10 +117,15 @@ __shared__ InstDev s_inst0;
 // items (pivot steps, replays) then do not queue for the FP64 pipe, which
 // is shared by the whole SM.  blockIdx.x until the order is known.
 __shared__ int32_t s_place;
+// grid barriers this CTA has passed in the running launch
+__shared__ uint32_t s_bar_epoch;
 
 __device__ void cache_inst0(const RunArgs &ra) {
   static_assert(sizeof(InstDev) % 8 == 0, "InstDev copies as 8-byte words");
-  if (threadIdx.x == 0) s_place = blockIdx.x;
+  if (threadIdx.x == 0) {
+    s_place = blockIdx.x;
+    s_bar_epoch = 0u;
+  }
   const unsigned long long *src = reinterpret_cast<const unsigned long long *>(ra.insts[0]);
   unsigned long long *dst = reinterpret_cast<unsigned long long *>(&s_inst0);
   for (int i = threadIdx.x; i < (int)(sizeof(InstDev) / 8); i += blockDim.x) dst[i] = src[i];
@@ -187,26 +192,32 @@ __device__ double block_sum(double v, double *red) {
 // ---------------------------------------------------------------------------
 // grid barrier for the persistent form: arrive, then wait for the generation
 // to change; every wait gives up after wait_ns and raises the abort flag.
+// Grid barrier of the persistent kernel.  The arrival counter only rises
+// (the host clears it before each launch): the k-th barrier completes when
+// it reaches k G, so a CTA arrives with one atomic and polls the same word.
+// There is no reset or generation flip by the last arrival, whose extra
+// round trips to L2 were on every barrier's critical path.  Every wait is
+// bounded by wait_ns; on expiry the CTA records where, raises abort (which
+// every poller checks) and returns false.
 __device__ bool grid_barrier(const RunArgs &ra, int where) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
     Barrier *bar = ra.bar;
-    volatile unsigned int *vgen = &bar->gen;
+    volatile unsigned int *vcount = &bar->count;
     volatile int32_t *vabort = &bar->abort;
-    const unsigned int g = *vgen;
-    __threadfence();
+    const unsigned int target = (s_bar_epoch + 1u) * gridDim.x;
+    s_bar_epoch += 1u;
+    __threadfence();  // this CTA's writes before its arrival
     const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
-    if (arrived == gridDim.x) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
+    if (arrived < target) {
       const uint64_t t0 = globaltimer_ns();
-      while (*vgen == g) {
-        if (*vabort) { ok = 0; break; }
-        __nanosleep(100);
+      while (*vcount < target) {
+        if (*vabort) {
+          ok = 0;
+          break;
+        }
         if (globaltimer_ns() - t0 > (uint64_t)ra.wait_ns) {
           atomicCAS(&bar->where, 0, where);
           atomicExch(&bar->abort, 1);
@@ -215,7 +226,7 @@ __device__ bool grid_barrier(const RunArgs &ra, int where) {
         }
       }
     }
-    __threadfence();
+    __threadfence();  // the other CTAs' writes after the barrier
     if (*vabort) ok = 0;
   }
   __syncthreads();
