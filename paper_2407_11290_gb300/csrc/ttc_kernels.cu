@@ -97,11 +97,20 @@ struct ReplaySmem {
   double delta[LANE_NZ];
 };
 
+// the error's samples when the tables meet: a warp's 32 samples' table rows
+// (up to 16 entries, rows padded to 17 against bank conflicts); after the
+// block reduction's words
+struct SampleSmem {
+  double red_pad[NT / 32];
+  double rows[NT / 32][32 * 17];
+};
+
 union __align__(16) PhaseSmem {
   ScreenSmem s;
   DecideSmem d;
   SpreadSmem sp;
   ReplaySmem rp;
+  SampleSmem sw;
   double red[NT / 32];
 };
 
@@ -2211,6 +2220,72 @@ __device__ double sample_residual(const InstDev &in, const int32_t *r, int pL, i
 }
 
 
+// The error's samples when the prefix and suffix tables meet (pL + pR = d,
+// rows of len <= 16): lane l of a warp takes the l-th of 32 consecutive
+// samples, as in the thread dealing of the plain loop.  The warp loads the
+// 32 samples' rows together, two rows per instruction, into shared memory,
+// and each lane then runs the contract's chain on its own two rows.  The
+// operations and their order per thread are those of sample_residual.
+__device__ __noinline__ double samples_joined(const InstDev &in, int pL, int pR, int len,
+                                              int64_t base, int64_t ns, int64_t gs, int64_t NTOT,
+                                              SampleSmem &sw) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, half = lane >> 4, el = lane & 15;
+  double *buf = sw.rows[threadIdx.x >> 5];
+  const int d = in.d;
+  double part = 0.0;
+  for (int64_t x = first_item(base, gs, NTOT);; x += NTOT) {
+    const int valid = x < base + ns;
+    if (!__any_sync(FULL, valid)) break;
+    const int64_t k = valid ? x - base : 0;
+    const double xk = valid ? in.xs[k] : 0.0;
+    int64_t eL = 0, eR = 0, st = 1;
+    for (int m = 0; m < pL; ++m) {
+      eL += sample_coord(in, k, m) * st;
+      st *= in.n[m];
+    }
+    st = 1;
+    for (int m = d - pR; m < d; ++m) {
+      eR += sample_coord(in, k, m) * st;
+      st *= in.n[m];
+    }
+    double xv[16], yv[16];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const double *tab = side == 0 ? in.tabL : in.tabR;
+      const int64_t e = side == 0 ? eL : eR;
+      double v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int sr = 2 * q + half;
+        const int64_t es = __shfl_sync(FULL, e, sr);
+        const int vs = __shfl_sync(FULL, valid, sr);
+        v[q] = (vs && el < len) ? tab[es * len + el] : 0.0;
+      }
+      __syncwarp();  // the previous rows are read
+#pragma unroll
+      for (int q = 0; q < 16; ++q) buf[(2 * q + half) * 17 + el] = v[q];
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        if (side == 0)
+          xv[t] = buf[lane * 17 + t];
+        else
+          yv[t] = buf[lane * 17 + t];
+      }
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+      if (t < len) acc = __fma_rn(xv[t], yv[t], acc);
+    if (valid) {
+      const double e = __dsub_rn(xk, acc);
+      part = __fma_rn(e, e, part);
+    }
+  }
+  return part;
+}
+
 __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
   __shared__ CtrlSnap snap;
   const int64_t NTOT = (int64_t)gridDim.x * NT;
@@ -2301,9 +2376,14 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
       const int64_t ns = in.nsamples;
       int pL, pR;
       choose_split(in, rn, pL, pR);
-      for (int64_t x = first_item(base, gs, NTOT); x < base + ns; x += NTOT) {
-        const double e = sample_residual(in, rn, pL, pR, x - base);
-        part = __fma_rn(e, e, part);
+      const int jl = pL >= 2 && pR >= 2 && pL + pR == in.d ? (int)core_s(in, rn, pL) : 0;
+      if (jl > 0 && jl <= 16) {
+        part = samples_joined(in, pL, pR, jl, base, ns, gs, NTOT, sm.sw);
+      } else {
+        for (int64_t x = first_item(base, gs, NTOT); x < base + ns; x += NTOT) {
+          const double e = sample_residual(in, rn, pL, pR, x - base);
+          part = __fma_rn(e, e, part);
+        }
       }
       base += ns;
       const double s = block_sum(part, sm.red);
