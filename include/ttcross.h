@@ -68,10 +68,11 @@ typedef enum {
    ttcross_create only (the data is copied to the device). */
 typedef struct {
   int32_t kind; /* ttc_gen_kind */
-  /* TTC_GEN_TT: ranks rho[0..d] with rho[0] = rho[d] = 1, rho[m] <= 256, and
-     the cores concatenated, core m laid out [rho_m][n_m][rho_{m+1}]
-     row-major (doubles).  The entry is the left-to-right product of the core
-     slices, each dot product a serial FMA chain. */
+  /* TTC_GEN_TT: ranks rho[0..d] with rho[0] = rho[d] = 1, 1 <= rho[m] <= 160
+     (else TTC_ERR_INVALID_ARG), and the cores concatenated, core m laid out
+     [rho_m][n_m][rho_{m+1}] row-major (doubles).  The entry is the
+     left-to-right product of the core slices, each dot product a serial FMA
+     chain. */
   const int32_t *tt_ranks;
   const double *tt_cores;
   /* TTC_GEN_MAXWELLIAN: modes ordered (x_0..x_{dx-1}, v_0..v_{dv-1});

@@ -278,8 +278,8 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     if (gen->tt_ranks[0] != 1 || gen->tt_ranks[d] != 1)
       return fail(TTC_ERR_INVALID_ARG, "TT ranks must start and end with 1");
     for (int m = 1; m < d; ++m)
-      if (gen->tt_ranks[m] < 1 || gen->tt_ranks[m] > 32)
-        return fail(TTC_ERR_INVALID_ARG, "TT generator ranks must be in [1,32]");
+      if (gen->tt_ranks[m] < 1 || gen->tt_ranks[m] > TT_GEN_RMAX)
+        return fail(TTC_ERR_INVALID_ARG, "TT generator ranks must be in [1,%d]", TT_GEN_RMAX);
   } else if (gen->kind == TTC_GEN_MAXWELLIAN) {
     if (gen->dx < 1 || gen->dv < 1 || gen->dx + gen->dv != d)
       return fail(TTC_ERR_INVALID_ARG, "Maxwellian needs dx, dv >= 1 and dx + dv = d");

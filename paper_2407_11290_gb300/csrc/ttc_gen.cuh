@@ -6,9 +6,9 @@
 namespace ttc {
 
 // TT given by cores: left-to-right product of the slices, each dot product a
-// serial FMA chain (device ranks <= 32).
+// serial FMA chain (ranks <= TT_GEN_RMAX; the vectors live in local memory).
 __device__ __noinline__ double gen_tt(const InstDev &in, const int32_t *idx) {
-  double v[32], w[32];
+  double v[TT_GEN_RMAX], w[TT_GEN_RMAX];
   const int d = in.d;
   int rl = in.rho[1];
   const double *G0 = in.tt + in.core_off[0];

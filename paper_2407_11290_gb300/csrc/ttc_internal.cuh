@@ -24,6 +24,7 @@
 
 namespace ttc {
 
+constexpr int TT_GEN_RMAX = 160;  // largest TT rank of a TT-cores generator
 constexpr int BM = 64, BN = 64;   // screen tile (superblock rows x columns)
 constexpr int RCAP = 256;         // largest rank capacity the kernels accept
 constexpr int GRID_CAP = 4096;    // largest persistent grid (partial-sum slots)

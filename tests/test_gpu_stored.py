@@ -203,3 +203,31 @@ def test_stored_maxwellian6d_reaches_eps_above_rank_128(tt):
         num += (x - v[0, 0]) ** 2
         den += x * x
     assert (num / den) ** 0.5 <= 3 * w["eps"]
+
+
+@pytest.mark.parametrize("ranks,n", [([1, 10, 48, 48, 10, 1], 10), ([1, 10, 100, 100, 10, 1], 10),
+                                     ([1, 12, 132, 132, 12, 1], 12)])
+def test_stored_long_replay_histories(tt, ranks, n):
+    """Two adjacent bonds of rank above 32: rows entering a superblock replay
+    pivot histories longer than a warp (Alg. 4 with 2, 4 and 8 entries of
+    T(a, :) per lane).  Pivots, T, R and U equal the oracle's bit for bit, and
+    the cross stops at the TT's own ranks."""
+    w = W.random_tt([n] * 5, ranks, seed=21)
+    g, rc, o, orc, ost = run_stored(tt, w, 1e-12, max(ranks) + 8, 0)
+    assert rc == orc == 0
+    assert list(g.ranks()) == ranks
+    assert_same(g, o)
+
+
+def test_recompute_long_replay_histories(tt):
+    """The recompute form on the same replays (ranks 48, two register tiles)."""
+    ranks = [1, 10, 48, 48, 10, 1]
+    w = W.random_tt([10] * 5, ranks, seed=21)
+    g = tt.TTCross(w["n"], w["gen"], max_rank=56, nsamples=0)
+    g.run(1e-12)
+    assert g.sync() == 0
+    o = oracle.Oracle(w["n"], w["gen"], 56, nthreads=NT)
+    orc, ost = o.run(1e-12, nsamples=0)
+    assert orc == 0
+    assert list(g.ranks()) == ranks
+    assert_same(g, o)
