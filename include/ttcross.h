@@ -50,7 +50,8 @@ typedef enum {
   TTC_OK = 0,
   TTC_ERR_INVALID_ARG = 1,   /* bad argument; nothing was launched */
   TTC_ERR_OOM = 2,           /* device allocation failed */
-  TTC_ERR_ZERO_START = 3,    /* X(0,...,0) == 0: the first pivot is unusable */
+  TTC_ERR_ZERO_START = 3,    /* X is zero at the origin and at every error sample:
+                                no start pivot (Alg. 1 line 1) */
   TTC_ERR_NONFINITE = 4,     /* a generated entry or residual was NaN/Inf */
   TTC_ERR_DEVICE_TIMEOUT = 5,/* a device-side wait ran past its limit */
   TTC_ERR_CUDA = 6,          /* a CUDA runtime call failed */
@@ -158,7 +159,9 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen,
                           const ttc_options *opt, ttc_handle **out);
 
 /* Runs the adaptive cross to accuracy eps (Sec. 1 eq. FrobeniusNorm, error
-   estimated as in Sec. 5) from the start pivot (0,...,0).
+   estimated as in Sec. 5).  Every bond starts from one pivot, the entry of
+   largest |X| over the error samples and the origin (Alg. 1 line 1 with a
+   zero approximation; ties to the lowest linear index), at rank 1.
    eps == 0 selects prescribed-rank mode: every bond grows to its cap.
    max_rank (<= the capacity; <= 0 means the capacity) caps every bond.
    subtensor_grid (nullable, d entries >= 1) splits every mode into that many
@@ -172,11 +175,19 @@ ttc_status ttcross_run(ttc_handle *h, double eps, int max_rank,
                        const int32_t *subtensor_grid, void *stream);
 
 /* Runs count independent instances (each created by ttcross_create) in one
-   persistent launch on `stream`.  eps[i], max_rank[i] as in ttcross_run;
-   grids may be NULL.  The handles must be distinct and live on the current
-   device. */
+   persistent launch on `stream` (the batching of many tensors of uneven
+   shape and rank in one launch; the paper runs one tensor at a time).
+   eps[i], max_rank[i] (max_rank may be NULL: every instance's capacity) and
+   grids[i] as eps, max_rank and subtensor_grid of ttcross_run; grids may be
+   NULL, and so may any grids[i] (grids[i] has d_i entries).  The handles
+   must be distinct and live on the current device.  Errors: INVALID_ARG
+   (checked on the host before anything is launched; this includes a batch
+   of two or more instances where an FP32 / float-float instance of the
+   recompute form has a non-Hilbert generator, a combination that is not
+   supported), CUDA, OOM. */
 ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps,
-                             const int32_t *max_rank, void *stream);
+                             const int32_t *max_rank, const int32_t *const *grids,
+                             void *stream);
 
 /* Waits for the last run of h and returns its device-side status. */
 ttc_status ttcross_sync(ttc_handle *h);

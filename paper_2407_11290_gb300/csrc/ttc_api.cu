@@ -179,7 +179,7 @@ ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, 
   ra.persistent = h0->opt.host_loop ? 0 : 1;
   ra.mixed = 0;
   for (int i = 0; i < count; ++i)
-    if (hs[i]->hi.prec != P_FP64) ra.mixed = 1;
+    if (hs[i]->hi.prec != P_FP64 && !hs[i]->hi.stored) ra.mixed = 1;  // refinement phases
   int64_t iters = 0;
   for (int i = 0; i < count; ++i) {
     int64_t s = hs[i]->opt.max_refine + 4;
@@ -261,8 +261,6 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     return fail(TTC_ERR_INVALID_ARG, "grid_ctas outside [0,%d]", GRID_CAP);
   if (o.residual != TTC_RESIDUAL_RECOMPUTE && o.residual != TTC_RESIDUAL_STORED)
     return fail(TTC_ERR_INVALID_ARG, "unknown residual form %d", o.residual);
-  if (o.residual == TTC_RESIDUAL_STORED && o.precision != TTC_PREC_FP64)
-    return fail(TTC_ERR_INVALID_ARG, "the stored residual form is FP64 only");
   int64_t total = 1;
   bool overflow = false;
   int64_t hsum = 0;
@@ -619,7 +617,7 @@ ttc_status ttcross_run(ttc_handle *h, double eps, int max_rank, const int32_t *s
 }
 
 ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps,
-                             const int32_t *max_rank, void *stream) {
+                             const int32_t *max_rank, const int32_t *const *grids, void *stream) {
   g_err.clear();
   if (!hs || count < 1 || !eps) return fail(TTC_ERR_INVALID_ARG, "bad batch arguments");
   for (int i = 0; i < count; ++i) {
@@ -628,12 +626,26 @@ ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return fail(TTC_ERR_INVALID_ARG, "handle %d repeated", i);
     if (hs[i]->device != hs[0]->device) return fail(TTC_ERR_INVALID_ARG, "handles on different devices");
+    const int32_t *gi = grids ? grids[i] : nullptr;
+    if (gi)
+      for (int m = 0; m < hs[i]->d; ++m)
+        if (gi[m] < 1 || gi[m] > hs[i]->n[m])
+          return fail(TTC_ERR_INVALID_ARG, "grids[%d][%d]=%d outside [1,n]", i, m, gi[m]);
+    // An FP32 / float-float recompute-form batch of non-Hilbert tensors ended
+    // in an illegal address on the GPU twice; its cause is not found, so that
+    // combination is refused here, before anything is launched.
+    if (count >= 2 && hs[i]->hi.prec != P_FP64 && !hs[i]->hi.stored &&
+        hs[i]->hi.gen != TTC_GEN_HILBERT)
+      return fail(TTC_ERR_INVALID_ARG,
+                  "instance %d: a mixed-precision recompute-form batch supports the Hilbert "
+                  "generator only (use the stored residual form or FP64)", i);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   for (int i = 0; i < count; ++i) {
-    ttc_status s = ensure_cands(hs[i], nullptr);
+    const int32_t *gi = grids ? grids[i] : nullptr;
+    ttc_status s = ensure_cands(hs[i], gi);
     if (s) return s;
-    Ctrl c = make_ctrl(hs[i], eps[i], max_rank ? max_rank[i] : 0, nullptr);
+    Ctrl c = make_ctrl(hs[i], eps[i], max_rank ? max_rank[i] : 0, gi);
     k_set_ctrl<<<1, 1, 0, st>>>(hs[i]->d_ctrl, c);
     CU(cudaGetLastError());
   }

@@ -348,7 +348,7 @@ __device__ void write_plan_warp(const InstDev &in, Ctrl &cr, const int32_t *r, i
     const int64_t sc = pc > 0 ? (in.n[lane + 1] + pc - 1) / pc : 64;
     small = sr <= 32 && sc <= 32;
   }
-  const bool pieces32 = __all_sync(0xffffffffu, small) && in.prec == P_FP64;
+  const bool pieces32 = __all_sync(0xffffffffu, small) && (in.prec == P_FP64 || in.stored);
   int te = 64;
   TileGeo g = g64;
   if (pieces32) {
@@ -518,6 +518,96 @@ __device__ __forceinline__ void tile_chain_fp64(const BondDev &B, int K, int64_t
   }
 }
 
+// acc[u][v] ~ T(r0 + ty + 16u, :) R(:, c0 + tx + 16v) over t < K on the FP32
+// pipe, from the (hi, lo) FP32 shadows of T and R (mixed forms of the stored
+// screen).  SPLIT: float-float, th rh = p + pe exactly (pe by FMA), the cross
+// terms th rl + tl rh and pe join the low word, the high word is summed by
+// TwoSum and the pair renormalised every term, so the result carries about
+// 44 bits; else plain FP32 products and sums.  The pair is returned as one
+// FP64 value (hi + lo).
+template <int TE, bool SPLIT>
+__device__ __forceinline__ void tile_chain_ff(const BondDev &B, int K, int64_t r0, int nr,
+                                              int64_t c0, int nc,
+                                              double (&acc)[TE / 16][TE / 16], ScreenSmem &sm) {
+  constexpr int U = TE / 16;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float sh[U][U], sl[U][U];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+      sh[u][v] = 0.f;
+      sl[u][v] = 0.f;
+    }
+  constexpr int PER = KC * TE / NT;
+  static_assert(KC * TE % NT == 0, "staging passes");
+  for (int t0 = 0; t0 < K; t0 += KC) {
+    const int kc = min(KC, K - t0);
+    float th[PER], tl[PER], rh[PER], rl[PER];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+      const int x = tid + NT * m, tt = x / TE, ee = x - tt * TE;
+      const bool tv = tt < kc && ee < nr, rv = tt < kc && ee < nc;
+      const int64_t ot = (int64_t)(t0 + tt) * B.ldT + r0 + ee;
+      const int64_t orr = (int64_t)(t0 + tt) * B.ldR + c0 + ee;
+      th[m] = tv ? B.Thi[ot] : 0.f;
+      rh[m] = rv ? B.Rhi[orr] : 0.f;
+      tl[m] = (SPLIT && tv) ? B.Tlo[ot] : 0.f;
+      rl[m] = (SPLIT && rv) ? B.Rlo[orr] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+      const int x = tid + NT * m, tt = x / TE, ee = x - tt * TE;
+      if (tt < kc) {
+        sm.op.f.Th[tt][ee] = th[m];
+        sm.op.f.Rh[tt][ee] = rh[m];
+        if (SPLIT) {
+          sm.op.f.Tl[tt][ee] = tl[m];
+          sm.op.f.Rl[tt][ee] = rl[m];
+        }
+      }
+    }
+    __syncthreads();
+    for (int tt = 0; tt < kc; ++tt) {
+      float a[U], al[U], b[U], bl[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        a[u] = sm.op.f.Th[tt][ty + 16 * u];
+        al[u] = SPLIT ? sm.op.f.Tl[tt][ty + 16 * u] : 0.f;
+      }
+#pragma unroll
+      for (int v = 0; v < U; ++v) {
+        b[v] = sm.op.f.Rh[tt][tx + 16 * v];
+        bl[v] = SPLIT ? sm.op.f.Rl[tt][tx + 16 * v] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int v = 0; v < U; ++v) {
+          if (SPLIT) {
+            const float p = __fmul_rn(a[u], b[v]);
+            const float pe = __fmaf_rn(a[u], b[v], -p);
+            const float cross = __fmaf_rn(al[u], b[v], __fmaf_rn(a[u], bl[v], pe));
+            const float s1 = __fadd_rn(sh[u][v], p);
+            const float bb = __fsub_rn(s1, sh[u][v]);
+            const float e = __fadd_rn(__fsub_rn(sh[u][v], __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+            const float lo = __fadd_rn(sl[u][v], __fadd_rn(e, cross));
+            const float s2 = __fadd_rn(s1, lo);
+            sl[u][v] = __fsub_rn(lo, __fsub_rn(s2, s1));
+            sh[u][v] = s2;
+          } else {
+            sh[u][v] = __fmaf_rn(a[u], b[v], sh[u][v]);
+          }
+        }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int v = 0; v < U; ++v) acc[u][v] = __dadd_rn((double)sh[u][v], (double)sl[u][v]);
+}
+
 template <bool HIL, int TE>
 __device__ __noinline__ void screen_tile_fp64_t(const InstDev &in, int b, int K, int64_t r0, int nr,
                                                 int64_t c0, int nc, Cand *out, ScreenSmem &sm) {
@@ -585,7 +675,7 @@ __device__ __forceinline__ void screen_tile_fp64(const InstDev &in, int b, int K
 // and erow = E(a*, :).  Entries outside it have just entered the superblock
 // and get A - chain(T(a,:), R(:,c)) with the current factors.  Both are written
 // back to E; the tile's best |E| is kept as in the FP64 screen.
-template <bool HIL, int TE>
+template <bool HIL, int TE, int MIX>
 __device__ __noinline__ void screen_tile_stored_t(const InstDev &in, int b, int K, int64_t r0,
                                                   int nr, int64_t c0, int nc, int32_t sr,
                                                   int32_t sc, int pend, Cand *out,
@@ -632,7 +722,10 @@ __device__ __noinline__ void screen_tile_stored_t(const InstDev &in, int b, int 
     __syncthreads();  // publishes the tile metadata
   } else {
     double acc[U][U];
-    tile_chain_fp64<TE>(B, K, r0, nr, c0, nc, acc, sm);
+    if (MIX == 0)
+      tile_chain_fp64<TE>(B, K, r0, nr, c0, nc, acc, sm);
+    else
+      tile_chain_ff<TE, MIX == 2>(B, K, r0, nr, c0, nc, acc, sm);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int rr = ty + 16 * u;
@@ -691,21 +784,37 @@ __device__ __noinline__ void screen_tile_stored_t(const InstDev &in, int b, int 
   }
 }
 
+template <int MIX>
+__device__ __forceinline__ void screen_tile_stored_m(const InstDev &in, int b, int K, int64_t r0,
+                                                     int nr, int64_t c0, int nc, int te,
+                                                     int32_t sr, int32_t sc, int pend, Cand *out,
+                                                     ScreenSmem &sm) {
+  if (te == 32) {
+    if (in.gen == 0)
+      screen_tile_stored_t<true, 32, MIX>(in, b, K, r0, nr, c0, nc, sr, sc, pend, out, sm);
+    else
+      screen_tile_stored_t<false, 32, MIX>(in, b, K, r0, nr, c0, nc, sr, sc, pend, out, sm);
+  } else {
+    if (in.gen == 0)
+      screen_tile_stored_t<true, 64, MIX>(in, b, K, r0, nr, c0, nc, sr, sc, pend, out, sm);
+    else
+      screen_tile_stored_t<false, 64, MIX>(in, b, K, r0, nr, c0, nc, sr, sc, pend, out, sm);
+  }
+}
+
+// the stored screen of one tile; the mixed forms form the entries new to the
+// superblock on the FP32 pipe (FP32 or float-float products), the carried
+// ones stay FP64
 __device__ __forceinline__ void screen_tile_stored(const InstDev &in, int b, int K, int64_t r0,
                                                    int nr, int64_t c0, int nc, int te, int32_t sr,
                                                    int32_t sc, int pend, Cand *out,
                                                    ScreenSmem &sm) {
-  if (te == 32) {
-    if (in.gen == 0)
-      screen_tile_stored_t<true, 32>(in, b, K, r0, nr, c0, nc, sr, sc, pend, out, sm);
-    else
-      screen_tile_stored_t<false, 32>(in, b, K, r0, nr, c0, nc, sr, sc, pend, out, sm);
-  } else {
-    if (in.gen == 0)
-      screen_tile_stored_t<true, 64>(in, b, K, r0, nr, c0, nc, sr, sc, pend, out, sm);
-    else
-      screen_tile_stored_t<false, 64>(in, b, K, r0, nr, c0, nc, sr, sc, pend, out, sm);
-  }
+  if (in.prec == P_FP64)
+    screen_tile_stored_m<0>(in, b, K, r0, nr, c0, nc, te, sr, sc, pend, out, sm);
+  else if (in.prec == P_FP32)
+    screen_tile_stored_m<1>(in, b, K, r0, nr, c0, nc, te, sr, sc, pend, out, sm);
+  else
+    screen_tile_stored_m<2>(in, b, K, r0, nr, c0, nc, te, sr, sc, pend, out, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -1449,6 +1558,97 @@ __device__ void decide_bond_fp64(const InstDev &in, Ctrl &cr, int b, DecideSmem 
                   sm.q_maxr);
 }
 
+// Mixed stored form, decide item of bond b: the tile candidates hold the
+// best stored |E| of each tile, where the entries new to the superblock were
+// formed on the FP32 pipe.  The top-k of them (by stored |E|, ties to the
+// lowest linear index; k = topk, at most RS_K) are re-scored in FP64 as
+// A - chain(T(a,:), R(:,c)) with the current factors, and the best FP64 value
+// (same tie rule) is the candidate of the stop test.  One pass over the slots: every thread keeps
+// its own k best, then k block reductions over the threads' list heads.
+constexpr int RS_K = 8;  // candidates re-scored per bond in the mixed stored form
+__device__ void decide_bond_rescore(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
+  const int tid = threadIdx.x;
+  if (tid == 0) sm.q_nt = ld_cg(cr.ntiles[b]);
+  if (tid == 1) sm.q_r = ld_cg(cr.r[b]);
+  if (tid == 2) sm.q_tau = ld_cg(cr.tau);
+  if (tid == 3) sm.q_xrms = ld_cg(cr.xrms);
+  if (tid == 4) sm.q_maxr = ld_cg(cr.maxr[b]);
+  if (tid == 5) sm.q_prow = ld_cg(cr.plan_rows[b]);
+  if (tid == 6) sm.q_pcol = ld_cg(cr.plan_cols[b]);
+  __syncthreads();
+  if (tid == 0) {
+    cr.st_rows[b] = sm.q_prow;
+    cr.st_cols[b] = sm.q_pcol;
+    cr.e_pend[b] = 0;
+    if (b == 0) cr.steal = 0;
+  }
+  const int64_t nt = sm.q_nt;
+  const int k = (int)min((int64_t)min(in.topk, RS_K), nt);
+  const Cand *cand = in.cand + in.bond[b].cand_base;
+  KeyBest loc[RS_K];
+#pragma unroll
+  for (int j = 0; j < RS_K; ++j) loc[j] = KeyBest{0ull, LLONG_MAX, -1, -1};
+  int bad = 0;
+  for (int64_t t = tid; t < nt; t += NT) {
+    KeyBest o{cand[t].key, cand[t].lin, cand[t].row, cand[t].col};
+    bad += o.row == -1;
+    if (o.row < 0) continue;
+    // insertion into the sorted list loc[0..k-1]
+#pragma unroll
+    for (int j = 0; j < RS_K; ++j) {
+      if (j >= k) break;
+      if (loc[j].row < 0 || key_better(o.key, o.lin, loc[j].key, loc[j].lin)) {
+        const KeyBest tmp = loc[j];
+        loc[j] = o;
+        o = tmp;
+        if (o.row < 0) break;
+      }
+    }
+  }
+  if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
+  for (int j = 0; j < k; ++j) {
+    const KeyBest win = block_best(loc[0], sm.rk, sm.rl, sm.rr, sm.rc);
+    if (tid == 0) {
+      sm.skey[j] = win.key;
+      sm.slin[j] = win.lin;
+      sm.srow[j] = win.row;
+      sm.scol[j] = win.col;
+    }
+    __syncthreads();
+    if (loc[0].row >= 0 && loc[0].row == sm.srow[j] && loc[0].col == sm.scol[j]) {
+#pragma unroll
+      for (int q = 0; q + 1 < RS_K; ++q) loc[q] = loc[q + 1];
+      loc[RS_K - 1] = KeyBest{0ull, LLONG_MAX, -1, -1};
+    }
+  }
+  // FP64 re-score of the k candidates, one thread each
+  const BondDev &B = in.bond[b];
+  if (tid < k && sm.srow[tid] >= 0) {
+    const int64_t a = sm.srow[tid], c = sm.scol[tid];
+    const double e = __dsub_rn(sb_entry(in, b, a, c), chain(B.T + a, B.ldT, B.R + c, B.ldR, sm.q_r));
+    sm.skey[tid] = abs_key(e);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    KeyBest best{0ull, LLONG_MAX, -1, -1};
+    for (int j = 0; j < k; ++j) {
+      KeyBest o{sm.skey[j], sm.slin[j], sm.srow[j], sm.scol[j]};
+      kb_take(best, o);
+    }
+    cr.best_key[b] = best.key;
+    cr.best_lin[b] = best.lin;
+    cr.best_row[b] = best.row;
+    cr.best_col[b] = best.col;
+    atomicAdd((unsigned long long *)&cr.tiles_refined, (unsigned long long)k);
+    sm.rk[0] = best.key;
+    sm.rr[0] = best.row;
+    sm.rc[0] = best.col;
+  }
+  __syncthreads();
+  finalize_bond_v(in, cr, b, sm, sm.rk[0], sm.rr[0], sm.rc[0], sm.q_r, sm.q_tau, sm.q_xrms,
+                  sm.q_maxr);
+}
+
 // mixed forms, part 1 for bond b: re-score the top-k tile bests in FP64,
 // then queue for the FP64 refinement every tile whose bound reaches the best
 // exact value (when that exceeds the threshold theta: the tile could hold the
@@ -1605,9 +1805,10 @@ __device__ void verify_instance(const InstDev &in, Ctrl &cr, DecideSmem &sm) {
         cr.tau = ld_cg(cr.tau) / 10.0;
         cr.refinements = ld_cg(cr.refinements) + 1;
         cr.state = ST_SCREEN;
-        // the mixed forms certified their bests only against the old
-        // threshold: they screen again
-        sm.flag = in.prec == P_FP64 ? 1 : 0;
+        // the mixed recompute forms certified their bests only against the
+        // old threshold: they screen again; the FP64 and stored forms keep
+        // FP64 values of their bests
+        sm.flag = (in.prec == P_FP64 || in.stored) ? 1 : 0;
       }
     }
     __syncthreads();
@@ -1659,6 +1860,8 @@ __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
       verify_instance(in, cr, sm.d);
     } else if (in.prec == P_FP64) {
       decide_bond_fp64(in, cr, b, sm.d);
+    } else if (in.stored) {
+      decide_bond_rescore(in, cr, b, sm.d);
     } else {
       merge_bond_mixed(in, cr, b, sm.d);
     }

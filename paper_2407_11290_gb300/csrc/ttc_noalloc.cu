@@ -30,9 +30,10 @@ void set_last_error(const char *msg);  // ttc_api.cu: shared with ttcross_last_e
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
 constexpr int64_t kChunk = 4096;          // samples per partial-sum slot
 constexpr int kMaxChunks = 4096;          // slots -> at most 16,777,216 samples
-constexpr int kMaxRank = 128;
+constexpr int kMaxRank = 256;             // core sizes s_m: 8 register slots per lane
 constexpr int kMaxD = 16;
 constexpr int kMaxDevices = 64;
 
@@ -59,52 +60,93 @@ __device__ __forceinline__ uint64_t mix_at(uint64_t seed, uint64_t k) {
   return z ^ (z >> 31);
 }
 
-__device__ double entry(const ErrArgs &a, const int32_t *idx) {
+// index of mode m of sample k (SplitMix64 counter form, sample-major,
+// mode-minor, index = floor(x n / 2^64); entry k in column-major order when
+// every entry is used); computed alone, so no index array lives in memory
+__device__ __forceinline__ int32_t coord(const ErrArgs &a, int64_t k, int m) {
+  if (a.exhaustive) {
+    int64_t l = k;
+    for (int j = 0; j < m; ++j) l /= a.n[j];
+    return (int32_t)(l % a.n[m]);
+  }
+  return (int32_t)__umul64hi(mix_at(a.seed, (uint64_t)(k * a.d + m)), (uint64_t)a.n[m]);
+}
+
+__device__ __forceinline__ double x_at(const ErrArgs &a, int64_t k, int m) {
+  const double two_pi = 6.283185307179586476925286766559;
+  return __dmul_rn(two_pi, (double)coord(a, k, m)) / (double)a.n[m];
+}
+
+// X at sample k: the Hilbert tensor or the Maxwellian of the generator
+__device__ double entry(const ErrArgs &a, int64_t k) {
   if (a.gen == TTC_GEN_HILBERT) {
     int64_t s = 1;
-    for (int m = 0; m < a.d; ++m) s += idx[m];
+    for (int m = 0; m < a.d; ++m) s += coord(a, k, m);
     return 1.0 / (double)s;
   }
   const double two_pi = 6.283185307179586476925286766559;
-  double x[kMaxD];
   double prod_sin = 1.0, sum_x = 0.0;
   for (int m = 0; m < a.dx; ++m) {
-    x[m] = __dmul_rn(two_pi, (double)idx[m]) / (double)a.n[m];
-    prod_sin = __dmul_rn(prod_sin, sin(x[m]));
-    sum_x = __dadd_rn(sum_x, x[m]);
+    const double x = x_at(a, k, m);
+    prod_sin = __dmul_rn(prod_sin, sin(x));
+    sum_x = __dadd_rn(sum_x, x);
   }
   const double rho = __dadd_rn(1.0, __dmul_rn(a.a_rho, prod_sin));
   const double T = __dadd_rn(1.0, __dmul_rn(a.a_T, cos(sum_x)));
   double q = 0.0;
   for (int j = 0; j < a.dv; ++j) {
     const int m = a.dx + j;
-    const double v =
-        __dadd_rn(a.vmin, __dmul_rn(__dsub_rn(a.vmax, a.vmin), (double)idx[m]) / (double)(a.n[m] - 1));
-    const double u = __dmul_rn(a.a_u, cos(x[(j + 1) % a.dx]));
+    const double v = __dadd_rn(
+        a.vmin, __dmul_rn(__dsub_rn(a.vmax, a.vmin), (double)coord(a, k, m)) / (double)(a.n[m] - 1));
+    const double u = __dmul_rn(a.a_u, cos(x_at(a, k, (j + 1) % a.dx)));
     const double dvu = __dsub_rn(v, u);
     q = __dadd_rn(q, __dmul_rn(dvu, dvu));
   }
   return __dmul_rn(rho / pow(__dmul_rn(two_pi, T), 0.5 * (double)a.dv), exp(-q / __dmul_rn(2.0, T)));
 }
 
-// X~(i) = G_1(i_1) ... G_d(i_d), each dot product a serial FMA chain
-__device__ double tt_value(const ErrArgs &a, const int32_t *idx) {
-  double v[kMaxRank], w[kMaxRank];
+// X~ at sample k by one warp: X~ = G_1(i_1) ... G_d(i_d), left to right.
+// Lane l keeps v[32 j + l] (j < K) in registers; each output w[u] of a core
+// is the serial FMA chain over p = 0, 1, ... of v[p] G(p, i, u), v[p]
+// broadcast from its lane, so the order of the operations is that of a plain
+// per-sample loop and no vector lives in local memory.  Every lane returns
+// the value.
+template <int K>
+__device__ double tt_value_warp(const ErrArgs &a, int64_t k) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  double v[K], w[K];
   int rl = a.s[1];
-  for (int t = 0; t < rl; ++t) v[t] = a.core[0][(int64_t)idx[0] * rl + t];
+  {
+    const double *G = a.core[0] + (int64_t)coord(a, k, 0) * rl;
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = 32 * j + lane < rl ? G[32 * j + lane] : 0.0;
+  }
   for (int m = 1; m < a.d; ++m) {
     const int rr = a.s[m + 1];
-    const double *G = a.core[m] + (int64_t)idx[m] * rr;
     const int64_t ld = a.n[m] * rr;
-    for (int u = 0; u < rr; ++u) {
-      double acc = 0.0;
-      for (int p = 0; p < rl; ++p) acc = __fma_rn(v[p], G[p * ld + u], acc);
-      w[u] = acc;
+    const double *G = a.core[m] + (int64_t)coord(a, k, m) * rr;
+#pragma unroll
+    for (int j = 0; j < K; ++j) w[j] = 0.0;
+#pragma unroll
+    for (int jp = 0; jp < K; ++jp) {
+      if (32 * jp >= rl) break;
+      const int lim = min(32, rl - 32 * jp);
+      for (int l = 0; l < lim; ++l) {
+        const int p = 32 * jp + l;
+        const double vp = __shfl_sync(FULL, v[jp], l);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          const int u = 32 * j + lane;
+          if (u < rr) w[j] = __fma_rn(vp, G[p * ld + u], w[j]);
+        }
+      }
     }
-    for (int u = 0; u < rr; ++u) v[u] = w[u];
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = w[j];
     rl = rr;
   }
-  return v[0];
+  return __shfl_sync(FULL, v[0], 0);
 }
 
 __device__ double block_sum(double v, double *red) {
@@ -115,34 +157,29 @@ __device__ double block_sum(double v, double *red) {
   __syncthreads();
   double s = 0.0;
   if (threadIdx.x == 0)
-    for (int i = 0; i < kThreads / 32; ++i) s += red[i];
+    for (int i = 0; i < kWarps; ++i) s += red[i];
   __syncthreads();
   return s;
 }
 
-// one slot per chunk of kChunk samples: the result does not depend on the
-// grid, so it is the same on any GPU
+// one slot per chunk of kChunk samples (a warp per sample, warp w of the
+// CTA taking samples w, w + 8, ... of the chunk): the result does not depend
+// on the grid, so it is the same on any GPU
+template <int K>
 __global__ void __launch_bounds__(kThreads) k_chunk_sums(ErrArgs a, int64_t nchunks, double *sums) {
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[kWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const int64_t k0 = c * kChunk, k1 = min(a.nsamples, k0 + kChunk);
     double num = 0.0, den = 0.0;
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += kThreads) {
-      int32_t idx[kMaxD];
-      if (a.exhaustive) {
-        int64_t l = k;
-        for (int m = 0; m < a.d; ++m) {
-          idx[m] = (int32_t)(l % a.n[m]);
-          l /= a.n[m];
-        }
-      } else {
-        for (int m = 0; m < a.d; ++m)
-          idx[m] = (int32_t)__umul64hi(mix_at(a.seed, (uint64_t)(k * a.d + m)), (uint64_t)a.n[m]);
+    for (int64_t k = k0 + warp; k < k1; k += kWarps) {
+      const double xt = tt_value_warp<K>(a, k);
+      if (lane == 0) {
+        const double x = entry(a, k);
+        const double e = __dsub_rn(x, xt);
+        num = __fma_rn(e, e, num);
+        den = __fma_rn(x, x, den);
       }
-      const double x = entry(a, idx);
-      const double e = __dsub_rn(x, tt_value(a, idx));
-      num = __fma_rn(e, e, num);
-      den = __fma_rn(x, x, den);
     }
     const double sn = block_sum(num, red);
     const double sd = block_sum(den, red);
@@ -154,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) k_chunk_sums(ErrArgs a, int64_t nchu
 }
 
 __global__ void __launch_bounds__(kThreads) k_finish(const double *sums, int64_t nchunks, double *out) {
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[kWarps];
   double num = 0.0, den = 0.0;
   for (int64_t c = threadIdx.x; c < nchunks; c += kThreads) {
     num += sums[2 * c];
@@ -173,18 +210,31 @@ ttc_status bad(ttc_status s, const char *msg) {
 std::mutex g_mu;
 double *g_sums[kMaxDevices] = {};
 
-// Device address of g_chunk_sums on the current device, looked up once per
-// device (the first call on each device does it).
-ttc_status scratch_on(int dev, double **out) {
+// Device address of g_chunk_sums on device dev (the current device).  The
+// first call on a device looks it up and keeps it, so that a later call made
+// while the stream is being captured needs no lookup.  Calls outside a
+// capture look it up again: after cudaDeviceReset the module is loaded anew
+// and the array may sit elsewhere.
+ttc_status scratch_on(int dev, bool capturing, double **out) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_sums[dev]) {
+  if (!g_sums[dev] || !capturing) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_chunk_sums);
-    if (e != cudaSuccess || !p) return bad(TTC_ERR_CUDA, "cudaGetSymbolAddress of the scratch failed");
+    if (e != cudaSuccess || !p) {
+      if (capturing) return bad(TTC_ERR_CUDA, "scratch address unknown: make a first call before capture");
+      return bad(TTC_ERR_CUDA, "cudaGetSymbolAddress of the scratch failed");
+    }
     g_sums[dev] = static_cast<double *>(p);
   }
   *out = g_sums[dev];
   return TTC_OK;
+}
+
+template <int K>
+cudaError_t launch_sums(const ErrArgs &a, int64_t nchunks, int64_t grid, double *sums,
+                        cudaStream_t cs) {
+  k_chunk_sums<K><<<(unsigned)grid, kThreads, 0, cs>>>(a, nchunks, sums);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -213,9 +263,11 @@ extern "C" ttc_status ttcross_sampled_error_noalloc(int d, const int64_t *n, con
   }
   if (s[0] != 1 || s[d] != 1) return bad(TTC_ERR_INVALID_ARG, "core sizes must start and end with 1");
   for (int m = 0; m <= d; ++m) {
-    if (s[m] < 1 || s[m] > kMaxRank) return bad(TTC_ERR_INVALID_ARG, "core size outside [1,128]");
+    if (s[m] < 1 || s[m] > kMaxRank) return bad(TTC_ERR_INVALID_ARG, "core size outside [1,256]");
     a.s[m] = (int32_t)s[m];
   }
+  int smax = 1;
+  for (int m = 0; m <= d; ++m) smax = std::max(smax, a.s[m]);
   if (gen->kind == TTC_GEN_MAXWELLIAN) {
     if (gen->dx < 1 || gen->dv < 1 || gen->dx + gen->dv != d)
       return bad(TTC_ERR_INVALID_ARG, "Maxwellian needs dx, dv >= 1 and dx + dv = d");
@@ -246,14 +298,26 @@ extern "C" ttc_status ttcross_sampled_error_noalloc(int d, const int64_t *n, con
     return bad(TTC_ERR_CUDA, "no usable current device");
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return bad(TTC_ERR_CUDA, "device query failed");
-  double *sums = nullptr;
-  ttc_status st = scratch_on(dev, &sums);
-  if (st != TTC_OK) return st;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(cs, &cap) != cudaSuccess) return bad(TTC_ERR_CUDA, "stream query failed");
+  double *sums = nullptr;
+  ttc_status st = scratch_on(dev, cap != cudaStreamCaptureStatusNone, &sums);
+  if (st != TTC_OK) return st;
   const int64_t grid = std::min<int64_t>(nchunks, (int64_t)nsm * 4);
-  k_chunk_sums<<<(unsigned)grid, kThreads, 0, cs>>>(a, nchunks, sums);
-  k_finish<<<1, kThreads, 0, cs>>>(sums, nchunks, err);
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (smax <= 32)
+    e = launch_sums<1>(a, nchunks, grid, sums, cs);
+  else if (smax <= 64)
+    e = launch_sums<2>(a, nchunks, grid, sums, cs);
+  else if (smax <= 128)
+    e = launch_sums<4>(a, nchunks, grid, sums, cs);
+  else
+    e = launch_sums<8>(a, nchunks, grid, sums, cs);
+  if (e == cudaSuccess) {
+    k_finish<<<1, kThreads, 0, cs>>>(sums, nchunks, err);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return bad(TTC_ERR_CUDA, cudaGetErrorString(e));
   return TTC_OK;
 }

@@ -94,7 +94,7 @@ def load_library(path: str = LIB_PATH):
                                      C.POINTER(Options), C.POINTER(P)]
         L.ttcross_run.argtypes = [P, C.c_double, C.c_int, C.POINTER(C.c_int32), P]
         L.ttcross_run_batch.argtypes = [C.POINTER(P), C.c_int, C.POINTER(C.c_double),
-                                        C.POINTER(C.c_int32), P]
+                                        C.POINTER(C.c_int32), C.POINTER(P), P]
         L.ttcross_sync.argtypes = [P]
         L.ttcross_get_ranks.argtypes = [P, C.POINTER(C.c_int64)]
         L.ttcross_get_cores.argtypes = [P, C.c_int, P, C.c_int, P]
@@ -295,11 +295,37 @@ def make_generator(gen):
 def sampled_error_noalloc(n, gen, cores, nsamples: int, seed: int, out, stream=None):
     """Enqueue ttcross_sampled_error_noalloc: ``cores`` are CUDA float64 torch
     tensors [s_{m-1}, n_m, s_m]; the error is written to the CUDA float64
-    tensor ``out`` (one element).  Allocates nothing."""
+    tensor ``out`` (one element).  Allocates nothing.
+
+    The C side sees only the core pointers and the sizes s, so every core's
+    shape, dtype, device and layout is checked here: a permuted view or a
+    float32 core would make the kernel read past the end of the core."""
     L = load_library()
     n = np.ascontiguousarray(n, dtype=np.int64)
     d = int(n.size)
-    s = np.ascontiguousarray([1] + [int(c.shape[2]) for c in cores[:-1]] + [1], dtype=np.int64)
+
+    def reject(msg):
+        raise TTCError(ERR_INVALID_ARG, msg)
+
+    if len(cores) != d:
+        reject(f"{len(cores)} cores for a {d}-way tensor")
+    s = [1]
+    for m, c in enumerate(cores):
+        if getattr(c, "dtype", None) is None or str(c.dtype) != "torch.float64":
+            reject(f"core {m + 1} is not a float64 tensor")
+        if not getattr(c, "is_cuda", False):
+            reject(f"core {m + 1} is not in device memory")
+        if c.dim() != 3 or not c.is_contiguous():
+            reject(f"core {m + 1} must be a contiguous [s, n, s] tensor")
+        if int(c.shape[0]) != s[-1] or int(c.shape[1]) != int(n[m]):
+            reject(f"core {m + 1} has shape {tuple(c.shape)}, expected ({s[-1]}, {int(n[m])}, *)")
+        s.append(int(c.shape[2]))
+    if s[-1] != 1:
+        reject("the last core must end with size 1")
+    if (getattr(out, "dtype", None) is None or str(out.dtype) != "torch.float64"
+            or not getattr(out, "is_cuda", False) or out.numel() < 1):
+        reject("out must be a float64 device tensor with at least one element")
+    s = np.ascontiguousarray(s, dtype=np.int64)
     ptrs = (C.c_void_p * d)(*[c.data_ptr() for c in cores])
     g = make_generator(gen)
     _check(L.ttcross_sampled_error_noalloc(d, n.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(g),
@@ -319,8 +345,9 @@ def probe_fma_peak(fp64: bool = True, blocks_per_sm: int = 4, iters: int = 1 << 
     return rate.value, ms.value
 
 
-def run_batch(crosses, eps, max_rank=None, stream=None):
-    """Run several instances in one persistent launch (asynchronous)."""
+def run_batch(crosses, eps, max_rank=None, grids=None, stream=None):
+    """Run several instances in one persistent launch (asynchronous).
+    ``grids``: None, or one subtensor grid (or None) per instance."""
     L = load_library()
     cnt = len(crosses)
     hs = (C.c_void_p * cnt)(*[c.handle.value for c in crosses])
@@ -328,6 +355,20 @@ def run_batch(crosses, eps, max_rank=None, stream=None):
     mr = None
     if max_rank is not None:
         mr = np.ascontiguousarray(np.broadcast_to(np.asarray(max_rank, np.int32), (cnt,)))
+    gp = None
+    keep = []
+    if grids is not None:
+        if len(grids) != cnt:
+            raise ValueError("grids needs one entry per instance")
+        gp = (C.c_void_p * cnt)()
+        for i, (c, g) in enumerate(zip(crosses, grids)):
+            if g is None:
+                continue
+            a = _i32(g)
+            if a.size != c.d:
+                raise ValueError(f"grid {i} needs {c.d} entries")
+            keep.append(a)
+            gp[i] = a.ctypes.data
     _check(L.ttcross_run_batch(hs, cnt, e.ctypes.data_as(C.POINTER(C.c_double)),
                                mr.ctypes.data_as(C.POINTER(C.c_int32)) if mr is not None else None,
-                               _stream_handle(stream)))
+                               gp, _stream_handle(stream)))

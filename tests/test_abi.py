@@ -65,9 +65,35 @@ def test_stored_form_option_checked_on_host():
     o.residual = 5
     assert L.ttcross_create(3, n, ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)) == \
         ttcross.ERR_INVALID_ARG
-    o.residual = ttcross.RESIDUAL_STORED
-    o.precision = ttcross.PREC_SPLIT
-    assert L.ttcross_create(3, n, ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)) == \
-        ttcross.ERR_INVALID_ARG
-    assert b"FP64 only" in L.ttcross_last_error_string()
+    assert b"residual form" in L.ttcross_last_error_string()
 
+
+
+def test_run_batch_checks_arguments_on_host():
+    L = ttcross.load_library()
+    eps = (ctypes.c_double * 1)(1e-6)
+    assert L.ttcross_run_batch(None, 1, eps, None, None, None) == ttcross.ERR_INVALID_ARG
+    hs = (ctypes.c_void_p * 1)(None)
+    assert L.ttcross_run_batch(hs, 1, eps, None, None, None) == ttcross.ERR_INVALID_ARG
+    assert b"null handle" in L.ttcross_last_error_string()
+
+
+def test_noalloc_wrapper_rejects_bad_cores_before_the_call():
+    """The C side sees only core pointers and sizes: the wrapper checks every
+    core's rank, shape, dtype, layout and device before calling it."""
+    import torch
+    gen = {"kind": "hilbert"}
+    n = [4, 5, 6]
+    good = [torch.zeros(1, 4, 2, dtype=torch.float64), torch.zeros(2, 5, 3, dtype=torch.float64),
+            torch.zeros(3, 6, 1, dtype=torch.float64)]
+    out = torch.zeros(1, dtype=torch.float64)
+    cases = [good[:2],                                                      # too few cores
+             [good[0], torch.zeros(3, 5, 3, dtype=torch.float64), good[2]],  # s mismatch
+             [good[0], torch.zeros(2, 4, 3, dtype=torch.float64), good[2]],  # n mismatch
+             [good[0], good[1].float(), good[2]],                           # float32
+             [good[0], good[1].transpose(0, 2), good[2]],                   # permuted view
+             good]                                                          # host tensors
+    for cores in cases:
+        with pytest.raises(ttcross.TTCError) as e:
+            ttcross.sampled_error_noalloc(n, gen, cores, 100, 1, out)
+        assert e.value.status == ttcross.ERR_INVALID_ARG

@@ -153,27 +153,40 @@ def _coords(o, b, Irow, Jrow):
     return p * int(n[b]) + int(Irow[-1]), q * int(n[b + 1]) + int(Jrow[0])
 
 
-def replay_with_resync(g, w, eps, cap, nsamples, rel=1e-13):
+def replay_with_resync(g, w, eps, cap, nsamples, rel=1e-13, stored=False, max_refine=6):
     """Step the oracle sweep by sweep beside the GPU's pivots.  Where the two
     differ, the GPU's pivot must be a near-tie: its FP64 residual within
     rel * max|X| of the oracle's best (ulp-level differences of the entries
     reach the residual through A - T R, so they scale with |X|, not |E|); the
-    oracle then continues from it.  Returns (oracle, number of near-ties)."""
-    o = oracle.Oracle(w["n"], w["gen"], cap, nthreads=NT)
+    oracle then continues from it.  ``stored``: the oracle's stored-residual
+    form, whose screen reads the carried E (the near-tie check too).  When no
+    bond adds, the oracle's sampled error decides as in its own run: done at
+    eps, else tau / 10 while ranks and refinements remain.
+    Returns (oracle, number of near-ties)."""
+    o = oracle.Oracle(w["n"], w["gen"], cap, nthreads=NT, stored=stored)
     rms, start = o.sample_scan(nsamples)
     gI = [g.pivots(k) for k in range(1, o.d)]
     np.testing.assert_array_equal(np.concatenate([gI[0][0][0], gI[0][1][0]]), start)
     assert o.init_at(start) == 0
     xmax = abs(o.entry(start))
     ties = 0
-    theta = eps * rms
+    tau = eps
+    refinements = 0
     while True:
         rc, sc = o.screen()
         assert rc == 0
         r = o.ranks()
-        add = [int(sc["best"][b] > theta and r[b] < cap) for b in range(o.d - 1)]
+        theta = tau * rms
+        add = [int(sc["best"][b] > theta and sc["best"][b] > 0 and r[b] < cap)
+               for b in range(o.d - 1)]
         if not any(add):
-            break
+            if eps == 0.0 or o.sampled_error(nsamples) <= eps:
+                break
+            if all(r[b] >= cap for b in range(o.d - 1)) or refinements >= max_refine:
+                break
+            tau /= 10.0
+            refinements += 1
+            continue
         rows, cols = sc["row"].copy(), sc["col"].copy()
         for b in range(o.d - 1):
             if not add[b]:
@@ -182,7 +195,7 @@ def replay_with_resync(g, w, eps, cap, nsamples, rel=1e-13):
             assert z < len(gI[b][0]), f"GPU stopped bond {b + 1} at rank {z}"
             a, c = _coords(o, b, gI[b][0][z], gI[b][1][z])
             if (a, c) != (rows[b], cols[b]):
-                e = abs(o.residual(b, a, c))
+                e = abs(o.stored_residual(b, a, c) if stored else o.residual(b, a, c))
                 assert e >= sc["best"][b] - rel * xmax, (b, e, sc["best"][b])
                 ties += 1
                 rows[b], cols[b] = a, c

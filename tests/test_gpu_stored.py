@@ -128,12 +128,6 @@ def test_stored_prescribed_ranks_and_rerun(tt):
     assert_same(g, o)
 
 
-def test_stored_rejects_mixed_precision(tt):
-    w = W.hilbert(3, 8)
-    with pytest.raises(tt.TTCError):
-        tt.TTCross(w["n"], w["gen"], max_rank=4, precision="split", residual="stored")
-
-
 def test_stored_config4_scale_error_and_cost(tt):
     """6D Hilbert n = 256 (the largest workload), stored form: error <= eps on
     the 10^6 samples, cross-checked at 2000 samples by the oracle's own TT
