@@ -82,6 +82,9 @@ struct ttc_handle {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool ran = false;
   bool events_ok = false;
+  bool synced = false;          // h_ctrl holds the finished last run
+  ttc_status sync_status = TTC_OK;
+  std::string sync_msg;
   std::vector<double> tt_cores;
   std::vector<int32_t> tt_ranks;
 };
@@ -613,6 +616,7 @@ ttc_status ttcross_run(ttc_handle *h, double eps, int max_rank, const int32_t *s
   if (h->events_ok) CU(cudaEventRecord(h->ev1, st));
   h->stream = st;
   h->ran = true;
+  h->synced = false;
   return TTC_OK;
 }
 
@@ -656,22 +660,51 @@ ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps
   CU(cudaMemcpyAsync(d_list, lst.data(), sizeof(InstDev *) * count, cudaMemcpyHostToDevice, st));
   CU(cudaStreamSynchronize(st));  // the host vector dies at return
   ttc_handle *h0 = hs[0];
-  if (h0->events_ok) CU(cudaEventRecord(h0->ev0, st));
+  for (int i = 0; i < count; ++i)
+    if (hs[i]->events_ok) CU(cudaEventRecord(hs[i]->ev0, st));
   ttc_status s = launch_run(hs, count, d_list, st);
-  if (h0->events_ok) cudaEventRecord(h0->ev1, st);
+  // every instance keeps its own copy of the launch's barrier words (abort
+  // flag, phase times) and its own events, so that it can be synchronised,
+  // queried or destroyed independently of the others
+  for (int i = 1; i < count && s == TTC_OK; ++i)
+    if (cudaMemcpyAsync(hs[i]->d_bar, h0->d_bar, sizeof(Barrier), cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+      s = fail(TTC_ERR_CUDA, "copy of the barrier words failed");
+  for (int i = 0; i < count; ++i)
+    if (hs[i]->events_ok) cudaEventRecord(hs[i]->ev1, st);
   cudaFreeAsync(d_list, st);
   if (s) return s;
   for (int i = 0; i < count; ++i) {
     hs[i]->stream = st;
     hs[i]->ran = true;
+    hs[i]->synced = false;
   }
   return TTC_OK;
 }
+
+static ttc_status sync_run(ttc_handle *h);
 
 ttc_status ttcross_sync(ttc_handle *h) {
   ttc_status s = check_handle(h);
   if (s) return s;
   if (!h->ran) return fail(TTC_ERR_INVALID_ARG, "no run to wait for");
+  // the first wait after a run reads its control block; later calls (every
+  // getter waits) return what it found without touching the device
+  if (h->synced) {
+    if (h->sync_status != TTC_OK && h->sync_status != TTC_NOT_CONVERGED)
+      return fail(h->sync_status, "%s", h->sync_msg.c_str());
+    return h->sync_status;
+  }
+  s = sync_run(h);
+  if (s != TTC_ERR_CUDA || h->h_ctrl.state == ST_DONE) {
+    h->synced = true;
+    h->sync_status = s;
+    h->sync_msg = g_err;
+  }
+  return s;
+}
+
+static ttc_status sync_run(ttc_handle *h) {
   CU(cudaStreamSynchronize(h->stream));
   CU(cudaMemcpy(&h->h_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
   Barrier bar;

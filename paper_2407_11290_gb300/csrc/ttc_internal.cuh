@@ -85,8 +85,9 @@ struct Ctrl {
   // pivot (ew, erow) is still to be applied by the next screen
   int32_t st_rows[TTC_MAXD], st_cols[TTC_MAXD];
   int32_t e_pend[TTC_MAXD];
-  int32_t steal;             // stored form: tiles handed out by the running screen
-                             // (cleared by the decide phase after it)
+  int32_t steal, steal2;     // stored form: items handed out by the running screen
+                             // from its fresh / carried queues (cleared by the
+                             // decide phase after it)
   int64_t entries_fresh;     // entries evaluated as A - T R (the rest carried)
   int64_t stored_bytes;      // bytes of E read and written by the screens
   int32_t dkind;             // work of the coming decide phases, fixed by the

@@ -668,18 +668,86 @@ __device__ __forceinline__ void screen_tile_fp64(const InstDev &in, int b, int K
 }
 
 // ---------------------------------------------------------------------------
+// Stored residual values.  The FP64 form keeps E, the rank-one step's column
+// ew and row erow as doubles and carries E by the FP64 FMA of the stored-form
+// contract.  The mixed forms keep them as float-float pairs (hi, lo) in the
+// same 8 bytes and carry E on the FP32 pipe (about 44 bits; a carried entry
+// then costs no FP64 instruction); their screen keys are |hi|.
+template <int MIX>
+struct SV;
+template <>
+struct SV<0> {
+  using T = double;
+  static __device__ __forceinline__ T load(const double *E, int64_t i) { return E[i]; }
+  static __device__ __forceinline__ void store(double *E, int64_t i, T v) { E[i] = v; }
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ T step(T w, T e, T a) { return __fma_rn(w, e, a); }
+  static __device__ __forceinline__ T from(double x) { return x; }
+  static __device__ __forceinline__ uint64_t key(T v) { return abs_key(v); }
+};
+struct SVff {
+  using T = float2;
+  static __device__ __forceinline__ T load(const double *E, int64_t i) {
+    return reinterpret_cast<const float2 *>(E)[i];
+  }
+  static __device__ __forceinline__ void store(double *E, int64_t i, T v) {
+    reinterpret_cast<float2 *>(E)[i] = v;
+  }
+  static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+  // a + w e: w.x e.x = p + pe exactly, the cross terms and pe join the low
+  // word, TwoSum of the high words, renormalised (12 FP32 operations)
+  static __device__ __forceinline__ T step(T w, T e, T a) {
+    const float p = __fmul_rn(w.x, e.x);
+    const float pe = __fmaf_rn(w.x, e.x, -p);
+    const float cr = __fmaf_rn(w.x, e.y, __fmaf_rn(w.y, e.x, pe));
+    const float s1 = __fadd_rn(a.x, p);
+    const float bb = __fsub_rn(s1, a.x);
+    const float er = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+    const float lo = __fadd_rn(a.y, __fadd_rn(er, cr));
+    const float s2 = __fadd_rn(s1, lo);
+    return make_float2(s2, __fsub_rn(lo, __fsub_rn(s2, s1)));
+  }
+  static __device__ __forceinline__ T from(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(__dsub_rn(x, (double)h)));
+  }
+  static __device__ __forceinline__ uint64_t key(T v) {
+    return (uint64_t)(__float_as_uint(v.x) & 0x7FFFFFFFu);
+  }
+};
+template <>
+struct SV<1> : SVff {};
+template <>
+struct SV<2> : SVff {};
+
+// value of a stored entry as a double (update phase)
+__device__ __forceinline__ double sv_get(const InstDev &in, const double *E, int64_t i) {
+  if (in.prec == P_FP64) return E[i];
+  const float2 v = reinterpret_cast<const float2 *>(E)[i];
+  return __dadd_rn((double)v.x, (double)v.y);
+}
+__device__ __forceinline__ void sv_put(const InstDev &in, double *E, int64_t i, double x) {
+  if (in.prec == P_FP64)
+    E[i] = x;
+  else
+    SVff::store(E, i, SVff::from(x));
+}
+
 // stored-residual screen of one tile (eq. aca_approx_E).  Entries inside the
 // stored extent (row < sr and column < sc) are read from E and, when the bond
 // appended a pivot in the last sweep (pend), carried through its rank-one
-// step E(a,c) = fma(ew[a], erow[c], E(a,c)) with ew[a] = -(E(a,c*) / E(a*,c*))
-// and erow = E(a*, :).  Entries outside it have just entered the superblock
-// and get A - chain(T(a,:), R(:,c)) with the current factors.  Both are written
-// back to E; the tile's best |E| is kept as in the FP64 screen.
+// step E(a,c) = E(a,c) + ew[a] erow[c] with ew[a] = -(E(a,c*) / E(a*,c*)) and
+// erow = E(a*, :).  Entries outside it have just entered the superblock and
+// get A - chain(T(a,:), R(:,c)) with the current factors (MIX 0: FP64 chain
+// of the contract; 1 / 2: FP32 / float-float chain).  Both are written back
+// to E; the tile's best |E| is kept as in the FP64 screen.
 template <bool HIL, int TE, int MIX>
 __device__ __noinline__ void screen_tile_stored_t(const InstDev &in, int b, int K, int64_t r0,
                                                   int nr, int64_t c0, int nc, int32_t sr,
                                                   int32_t sc, int pend, Cand *out,
                                                   ScreenSmem &sm) {
+  using V = SV<MIX>;
+  using VT = typename V::T;
   constexpr int U = TE / 16;
   const BondDev &B = in.bond[b];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -688,7 +756,7 @@ __device__ __noinline__ void screen_tile_stored_t(const InstDev &in, int b, int 
   __syncthreads();
   stage_meta(in, b, r0, nr, c0, nc, sm);
   const bool carried = r0 + nr <= sr && c0 + nc <= sc;
-  double ev[U][U];
+  VT ev[U][U];
   if (carried) {
     // streaming tile: all loads first, then the rank-one step and the stores
 #pragma unroll
@@ -697,15 +765,17 @@ __device__ __noinline__ void screen_tile_stored_t(const InstDev &in, int b, int 
 #pragma unroll
       for (int v = 0; v < U; ++v) {
         const int cc = tx + 16 * v;
-        ev[u][v] = (rr < nr && cc < nc) ? B.E[(r0 + rr) * ld + c0 + cc] : 0.0;
+        ev[u][v] = (rr < nr && cc < nc) ? V::load(B.E, (r0 + rr) * ld + c0 + cc) : V::zero();
       }
     }
     if (pend) {
-      double wa[U], er[U];
+      VT wa[U], er[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) wa[u] = ty + 16 * u < nr ? B.ew[r0 + ty + 16 * u] : 0.0;
+      for (int u = 0; u < U; ++u)
+        wa[u] = ty + 16 * u < nr ? V::load(B.ew, r0 + ty + 16 * u) : V::zero();
 #pragma unroll
-      for (int v = 0; v < U; ++v) er[v] = tx + 16 * v < nc ? B.erow[c0 + tx + 16 * v] : 0.0;
+      for (int v = 0; v < U; ++v)
+        er[v] = tx + 16 * v < nc ? V::load(B.erow, c0 + tx + 16 * v) : V::zero();
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int rr = ty + 16 * u;
@@ -713,8 +783,8 @@ __device__ __noinline__ void screen_tile_stored_t(const InstDev &in, int b, int 
         for (int v = 0; v < U; ++v) {
           const int cc = tx + 16 * v;
           if (rr < nr && cc < nc) {
-            ev[u][v] = __fma_rn(wa[u], er[v], ev[u][v]);
-            B.E[(r0 + rr) * ld + c0 + cc] = ev[u][v];
+            ev[u][v] = V::step(wa[u], er[v], ev[u][v]);
+            V::store(B.E, (r0 + rr) * ld + c0 + cc, ev[u][v]);
           }
         }
       }
@@ -731,25 +801,25 @@ __device__ __noinline__ void screen_tile_stored_t(const InstDev &in, int b, int 
       const int rr = ty + 16 * u;
       const int64_t a = r0 + rr;
       const bool arow = rr < nr && a < sr;
-      const double wa = (pend && arow) ? B.ew[a] : 0.0;
+      const VT wa = (pend && arow) ? V::load(B.ew, a) : V::zero();
 #pragma unroll
       for (int v = 0; v < U; ++v) {
         const int cc = tx + 16 * v;
         const int64_t c = c0 + cc;
         if (rr >= nr || cc >= nc) {
-          ev[u][v] = 0.0;
+          ev[u][v] = V::zero();
           continue;
         }
-        double e;
+        VT e;
         if (arow && c < sc) {
-          e = B.E[a * ld + c];
-          if (pend) e = __fma_rn(wa, B.erow[c], e);
+          e = V::load(B.E, a * ld + c);
+          if (pend) e = V::step(wa, V::load(B.erow, c), e);
         } else {
           const double A =
               HIL ? in.hilb[sm.srow[rr] + sm.scol[cc]] : tile_entry(in, sm, wl, wr, rr, cc);
-          e = __dsub_rn(A, acc[u][v]);
+          e = V::from(__dsub_rn(A, acc[u][v]));
         }
-        B.E[a * ld + c] = e;
+        V::store(B.E, a * ld + c, e);
         ev[u][v] = e;
       }
     }
@@ -763,7 +833,7 @@ __device__ __noinline__ void screen_tile_stored_t(const InstDev &in, int b, int 
     for (int v = 0; v < U; ++v) {
       const int cc = tx + 16 * v;
       if (cc >= nc) continue;
-      const uint64_t k = abs_key(ev[u][v]);
+      const uint64_t k = V::key(ev[u][v]);
       if (best.row < 0 || k >= best.key) {
         const int64_t l = sm.lrow[rr] + sm.lcol[cc];
         if (best.row < 0 || k > best.key || l < best.lin) {
@@ -1090,67 +1160,103 @@ __device__ void screen_bookkeeping(const InstDev &in, const int32_t *r, const Ti
   cw.screened = 1;
 }
 
-// A carried 32-wide tile of bond b by one warp (lane = column): every load in
-// one round, the pending rank-one step E(a,c) = fma(ew[a], erow[c], E(a,c))
-// and its stores, then the tile's best |E| (ties: lowest linear index).  The
-// tile lies in one block (p, q) of the superblock, where the linear index is
+// A carried tile (TE = 32 or 64 wide) of bond b by one warp: lane l holds
+// columns l (and l + 32); rows go in rounds of 32 (TE = 32) or 8 (TE = 64),
+// every load of a round issued before its first use.  Then the pending
+// rank-one step E(a,c) = fma(ew[a], erow[c], E(a,c)) and its stores, and the
+// tile's best |E| (ties: lowest linear index).  The tile lies in one block
+// (p, q) of the superblock, where the linear index is
 // L.lin[p] + R.lin[q] + i stride_b + j stride_{b+1}: the ties need no loads.
 // Eight tiles per CTA are in flight instead of one.
+template <int TE, int MIX>
 __device__ __noinline__ void screen_carried_warp(const InstDev &in, int b, int64_t r0, int nr,
                                                  int64_t c0, int nc, int pend, Cand *out,
                                                  int spt) {
+  using V = SV<MIX>;
+  using VT = typename V::T;
   constexpr unsigned FULL = 0xffffffffu;
+  constexpr int NC = TE / 32;                // columns per lane
+  constexpr int RR = TE == 32 ? 32 : 8;      // rows per round
   const BondDev &B = in.bond[b];
   const int lane = threadIdx.x & 31;
   const int64_t ld = B.ldR;
-  const bool col_ok = lane < nc;
   const int64_t nb0 = in.n[b], nb1 = in.n[b + 1];
   const int64_t p = r0 / nb0, i0 = r0 - p * nb0;
   const int64_t q = c0 / nb1, j0 = c0 - q * nb1;
-  double ev[32];
-#pragma unroll
-  for (int rr = 0; rr < 32; ++rr)
-    ev[rr] = (col_ok && rr < nr) ? B.E[(r0 + rr) * ld + c0 + lane] : 0.0;
+  const int64_t sb = in.stride[b], sb1 = in.stride[b + 1];
   const int64_t lp = lane == 0 ? left_set(in, b).lin[p] : 0;
   const int64_t rq = lane == 1 ? right_set(in, b).lin[q] : 0;
-  if (pend) {
-    const double wa = lane < nr ? B.ew[r0 + lane] : 0.0;
-    const double er = col_ok ? B.erow[c0 + lane] : 0.0;
+  VT wa[NC], er[NC];
+  bool cok[NC];
 #pragma unroll
-    for (int rr = 0; rr < 32; ++rr) {
-      const double w = __shfl_sync(FULL, wa, rr);
-      if (rr < nr && col_ok) {
-        ev[rr] = __fma_rn(w, er, ev[rr]);
-        B.E[(r0 + rr) * ld + c0 + lane] = ev[rr];
-      }
-    }
+  for (int k = 0; k < NC; ++k) {
+    cok[k] = lane + 32 * k < nc;
+    wa[k] = (pend && lane + 32 * k < nr) ? V::load(B.ew, r0 + lane + 32 * k) : V::zero();
+    er[k] = (pend && cok[k]) ? V::load(B.erow, c0 + lane + 32 * k) : V::zero();
   }
-  // the lane's best: rows in order, only a larger key replaces (in one
-  // column the earlier row has the lower linear index)
   uint64_t bk = 0;
-  int brr = -1;
+  int64_t bl = LLONG_MAX;
+  int brr = -1, bcc = 0;
 #pragma unroll
-  for (int rr = 0; rr < 32; ++rr) {
-    if (rr < nr && col_ok) {
-      const uint64_t k = abs_key(ev[rr]);
-      if (brr < 0 || k > bk) {
-        bk = k;
-        brr = rr;
+  for (int r1 = 0; r1 < TE; r1 += RR) {
+    VT ev[RR][NC];
+#pragma unroll
+    for (int rr = 0; rr < RR; ++rr)
+#pragma unroll
+      for (int k = 0; k < NC; ++k)
+        ev[rr][k] = (cok[k] && r1 + rr < nr) ? V::load(B.E, (r0 + r1 + rr) * ld + c0 + lane + 32 * k)
+                                             : V::zero();
+    if (pend) {
+#pragma unroll
+      for (int rr = 0; rr < RR; ++rr) {
+        const int row = r1 + rr;
+        VT w;
+        if constexpr (MIX == 0) {
+          w = __shfl_sync(FULL, wa[row >> 5], row & 31);
+        } else {
+          w.x = __shfl_sync(FULL, wa[row >> 5].x, row & 31);
+          w.y = __shfl_sync(FULL, wa[row >> 5].y, row & 31);
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+          if (row < nr && cok[k]) {
+            ev[rr][k] = V::step(w, er[k], ev[rr][k]);
+            V::store(B.E, (r0 + row) * ld + c0 + lane + 32 * k, ev[rr][k]);
+          }
       }
     }
+    // the lane's best: rows in order, only a larger key replaces within a
+    // column (the earlier row has the lower linear index); across its
+    // columns the linear index decides
+#pragma unroll
+    for (int rr = 0; rr < RR; ++rr)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        const int row = r1 + rr;
+        if (row < nr && cok[k]) {
+          const uint64_t key = V::key(ev[rr][k]);
+          if (brr < 0 || key >= bk) {
+            const int64_t l = (i0 + row) * sb + (j0 + lane + 32 * k) * sb1;
+            if (brr < 0 || key > bk || l < bl) {
+              bk = key;
+              bl = l;
+              brr = row;
+              bcc = lane + 32 * k;
+            }
+          }
+        }
+      }
   }
-  int64_t bl = brr >= 0 ? (i0 + brr) * in.stride[b] + (j0 + lane) * in.stride[b + 1] : LLONG_MAX;
-  int bcol = lane;
   for (int off = 16; off > 0; off >>= 1) {
     const uint64_t ok = __shfl_xor_sync(FULL, bk, off);
     const int64_t ol = __shfl_xor_sync(FULL, bl, off);
     const int orr = __shfl_xor_sync(FULL, brr, off);
-    const int oc = __shfl_xor_sync(FULL, bcol, off);
+    const int oc = __shfl_xor_sync(FULL, bcc, off);
     if (orr >= 0 && (brr < 0 || ok > bk || (ok == bk && ol < bl))) {
       bk = ok;
       bl = ol;
       brr = orr;
-      bcol = oc;
+      bcc = oc;
     }
   }
   const int64_t LP = __shfl_sync(FULL, lp, 0), RQ = __shfl_sync(FULL, rq, 1);
@@ -1158,20 +1264,52 @@ __device__ __noinline__ void screen_carried_warp(const InstDev &in, int b, int64
     out->key = bk;
     out->lin = LP + RQ + bl;
     out->row = (int32_t)(r0 + brr);
-    out->col = (int32_t)(c0 + bcol);
+    out->col = (int32_t)(c0 + bcc);
     for (int k = 1; k < spt; ++k) out[k] = Cand{0ull, LLONG_MAX, -2, -2};
   }
 }
 
+__device__ __forceinline__ void carried_warp(const InstDev &in, int te, int b, int64_t r0, int nr,
+                                             int64_t c0, int nc, int pend, Cand *out, int spt) {
+  if (in.prec == P_FP64) {
+    if (te == 32)
+      screen_carried_warp<32, 0>(in, b, r0, nr, c0, nc, pend, out, spt);
+    else
+      screen_carried_warp<64, 0>(in, b, r0, nr, c0, nc, pend, out, spt);
+  } else {
+    if (te == 32)
+      screen_carried_warp<32, 2>(in, b, r0, nr, c0, nc, pend, out, spt);
+    else
+      screen_carried_warp<64, 2>(in, b, r0, nr, c0, nc, pend, out, spt);
+  }
+}
+
+// The stored screen of one instance.  Work items come from two queues:
+//   A: tiles new to a superblock (fresh: A - T R, r_k FMAs per entry, FP64
+//      pipe or FP32 pipe in the mixed forms), one tile (or quarter) per
+//      block item;
+//   B: carried tiles (one load, one FMA when a rank-one step is pending, one
+//      store per entry: memory-bound).  On bonds cut into subtensor pieces a
+//      carried tile lies in one block (p, q) and is screened by one warp, and
+//      an item is eight such tiles, one per warp; elsewhere an item is one
+//      tile screened by the whole CTA.
+// The CTAs of the first half of the SM-spread order (one per SM) start on A,
+// the others on B, so that every SM keeps its FP64 / FP32 pipe and its
+// memory path busy at once; a CTA whose queue runs dry moves to the other.
+// Place s takes the first item of its queue implicitly, later items come
+// from the queue's counter, fetched when an item starts so that the atomic's
+// round trip overlaps the tile.  The decide phase clears both counters.
+constexpr int CW = NT / 32;  // carried warp tiles per item
+
 __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, PhaseSmem &sm) {
   const Ctrl &cr = *in.ctrl;
-  int32_t *ctr = &in.ctrl->steal;
+  int32_t *ctr[2] = {&in.ctrl->steal, &in.ctrl->steal2};
   // per-bond geometry, stored extent and item counts, staged once
   __shared__ TileGeo s_geo[TTC_MAXB];
   __shared__ int32_t s_sr[TTC_MAXB], s_sc[TTC_MAXB], s_pend[TTC_MAXB];
   __shared__ int32_t s_tr0[TTC_MAXB], s_tc0[TTC_MAXB];
   __shared__ int32_t s_warp[TTC_MAXB];  // carried tiles go to single warps
-  __shared__ int32_t s_item;
+  __shared__ int32_t s_item, s_q;
   __syncthreads();
   if (threadIdx.x < in.nb) {
     const int b = threadIdx.x;
@@ -1186,121 +1324,134 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
     s_pend[b] = ld_cg(cr.e_pend[b]);
     s_tr0[b] = tr0;
     s_tc0[b] = tc0;
-    s_warp[b] = g.te == 32 && g.pr > 0 && g.pc > 0;
+    s_warp[b] = g.pr > 0 && g.pc > 0;
   }
   __syncthreads();
   // with fewer fresh tiles than CTAs, fresh tiles go out as quarters
-  // (32 x 32) so that their FP64 work spreads over four times as many CTAs;
+  // (32 x 32) so that their work spreads over four times as many CTAs;
   // candidate slots are then STORED_SLOTS per tile, else one
-  int32_t nf = 0, ncar = 0, nwc = 0;
+  int32_t nf = 0, nB = 0;
   for (int b = 0; b < in.nb; ++b) {
     const int32_t nt = s_geo[b].nrt * s_geo[b].nct, nc = s_tr0[b] * s_tc0[b];
     nf += nt - nc;
-    if (s_warp[b])
-      nwc += nc;
-    else
-      ncar += nc;
+    nB += s_warp[b] ? (nc + CW - 1) / CW : nc;
   }
   const bool quarters = s_geo[0].te == 64 && nf < (int32_t)gridDim.x;
   const int32_t spt = quarters ? STORED_SLOTS : 1;  // slots per tile
-  const int32_t nfresh = spt * nf, ntot = nfresh + ncar;
+  const int32_t nA = spt * nf;
+  const int32_t G = gridDim.x;
+  const int32_t HA = nA == 0 ? 0 : nB == 0 ? G : (G + 1) / 2;  // CTAs starting on A
+  const int32_t N[2] = {nA, nB}, H[2] = {HA, G - HA};
   if (blockIdx.x == 0 && threadIdx.x == 0) screen_bookkeeping(in, r, s_geo, s_sr, s_sc, s_pend, spt);
-  // item s_place first, then items G, G + 1, ... from the counter (every CTA
-  // fetching at once from one address would queue at its L2 slice)
-  for (int32_t pass = 0;; ++pass) {
-    if (threadIdx.x == 0) s_item = pass == 0 ? s_place : (int32_t)gridDim.x + atomicAdd(ctr, 1);
+  // thread 0 keeps the queue, whether it has switched, and the next item
+  int q0 = s_place < HA ? 0 : 1;
+  bool switched = false;
+  if (threadIdx.x == 0) {
+    int32_t j = q0 == 0 ? s_place : s_place - HA;
+    if (j >= N[q0]) {
+      switched = true;
+      q0 ^= 1;
+      j = H[q0] + atomicAdd(ctr[q0], 1);
+    }
+    s_q = q0;
+    s_item = j < N[q0] ? j : -1;
+  }
+  int32_t nxt = 0;
+  for (;;) {
     __syncthreads();
+    const int qq = s_q;
     int32_t j = s_item;
     __syncthreads();
-    if (j >= ntot) break;
-    // item j -> (bond, tile): fresh items (FP64-bound) and carried tiles
-    // (memory-bound) alternate, so the two CTAs of an SM tend to load
-    // different pipes; the longer list runs on alone at the end
-    const int32_t m = min(nfresh, ntot - nfresh);
-    bool fresh;
-    if (j < 2 * m) {
-      fresh = (j & 1) == 0;
-      j >>= 1;
-    } else {
-      fresh = nfresh > m;
-      j -= m;
-    }
-    int32_t q = 0;
-    if (fresh) {
-      q = j % spt;
+    if (j < 0) break;
+    if (threadIdx.x == 0) nxt = H[qq] + atomicAdd(ctr[qq], 1);
+    if (qq == 0) {
+      // a fresh tile (or quarter q of it)
+      const int32_t qt = j % spt;
       j /= spt;
-    }
-    for (int b = 0; b < in.nb; ++b) {
-      const TileGeo &g = s_geo[b];
-      const int32_t tr0 = s_tr0[b], tc0 = s_tc0[b];
-      const int32_t cnt = fresh ? g.nrt * g.nct - tr0 * tc0 : (s_warp[b] ? 0 : tr0 * tc0);
-      if (j >= cnt) {
-        j -= cnt;
-        continue;
-      }
-      int32_t tr, tc;
-      if (!fresh) {
-        tr = j / tc0;
-        tc = j - tr * tc0;
-      } else if (j < tr0 * (g.nct - tc0)) {
-        // new columns of the stored rows
-        tr = j / (g.nct - tc0);
-        tc = tc0 + (j - tr * (g.nct - tc0));
-      } else {
-        // new rows, every column
-        const int32_t u = j - tr0 * (g.nct - tc0);
-        tr = tr0 + u / g.nct;
-        tc = u - (tr - tr0) * g.nct;
-      }
-      int64_t r0, c0;
-      int nr, nc;
-      tile_rows(in, g, b, tr, r0, nr);
-      tile_cols(in, g, b, tc, c0, nc);
-      Cand *slot = in.cand + in.bond[b].cand_base + (int64_t)(tr * g.nct + tc) * spt;
-      if (fresh && quarters) {
-        // quarter q of the tile: rows / columns [32 qr, 32 qr + 32)
-        const int h = g.te / 2, qr = q >> 1, qc = q & 1;
-        const int nrq = min(h, nr - h * qr), ncq = min(h, nc - h * qc);
-        if (nrq > 0 && ncq > 0)
-          screen_tile_stored(in, b, r[b], r0 + h * qr, nrq, c0 + h * qc, ncq, h, s_sr[b],
-                             s_sc[b], s_pend[b], slot + q, sm.s);
-        else if (threadIdx.x == 0)
-          slot[q] = Cand{0ull, LLONG_MAX, -2, -2};  // an empty quarter
-      } else {
-        screen_tile_stored(in, b, r[b], r0, nr, c0, nc, g.te, s_sr[b], s_sc[b], s_pend[b],
-                           slot, sm.s);
-        if (threadIdx.x == 0)
-          for (int k = 1; k < spt; ++k) slot[k] = Cand{0ull, LLONG_MAX, -2, -2};
-      }
-      break;
-    }
-  }
-  // carried tiles of the warp bonds, a tile per warp, dealt statically (they
-  // cost alike) after the block items: warp slot x = s + G (w + W t) of place
-  // s, warp w takes tile x - ntot, so the first tiles land on distinct SMs
-  // that hold no block item
-  if (nwc > 0) {
-    const int32_t G = gridDim.x, nw = NT / 32;
-    for (int32_t x = s_place + G * (int32_t)(threadIdx.x >> 5); x < ntot + nwc; x += G * nw) {
-      if (x < ntot) continue;
-      int32_t k = x - ntot;
       for (int b = 0; b < in.nb; ++b) {
-        if (!s_warp[b]) continue;
         const TileGeo &g = s_geo[b];
-        const int32_t tc0 = s_tc0[b], cnt = s_tr0[b] * tc0;
-        if (k >= cnt) {
-          k -= cnt;
+        const int32_t tr0 = s_tr0[b], tc0 = s_tc0[b];
+        const int32_t cnt = g.nrt * g.nct - tr0 * tc0;
+        if (j >= cnt) {
+          j -= cnt;
           continue;
         }
-        const int32_t tr = k / tc0, tc = k - tr * tc0;
+        int32_t tr, tc;
+        if (j < tr0 * (g.nct - tc0)) {
+          // new columns of the stored rows
+          tr = j / (g.nct - tc0);
+          tc = tc0 + (j - tr * (g.nct - tc0));
+        } else {
+          // new rows, every column
+          const int32_t u = j - tr0 * (g.nct - tc0);
+          tr = tr0 + u / g.nct;
+          tc = u - (tr - tr0) * g.nct;
+        }
         int64_t r0, c0;
         int nr, nc;
         tile_rows(in, g, b, tr, r0, nr);
         tile_cols(in, g, b, tc, c0, nc);
         Cand *slot = in.cand + in.bond[b].cand_base + (int64_t)(tr * g.nct + tc) * spt;
-        screen_carried_warp(in, b, r0, nr, c0, nc, s_pend[b], slot, spt);
+        if (quarters) {
+          // quarter qt of the tile: rows / columns [32 qr, 32 qr + 32)
+          const int h = g.te / 2, qr = qt >> 1, qc = qt & 1;
+          const int nrq = min(h, nr - h * qr), ncq = min(h, nc - h * qc);
+          if (nrq > 0 && ncq > 0)
+            screen_tile_stored(in, b, r[b], r0 + h * qr, nrq, c0 + h * qc, ncq, h, s_sr[b],
+                               s_sc[b], s_pend[b], slot + qt, sm.s);
+          else if (threadIdx.x == 0)
+            slot[qt] = Cand{0ull, LLONG_MAX, -2, -2};  // an empty quarter
+        } else {
+          screen_tile_stored(in, b, r[b], r0, nr, c0, nc, g.te, s_sr[b], s_sc[b], s_pend[b],
+                             slot, sm.s);
+        }
         break;
       }
+    } else {
+      // carried tiles: eight warp tiles, or one block tile
+      for (int b = 0; b < in.nb; ++b) {
+        const TileGeo &g = s_geo[b];
+        const int32_t tc0 = s_tc0[b], nc_b = s_tr0[b] * tc0;
+        const int32_t cnt = s_warp[b] ? (nc_b + CW - 1) / CW : nc_b;
+        if (j >= cnt) {
+          j -= cnt;
+          continue;
+        }
+        const int32_t k = s_warp[b] ? j * CW + (int32_t)(threadIdx.x >> 5) : j;
+        if (k < nc_b) {
+          const int32_t tr = k / tc0, tc = k - tr * tc0;
+          int64_t r0, c0;
+          int nr, nc;
+          tile_rows(in, g, b, tr, r0, nr);
+          tile_cols(in, g, b, tc, c0, nc);
+          Cand *slot = in.cand + in.bond[b].cand_base + (int64_t)(tr * g.nct + tc) * spt;
+          if (!s_warp[b]) {
+            screen_tile_stored(in, b, r[b], r0, nr, c0, nc, g.te, s_sr[b], s_sc[b], s_pend[b],
+                               slot, sm.s);
+            if (threadIdx.x == 0)
+              for (int x = 1; x < spt; ++x) slot[x] = Cand{0ull, LLONG_MAX, -2, -2};
+          } else {
+            carried_warp(in, g.te, b, r0, nr, c0, nc, s_pend[b], slot, spt);
+          }
+        }
+        break;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (nxt >= N[qq]) {
+        nxt = -1;
+        if (!switched) {
+          switched = true;
+          q0 = qq ^ 1;
+          const int32_t t = H[q0] + atomicAdd(ctr[q0], 1);
+          nxt = t < N[q0] ? t : -1;
+        }
+      } else {
+        q0 = qq;
+      }
+      s_q = q0;
+      s_item = nxt;
     }
   }
 }
@@ -1531,7 +1682,7 @@ __device__ void decide_bond_fp64(const InstDev &in, Ctrl &cr, int b, DecideSmem 
     cr.st_rows[b] = sm.q_prow;
     cr.st_cols[b] = sm.q_pcol;
     cr.e_pend[b] = 0;
-    if (b == 0) cr.steal = 0;  // tile counter of the next screen
+    if (b == 0) cr.steal = cr.steal2 = 0;  // item counters of the next screen
   }
   const int64_t nt = sm.q_nt;
   KeyBest best{0ull, LLONG_MAX, -1, -1};
@@ -1580,7 +1731,7 @@ __device__ void decide_bond_rescore(const InstDev &in, Ctrl &cr, int b, DecideSm
     cr.st_rows[b] = sm.q_prow;
     cr.st_cols[b] = sm.q_pcol;
     cr.e_pend[b] = 0;
-    if (b == 0) cr.steal = 0;
+    if (b == 0) cr.steal = cr.steal2 = 0;
   }
   const int64_t nt = sm.q_nt;
   const int k = (int)min((int64_t)min(in.topk, RS_K), nt);
@@ -2546,10 +2697,11 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
           const int64_t rows = rows_of(in, ro, b), cols = cols_of(in, ro, b);
           const int64_t ld = B.ldR, as = B.prow[ro[b]], cs = B.pcol[ro[b]];
           for (int64_t x = first_item(base, gt, NTOT); x < base + rows; x += NTOT)
-            B.ew[x - base] = -(B.E[(x - base) * ld + cs] / B.E[as * ld + cs]);
+            sv_put(in, B.ew, x - base,
+                   -(sv_get(in, B.E, (x - base) * ld + cs) / sv_get(in, B.E, as * ld + cs)));
           base += rows;
           for (int64_t x = first_item(base, gt, NTOT); x < base + cols; x += NTOT)
-            B.erow[x - base] = B.E[as * ld + (x - base)];
+            B.erow[x - base] = B.E[as * ld + (x - base)];  // the same 8 bytes in either form
           base += cols;
         }
         if (ad[b]) {

@@ -249,8 +249,16 @@ class TTCross:
                                          _stream_handle(stream)))
         return out
 
-    def cores(self):
-        return [self.core(k) for k in range(1, self.d + 1)]
+    def cores(self, stream=None):
+        """Every core to host memory (one wait for the run)."""
+        s = self.ranks()
+        out = []
+        for k in range(1, self.d + 1):
+            c = np.zeros((int(s[k - 1]), int(self.n[k - 1]), int(s[k])), np.float64)
+            _check(self._L.ttcross_get_cores(self._h, int(k), c.ctypes.data_as(C.c_void_p), 0,
+                                             _stream_handle(stream)))
+            out.append(c)
+        return out
 
     def pivots(self, k: int):
         """(I_{<=k}, J_{>k}) of bond k (1-based) as int32 arrays."""
