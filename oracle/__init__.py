@@ -80,6 +80,11 @@ def lib():
             L.orc_residual.argtypes = [P, C.c_int, C.c_int64, C.c_int64]
             L.orc_apply.argtypes = [P, i32p, i32p, i32p]
             L.orc_set_stored.argtypes = [P, C.c_int]
+            L.orc_set_sampled.argtypes = [P, C.c_int64, C.c_uint64, C.c_int]
+            L.orc_last_screened.restype = C.c_int64
+            L.orc_last_screened.argtypes = [P]
+            L.orc_rook_moves.restype = C.c_int64
+            L.orc_rook_moves.argtypes = [P]
             L.orc_stored_residual.restype = C.c_double
             L.orc_stored_residual.argtypes = [P, C.c_int, C.c_int64, C.c_int64]
             L.orc_E.argtypes = [P, C.c_int, f64p]
@@ -206,6 +211,19 @@ class Oracle:
         out = np.zeros((rows.value, cols.value))
         self._L.orc_E(self._h, int(b), _p(out, C.c_double))
         return out
+
+    def set_sampled(self, nl: int, seed: int = 20240715, max_rook: int = 8):
+        """Alg. 1 with a random sample set of nl entries per superblock and up
+        to max_rook rounds of row / column refinement (nl = 0: exhaustive)."""
+        rc = self._L.orc_set_sampled(self._h, int(nl), C.c_uint64(seed), int(max_rook))
+        if rc:
+            raise ValueError(f"orc_set_sampled -> {rc}")
+
+    def last_screened(self) -> int:
+        return int(self._L.orc_last_screened(self._h))
+
+    def rook_moves(self) -> int:
+        return int(self._L.orc_rook_moves(self._h))
 
     def apply(self, add, row, col) -> int:
         add = np.ascontiguousarray(add, dtype=np.int32)

@@ -54,8 +54,19 @@ struct orc_state {
   int stored;
   double *E[ORC_MAXD];
   int64_t st_rows[ORC_MAXD], st_cols[ORC_MAXD];
+  /* Alg. 1 with a random sample set (recompute form): nl samples per bond
+     and screen, SplitMix64 seeded with lseed, at most max_rook rounds of
+     the row / column refinement; nl = 0 screens the whole superblock */
+  int64_t nl;
+  uint64_t lseed;
+  int max_rook;
+  int64_t screens;        /* screens since the start (the sample counter) */
+  int64_t last_screened;  /* entries evaluated by the last screen */
+  int64_t rook_moves;     /* refinement steps that moved a pivot */
   int initialized;
 };
+
+static uint64_t splitmix64_at(uint64_t seed, uint64_t k);
 
 /* ------------------------------------------------------------------------- */
 /* The arithmetic contract's dot product: a serial FMA chain from +0.        */
@@ -292,7 +303,17 @@ int orc_init_at(orc_state *s, const int32_t *start) {
     for (int64_t a = 0; a < rows; ++a) replay_row(s, b, a, 1);
     s->st_rows[b] = s->st_cols[b] = 0; /* nothing stored yet */
   }
+  s->screens = 0;
+  s->rook_moves = 0;
   s->initialized = 1;
+  return ORC_OK;
+}
+
+int orc_set_sampled(orc_state *s, int64_t nl, uint64_t seed, int max_rook) {
+  if (nl < 0 || max_rook < 0) return ORC_ERR_INVALID_ARG;
+  s->nl = nl;
+  s->lseed = seed;
+  s->max_rook = max_rook;
   return ORC_OK;
 }
 
@@ -348,6 +369,76 @@ static best_t screen_rows(const orc_state *s, int b, int64_t a0, int64_t a1) {
   return bt;
 }
 
+/* Residual E(a,c) = A - chain(T(a,:), R(:,c)) of one superblock entry as
+   best_t candidate bookkeeping: keeps (|E|, lin) under the tie rule. */
+static void take_entry(const orc_state *s, int b, int64_t a, int64_t c, best_t *bt) {
+  int32_t idx[ORC_MAXD];
+  sb_index(s, b, a, c, idx);
+  double A = orc_entry(s, idx);
+  double e = A - chain(s->T[b] + a * s->maxr[b], 1, s->R[b] + c, s->cols_cap[b], s->r[b]);
+  if (!isfinite(e)) { bt->bad = 1; return; }
+  double v = fabs(e);
+  int64_t lin = lin_index(s, idx);
+  if (better(v, lin, bt)) { bt->v = v; bt->lin = lin; bt->a = a; bt->c = c; }
+}
+
+/* Alg. 1 on the superblock of bond b with a random sample set L:
+     - L = nl entries (a, c) drawn with replacement, sample j of bond b in
+       screen t from SplitMix64 outputs 2k and 2k+1, k = (t (d-1) + b) nl + j,
+       a = floor(x rows / 2^64), c = floor(x' cols / 2^64);
+     - (a*, c*) = argmax over L of |E| (ties: lowest linear index);
+     - refinement (the while loop of Alg. 1): a* moves to the argmax of column
+       c*, then c* to the argmax of row a*, each only to a strictly larger
+       |E|; repeated until a round moves neither (the pivot then dominates
+       its row and column) or max_rook rounds have run.                     */
+static best_t sampled_screen(orc_state *s, int b) {
+  const int64_t rows = rows_of(s, b), cols = cols_of(s, b);
+  const int64_t t = s->screens;
+  best_t parts[256];
+  int nt = s->nthreads > 256 ? 256 : s->nthreads;
+  if (nt > s->nl) nt = s->nl < 1 ? 1 : (int)s->nl;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+#endif
+  for (int th = 0; th < nt; ++th) {
+    best_t bt = {-1.0, INT64_MAX, -1, -1, 0.0, 0};
+    const int64_t j0 = s->nl * th / nt, j1 = s->nl * (th + 1) / nt;
+    for (int64_t j = j0; j < j1; ++j) {
+      const uint64_t k = (uint64_t)((t * (s->d - 1) + b) * s->nl + j);
+      const uint64_t x0 = splitmix64_at(s->lseed, 2 * k), x1 = splitmix64_at(s->lseed, 2 * k + 1);
+      const int64_t a = (int64_t)(uint64_t)(((unsigned __int128)x0 * (uint64_t)rows) >> 64);
+      const int64_t c = (int64_t)(uint64_t)(((unsigned __int128)x1 * (uint64_t)cols) >> 64);
+      take_entry(s, b, a, c, &bt);
+    }
+    parts[th] = bt;
+  }
+  best_t bt = parts[0];
+  for (int th = 1; th < nt; ++th) {
+    if (parts[th].a >= 0 && (bt.a < 0 || better(parts[th].v, parts[th].lin, &bt))) bt = parts[th];
+    bt.bad |= parts[th].bad;
+  }
+  int64_t evaluated = s->nl;
+  for (int round = 0; round < s->max_rook && bt.a >= 0 && !bt.bad; ++round) {
+    int moved = 0;
+    /* column c*: the best row */
+    best_t col = {-1.0, INT64_MAX, -1, -1, 0.0, 0};
+    for (int64_t a = 0; a < rows; ++a) take_entry(s, b, a, bt.c, &col);
+    evaluated += rows;
+    bt.bad |= col.bad;
+    if (col.a >= 0 && col.v > bt.v) { bt.v = col.v; bt.lin = col.lin; bt.a = col.a; moved = 1; }
+    /* row a*: the best column */
+    best_t row = {-1.0, INT64_MAX, -1, -1, 0.0, 0};
+    for (int64_t c = 0; c < cols; ++c) take_entry(s, b, bt.a, c, &row);
+    evaluated += cols;
+    bt.bad |= row.bad;
+    if (row.a >= 0 && row.v > bt.v) { bt.v = row.v; bt.lin = row.lin; bt.c = row.c; moved = 1; }
+    s->rook_moves += moved;
+    if (!moved) break;
+  }
+  s->last_screened += evaluated;
+  return bt;
+}
+
 double orc_residual(const orc_state *s, int b, int64_t a, int64_t c) {
   return sb_entry(s, b, a, c) -
          chain(s->T[b] + a * s->maxr[b], 1, s->R[b] + c, s->cols_cap[b], s->r[b]);
@@ -362,6 +453,18 @@ int orc_screen(orc_state *s, double *best, int64_t *lin, int32_t *row,
                int32_t *col, double *maxabs) {
   if (!s->initialized) return ORC_ERR_INVALID_ARG;
   int bad = 0;
+  s->last_screened = 0;
+  if (s->nl > 0 && !s->stored) {
+    for (int b = 0; b < s->d - 1; ++b) {
+      best_t bt = sampled_screen(s, b);
+      bad |= bt.bad;
+      best[b] = bt.v; lin[b] = bt.lin;
+      row[b] = (int32_t)bt.a; col[b] = (int32_t)bt.c;
+      maxabs[b] = 0.0;
+    }
+    s->screens += 1;
+    return bad ? ORC_ERR_NONFINITE : ORC_OK;
+  }
   for (int b = 0; b < s->d - 1; ++b) {
     int64_t rows = rows_of(s, b);
     int nt = s->nthreads;
@@ -393,9 +496,14 @@ int orc_screen(orc_state *s, double *best, int64_t *lin, int32_t *row,
     best[b] = bt.v; lin[b] = bt.lin;
     row[b] = (int32_t)bt.a; col[b] = (int32_t)bt.c;
     maxabs[b] = bt.maxabs;
+    s->last_screened += rows * cols_of(s, b);
   }
+  s->screens += 1;
   return bad ? ORC_ERR_NONFINITE : ORC_OK;
 }
+
+int64_t orc_last_screened(const orc_state *s) { return s->last_screened; }
+int64_t orc_rook_moves(const orc_state *s) { return s->rook_moves; }
 
 /* ------------------------------------------------------------------------- */
 /* One pivot step on every bond that adds (eq. aca_approx_T, Sec. 3.1.1),
@@ -722,7 +830,7 @@ int orc_run(orc_state *s, double eps, int64_t nsamples, uint64_t seed,
   for (;;) {
     rc = orc_screen(s, best, lin, row, col, maxabs);
     st->sweeps += 1;
-    for (int b = 0; b < d - 1; ++b) st->entries_screened += rows_of(s, b) * cols_of(s, b);
+    st->entries_screened += s->last_screened;
     if (rc) { st->status = rc; return rc; }
     double theta = tau * xrms;
     int nadd = 0;

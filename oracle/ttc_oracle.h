@@ -10,8 +10,10 @@
  *   - the tensor X is given entry-wise by a function (Sec. 5 intro): Hilbert
  *     tensor (eq. HilbertTensor, 0-based: 1/(1+i_1+...+i_d)), a TT of given
  *     cores, or a Maxwellian f(x,v);
- *   - the greedy pivot search of Alg. 1 with the sample set L taken as the
- *     whole superblock of Alg. 2 (exhaustive residual screen);
+ *   - the greedy pivot search of Alg. 1 on the superblock of Alg. 2, with the
+ *     sample set L taken as the whole superblock (exhaustive residual screen)
+ *     or as random entries followed by the row / column refinement of Alg. 1
+ *     (orc_set_sampled);
  *   - all bonds searched simultaneously (Jacobi sweep, Sec. 2.3 / 3.2.3),
  *     pivots appended with nestedness (eq. nestedpivots);
  *   - the cross factor T = C U updated by eq. aca_approx_T / aca_approx_T_sub,
@@ -117,6 +119,20 @@ double orc_residual(const orc_state *s, int b, int64_t a, int64_t c);
 int orc_set_stored(orc_state *s, int on);
 /* Stored E(a,c) of bond b (NaN outside the stored extent or when off). */
 double orc_stored_residual(const orc_state *s, int b, int64_t a, int64_t c);
+
+/* Alg. 1 with a random sample set L (Sec. 2.3), recompute form only: nl > 0
+   screens nl random entries of every superblock (drawn with replacement by
+   SplitMix64(seed): sample j of bond b in screen t uses outputs 2k, 2k+1 with
+   k = (t (d-1) + b) nl + j, a = floor(x rows / 2^64), c = floor(x' cols /
+   2^64); t counts screens from the start), takes their argmax (tie rule as
+   above), then refines it: the row moves to the argmax of its column, then
+   the column to the argmax of its row, each only to a strictly larger |E|,
+   until a round moves neither or max_rook rounds ran.  nl = 0 restores the
+   exhaustive screen.  Ignored by the stored form. */
+int orc_set_sampled(orc_state *s, int64_t nl, uint64_t seed, int max_rook);
+/* entries the last screen evaluated; refinement steps that moved a pivot */
+int64_t orc_last_screened(const orc_state *s);
+int64_t orc_rook_moves(const orc_state *s);
 
 /* Append pivot (row[b], col[b]) to every bond b with add[b] != 0 (row/col are
    superblock coordinates of the sweep-start superblock), update T, R, U and
