@@ -119,6 +119,20 @@ typedef struct {
   int32_t grid_ctas;        /* persistent CTAs (0 = one wave at full occupancy) */
   double wait_limit_s;      /* limit of every device-side wait, seconds (default 2.0) */
   int32_t residual;         /* ttc_residual (default TTC_RESIDUAL_RECOMPUTE) */
+  /* Alg. 1 with a random sample set L (Sec. 2.3) instead of the whole
+     superblock, for superblocks too large to screen: screen_samples > 0
+     entries of every bond's superblock are drawn per screen (with
+     replacement; SplitMix64(screen_seed), sample j of bond k in screen t from
+     outputs 2i and 2i+1, i = (t (d-1) + k-1) screen_samples + j, row / column
+     = floor(x rows / 2^64) / floor(x' cols / 2^64)); their argmax (ties:
+     lowest linear index) is refined as in the while loop of Alg. 1: the row
+     moves to the argmax of the pivot's column, then the column to the argmax
+     of its row, each only to a strictly larger |E|, for at most rook_rounds
+     rounds or until a round moves neither.  Recompute form and FP64 only
+     (else TTC_ERR_INVALID_ARG).  0 (default): the whole superblock. */
+  int64_t screen_samples;
+  uint64_t screen_seed;     /* default 20240715 */
+  int32_t rook_rounds;      /* default 8, in [0, 64] */
 } ttc_options;
 
 typedef struct {

@@ -836,6 +836,14 @@ int orc_run(orc_state *s, double eps, int64_t nsamples, uint64_t seed,
     int nadd = 0;
     for (int b = 0; b < d - 1; ++b) {
       add[b] = best[b] > theta && best[b] > 0.0 && s->r[b] < s->maxr[b];
+      /* the pivot step divides by A(a*,c*) - chain(T(a*,:), R(:,c*)) (Sec.
+         3.1.1); where that residual, formed afresh, is zero (or so small that
+         its reciprocal overflows) the screened value was rounding noise and
+         the bond takes no pivot in this sweep */
+      if (add[b]) {
+        double piv = orc_residual(s, b, row[b], col[b]);
+        if (isfinite(piv) && !isfinite(1.0 / piv)) add[b] = 0;
+      }
       nadd += add[b];
     }
     if (nadd) {

@@ -181,6 +181,13 @@ ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, 
   ra.wait_ns = (int64_t)(h0->opt.wait_limit_s * 1e9);
   ra.persistent = h0->opt.host_loop ? 0 : 1;
   ra.mixed = 0;
+  ra.sampled = 0;
+  ra.max_rook = 0;
+  for (int i = 0; i < count; ++i)
+    if (hs[i]->hi.nl > 0) {
+      ra.sampled = 1;
+      ra.max_rook = std::max(ra.max_rook, hs[i]->hi.max_rook);
+    }
   for (int i = 0; i < count; ++i)
     if (hs[i]->hi.prec != P_FP64 && !hs[i]->hi.stored) ra.mixed = 1;  // refinement phases
   int64_t iters = 0;
@@ -210,6 +217,14 @@ ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, 
     if (done) return TTC_OK;
     CU(launch_phase(PH_SCREEN, ra, h0->grid, s));
     CU(launch_phase(PH_DECIDE, ra, h0->grid, s));
+    if (ra.sampled) {
+      // refinement rounds: a phase pair per step (no-ops once every bond is done)
+      for (int k = 0; k < 2 * ra.max_rook; ++k) {
+        CU(launch_phase(PH_ROOK_SCAN, ra, h0->grid, s));
+        CU(launch_phase(PH_ROOK_DECIDE, ra, h0->grid, s));
+      }
+      CU(launch_phase(PH_FINALIZE, ra, h0->grid, s));
+    }
     if (ra.mixed) {
       CU(launch_phase(PH_REFINE, ra, h0->grid, s));
       CU(launch_phase(PH_DECIDE2, ra, h0->grid, s));
@@ -238,6 +253,9 @@ ttc_status ttcross_default_options(ttc_options *opt) {
   opt->grid_ctas = 0;
   opt->wait_limit_s = 2.0;
   opt->residual = TTC_RESIDUAL_RECOMPUTE;
+  opt->screen_samples = 0;
+  opt->screen_seed = 20240715ull;
+  opt->rook_rounds = 8;
   return TTC_OK;
 }
 
@@ -264,6 +282,13 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     return fail(TTC_ERR_INVALID_ARG, "grid_ctas outside [0,%d]", GRID_CAP);
   if (o.residual != TTC_RESIDUAL_RECOMPUTE && o.residual != TTC_RESIDUAL_STORED)
     return fail(TTC_ERR_INVALID_ARG, "unknown residual form %d", o.residual);
+  if (o.screen_samples < 0 || o.screen_samples > ((int64_t)1 << 40) || o.rook_rounds < 0 ||
+      o.rook_rounds > 64)
+    return fail(TTC_ERR_INVALID_ARG, "screen_samples / rook_rounds out of range");
+  if (o.screen_samples > 0 &&
+      (o.residual != TTC_RESIDUAL_RECOMPUTE || o.precision != TTC_PREC_FP64))
+    return fail(TTC_ERR_INVALID_ARG,
+                "a sampled screen needs the recompute residual form and FP64 precision");
   int64_t total = 1;
   bool overflow = false;
   int64_t hsum = 0;
@@ -354,6 +379,9 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
   // about 1e-7 of the largest entries, which the stop thresholds here undercut
   I.prec = o.precision == TTC_PREC_AUTO ? P_SPLIT : o.precision;
   I.topk = o.topk;
+  I.nl = o.screen_samples;
+  I.lseed = o.screen_seed;
+  I.max_rook = o.rook_rounds;
   I.nsamples = ns;
   I.exhaustive = exhaustive ? 1 : 0;
   I.seed = o.seed;

@@ -90,6 +90,11 @@ struct Ctrl {
                              // decide phase after it)
   int64_t entries_fresh;     // entries evaluated as A - T R (the rest carried)
   int64_t stored_bytes;      // bytes of E read and written by the screens
+  // sampled screen: refinement step of each bond (0 none / done, 1 the
+  // column of the pivot next, 2 its row next), rounds run, whether the
+  // running round moved the pivot
+  int32_t rook_stage[TTC_MAXD], rook_round[TTC_MAXD], rook_moved[TTC_MAXD];
+  int64_t screen_t;          // sampled screen: screens run (the sample counter)
   int32_t dkind;             // work of the coming decide phases, fixed by the
                              // screen phase: DK_BONDS, DK_VERIFY or DK_NONE
   int32_t pad_dkind;
@@ -116,7 +121,12 @@ struct InstDev {
   int64_t mx_stride[TTC_MAXD];
   int32_t prec;
   int32_t topk;
-  int32_t stored;                    // stored-residual screen (FP64 only)
+  int32_t stored;                    // stored-residual screen
+  // Alg. 1 with a random sample set: samples per bond and screen (0: the
+  // whole superblock), their SplitMix64 seed, refinement rounds
+  int64_t nl;
+  uint64_t lseed;
+  int32_t max_rook;
   BondDev bond[TTC_MAXB];
   SetDev empty;                      // I_{<=0} / J_{>d}: one empty multi-index
   double *xs;                        // X at the error samples
@@ -178,6 +188,8 @@ struct RunArgs {
   int32_t persistent;
   int32_t max_iters;     // sweep cap of the launch (sum of rank caps + refinements)
   int32_t *smid;         // [grid] the SM each CTA of a persistent launch runs on
+  int32_t sampled;       // some instance screens a random sample set (Alg. 1)
+  int32_t max_rook;      // the largest refinement round count of the instances
 };
 
 // ---------------------------------------------------------------------------

@@ -145,6 +145,9 @@ __device__ __forceinline__ const InstDev &inst(const RunArgs &ra, int ii) {
   return ii == 0 ? s_inst0 : *ra.insts[ii];
 }
 
+// sampled screen's decide item (defined with its refinement phases below)
+__device__ void decide_bond_sampled(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm);
+
 // sampled-error split (defined with the error evaluation below)
 __device__ void choose_split(const InstDev &in, const int32_t *r, int &pL, int &pR);
 __device__ double split_cost(const InstDev &in, const int32_t *r, int pL, int pR);
@@ -1456,6 +1459,78 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
   }
 }
 
+// ---------------------------------------------------------------------------
+// Alg. 1 with a random sample set L (recompute form, FP64).  Per screen t
+// and bond b, samples j < nl are the superblock entries
+//   a = floor(x rows / 2^64), c = floor(x' cols / 2^64),
+//   x = SplitMix64(seed) output 2i, x' = output 2i+1, i = (t nb + b) nl + j;
+// their argmax (lowest linear index on ties) is refined by whole-column and
+// whole-row scans (the while loop of Alg. 1) in the refinement phases.
+
+// column-major linear index of superblock entry (a, c) of bond b
+__device__ __forceinline__ int64_t entry_lin(const InstDev &in, int b, int64_t a, int64_t c) {
+  const int64_t nb0 = in.n[b], nb1 = in.n[b + 1];
+  const int64_t p = a / nb0, i = a - p * nb0;
+  const int64_t q = c / nb1, j = c - q * nb1;
+  return left_set(in, b).lin[p] + i * in.stride[b] + j * in.stride[b + 1] +
+         right_set(in, b).lin[q];
+}
+
+// E(a,c) = A(a,c) - chain(T(a,:), R(:,c)) with K terms: the contract's residual
+__device__ __forceinline__ double residual_at(const InstDev &in, int b, int K, int64_t a,
+                                              int64_t c) {
+  const BondDev &B = in.bond[b];
+  return __dsub_rn(sb_entry(in, b, a, c), chain(B.T + a, B.ldT, B.R + c, B.ldR, K));
+}
+
+__device__ __forceinline__ void take_key(KeyBest &best, double e, int64_t lin, int64_t a,
+                                         int64_t c) {
+  const uint64_t k = abs_key(e);
+  if (best.row < 0 || k > best.key || (k == best.key && lin < best.lin)) {
+    best.key = k;
+    best.lin = lin;
+    best.row = (int32_t)a;
+    best.col = (int32_t)c;
+  }
+}
+
+// the CTA's best of its share of the samples of every bond, into the bond's
+// slot blockIdx.x (thread x of the grid takes samples x, x + G NT, ...)
+__device__ void screen_sampled_instance(const InstDev &in, const int32_t *r, int64_t t,
+                                        PhaseSmem &sm) {
+  const int64_t NTOT = (int64_t)gridDim.x * NT;
+  const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
+  for (int b = 0; b < in.nb; ++b) {
+    const int64_t rows = rows_of(in, r, b), cols = cols_of(in, r, b);
+    KeyBest best{0ull, LLONG_MAX, -1, -1};
+    for (int64_t j = gt; j < in.nl; j += NTOT) {
+      const uint64_t i = (uint64_t)((t * in.nb + b) * in.nl + j);
+      const int64_t a = (int64_t)__umul64hi(splitmix64_at(in.lseed, 2 * i), (uint64_t)rows);
+      const int64_t c = (int64_t)__umul64hi(splitmix64_at(in.lseed, 2 * i + 1), (uint64_t)cols);
+      take_key(best, residual_at(in, b, r[b], a, c), entry_lin(in, b, a, c), a, c);
+    }
+    best = block_best(best, sm.s.sk, sm.s.sl, sm.s.sr, sm.s.sc);
+    if (threadIdx.x == 0) {
+      Cand *slot = in.cand + in.bond[b].cand_base + blockIdx.x;
+      *slot = best.row >= 0 ? Cand{best.key, best.lin, best.row, best.col}
+                            : Cand{0ull, LLONG_MAX, -2, -2};
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Ctrl &cw = *in.ctrl;
+    int64_t fmas = 0;
+    for (int b = 0; b < in.nb; ++b) {
+      cw.ntiles[b] = gridDim.x;
+      fmas += in.nl * r[b];
+    }
+    cw.sweeps += 1;
+    cw.entries += in.nl * in.nb;
+    cw.entries_fresh += in.nl * in.nb;
+    cw.screen_fmas += fmas;
+    cw.screened = 1;
+  }
+}
+
 __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
   __shared__ CtrlSnap snap;
   const int32_t G = gridDim.x;
@@ -1472,6 +1547,11 @@ __device__ void phase_screen(const RunArgs &ra, PhaseSmem &sm) {
     const int32_t *r = snap.r;
     if (in.stored) {
       screen_stored_instance(in, r, sm);
+      continue;
+    }
+    if (in.nl > 0) {
+      // the screen counter is advanced by the decide phase, never here
+      screen_sampled_instance(in, r, ld_cg(cr.screen_t), sm);
       continue;
     }
     // every bond's tile geometry, one bond per thread
@@ -1569,11 +1649,14 @@ __device__ bool append_pivot(const InstDev &in, Ctrl &cr, int b, int64_t as, int
     const double piv = __dsub_rn(sm.apiv, chain(sm.hps, 1, sm.hcs, 1, z));
     const double delta = 1.0 / piv;
     sm.delta = delta;
-    sm.flag = isfinite(delta) ? 1 : 0;
+    // 1: a usable pivot; 0: the residual formed afresh at the pivot is zero
+    // (or its reciprocal overflows), so the screened value was rounding
+    // noise and the bond takes no pivot; -1: not finite
+    sm.flag = isfinite(delta) ? 1 : isfinite(piv) ? 0 : -1;
     B.delta[z] = delta;
   }
   __syncthreads();
-  if (!sm.flag) return false;
+  if (sm.flag != 1) return false;
   const double delta = sm.delta;
   double *U = B.U;
   const double *Ur = ustage ? sm.us : U;
@@ -1646,7 +1729,7 @@ __device__ void finalize_bond_v(const InstDev &in, Ctrl &cr, int b, DecideSmem &
   bool ok = true;
   if (add) ok = append_pivot(in, cr, b, row, col, rb, sm);
   if (add && ok && in.stored) stored_step(cr, b);
-  if (!ok) fail_instance(cr, 4);
+  if (add && !ok && sm.flag < 0) fail_instance(cr, 4);
   __syncthreads();
   if (threadIdx.x == 0) {
     cr.add[b] = (add && ok) ? 1 : 0;
@@ -1959,7 +2042,8 @@ __device__ void verify_instance(const InstDev &in, Ctrl &cr, DecideSmem &sm) {
         // the mixed recompute forms certified their bests only against the
         // old threshold: they screen again; the FP64 and stored forms keep
         // FP64 values of their bests
-        sm.flag = (in.prec == P_FP64 || in.stored) ? 1 : 0;
+        // (a sampled screen draws new samples, as its reference does)
+        sm.flag = ((in.prec == P_FP64 || in.stored) && in.nl == 0) ? 1 : 0;
       }
     }
     __syncthreads();
@@ -1981,8 +2065,12 @@ __device__ void verify_instance(const InstDev &in, Ctrl &cr, DecideSmem &sm) {
 // phase fixed.  The numbering must not depend on words that items rewrite
 // during the phase (state, screened, pending): a CTA that read them late
 // would number the items differently, and one bond would be decided twice.
+// item kinds of for_decide_items
+enum ItemMode { IM_DECIDE = 0, IM_PENDING = 1, IM_ROOK = 2, IM_FINALIZE = 3 };
+
 template <class F>
-__device__ void for_decide_items(const RunArgs &ra, bool second, F &&f) {
+__device__ void for_decide_items(const RunArgs &ra, int mode, F &&f) {
+  __shared__ int s_take;
   const int64_t G = gridDim.x;
   int64_t first = 0;
   for (int ii = 0; ii < ra.count; ++ii) {
@@ -1991,24 +2079,38 @@ __device__ void for_decide_items(const RunArgs &ra, bool second, F &&f) {
     const int64_t end = first + in.nb + 1;
     for (int64_t x = first + ((s_place - first) % G + G) % G; x < end; x += G) {
       const int slot = (int)(x - first) - 1;
-      const int kind = ld_cg(cr.dkind);
-      if (slot < 0) {
-        if (!second && kind == DK_VERIFY) f(ii, -1);
-      } else if (kind == DK_BONDS && ld_cg(cr.state) != ST_DONE &&
-                 (!second || ld_cg(cr.pending[slot]))) {
-        f(ii, slot);
+      // one thread decides and the CTA follows: the words it reads can be
+      // rewritten by other CTAs' items during the phase (a failing bond ends
+      // the instance), and every thread of the CTA must take the same branch
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const int kind = ld_cg(cr.dkind);
+        bool take;
+        if (slot < 0) {
+          take = mode == IM_DECIDE && kind == DK_VERIFY;
+        } else {
+          take = kind == DK_BONDS && ld_cg(cr.state) != ST_DONE;
+          if (mode == IM_PENDING) take = take && ld_cg(cr.pending[slot]);
+          if (mode == IM_ROOK) take = take && in.nl > 0 && ld_cg(cr.rook_stage[slot]) != 0;
+          if (mode == IM_FINALIZE) take = take && in.nl > 0;
+        }
+        s_take = take ? 1 : 0;
       }
+      __syncthreads();
+      if (s_take) f(ii, slot);
     }
     first = end;
   }
 }
 
 __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
-  for_decide_items(ra, false, [&](int ii, int b) {
+  for_decide_items(ra, IM_DECIDE, [&](int ii, int b) {
     const InstDev &in = inst(ra, ii);
     Ctrl &cr = *in.ctrl;
     if (b < 0) {
       verify_instance(in, cr, sm.d);
+    } else if (in.nl > 0) {
+      decide_bond_sampled(in, cr, b, sm.d);
     } else if (in.prec == P_FP64) {
       decide_bond_fp64(in, cr, b, sm.d);
     } else if (in.stored) {
@@ -2022,7 +2124,7 @@ __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
 // mixed forms, part 2: the FP64 results of the refined tiles join the
 // re-scored candidates; the best is the FP64 argmax of the screen.
 __device__ void phase_decide2(const RunArgs &ra, PhaseSmem &sm) {
-  for_decide_items(ra, true, [&](int ii, int b) {
+  for_decide_items(ra, IM_PENDING, [&](int ii, int b) {
     const InstDev &in = inst(ra, ii);
     Ctrl &cr = *in.ctrl;
     DecideSmem &d = sm.d;
@@ -2046,6 +2148,163 @@ __device__ void phase_decide2(const RunArgs &ra, PhaseSmem &sm) {
     }
     __syncthreads();
     finalize_bond(in, cr, b, d);
+  });
+}
+
+// merge of the G candidate slots of bond b (block-wide; the best is valid
+// in every thread)
+__device__ KeyBest merge_slots(const InstDev &in, Ctrl &cr, int b, int64_t nt, DecideSmem &sm) {
+  const Cand *cand = in.cand + in.bond[b].cand_base;
+  KeyBest best{0ull, LLONG_MAX, -1, -1};
+  int bad = 0;
+  for (int64_t t = threadIdx.x; t < nt; t += NT) {
+    KeyBest o{cand[t].key, cand[t].lin, cand[t].row, cand[t].col};
+    bad += o.row == -1;
+    kb_take(best, o);
+  }
+  if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
+  best = block_best(best, sm.rk, sm.rl, sm.rr, sm.rc);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sm.rk[0] = best.key;
+    sm.rl[0] = best.lin;
+    sm.rr[0] = best.row;
+    sm.rc[0] = best.col;
+  }
+  __syncthreads();
+  return KeyBest{sm.rk[0], sm.rl[0], sm.rr[0], sm.rc[0]};
+}
+
+// sampled screen, decide item of bond b: the argmax over the samples becomes
+// the pivot candidate, and its refinement starts (column step first)
+__device__ void decide_bond_sampled(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
+  const KeyBest best = merge_slots(in, cr, b, gridDim.x, sm);
+  if (threadIdx.x == 0) {
+    cr.best_key[b] = best.key;
+    cr.best_lin[b] = best.lin;
+    cr.best_row[b] = best.row;
+    cr.best_col[b] = best.col;
+    const bool go = in.max_rook > 0 && best.row >= 0 && best.key <= KEY_INF;
+    cr.rook_stage[b] = go ? 1 : 0;
+    cr.rook_round[b] = 0;
+    cr.rook_moved[b] = 0;
+    if (b == 0) cr.screen_t = ld_cg(cr.screen_t) + 1;
+  }
+  __syncthreads();
+}
+
+// some bond of a sampled instance is in a refinement step
+__device__ bool any_rook(const RunArgs &ra) {
+  __shared__ int hit;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    hit = 0;
+    for (int ii = 0; ii < ra.count; ++ii) {
+      const InstDev &in = inst(ra, ii);
+      if (in.nl == 0) continue;
+      const Ctrl &cr = *in.ctrl;
+      if (ld_cg(cr.state) == ST_DONE || ld_cg(cr.dkind) != DK_BONDS) continue;
+      for (int b = 0; b < in.nb; ++b)
+        if (ld_cg(cr.rook_stage[b])) hit = 1;
+    }
+  }
+  __syncthreads();
+  return hit != 0;
+}
+
+// refinement scan: the pivot's column (step 1) or row (step 2) of every bond
+// in a refinement step, spread over the grid; each CTA's best of its share
+// goes to its slot
+__device__ void phase_rook_scan(const RunArgs &ra, PhaseSmem &sm) {
+  __shared__ CtrlSnap snap;
+  __shared__ int32_t s_stage[TTC_MAXB], s_row[TTC_MAXB], s_col[TTC_MAXB];
+  const int64_t NTOT = (int64_t)gridDim.x * NT;
+  const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
+  for (int ii = 0; ii < ra.count; ++ii) {
+    const InstDev &in = inst(ra, ii);
+    if (in.nl == 0) continue;
+    const Ctrl &cr = *in.ctrl;
+    snap_ctrl(cr, in.nb, snap);
+    if (snap.state == ST_DONE || ld_cg(cr.dkind) != DK_BONDS) continue;
+    if (threadIdx.x < in.nb) {
+      s_stage[threadIdx.x] = ld_cg(cr.rook_stage[threadIdx.x]);
+      s_row[threadIdx.x] = ld_cg(cr.best_row[threadIdx.x]);
+      s_col[threadIdx.x] = ld_cg(cr.best_col[threadIdx.x]);
+    }
+    __syncthreads();
+    const int32_t *r = snap.r;  // the sweep-start ranks (no pivot added yet)
+    for (int b = 0; b < in.nb; ++b) {
+      const int st = s_stage[b];
+      if (!st) continue;
+      const int64_t rows = rows_of(in, r, b), cols = cols_of(in, r, b);
+      KeyBest best{0ull, LLONG_MAX, -1, -1};
+      if (st == 1) {
+        const int64_t c = s_col[b];
+        for (int64_t a = gt; a < rows; a += NTOT)
+          take_key(best, residual_at(in, b, r[b], a, c), entry_lin(in, b, a, c), a, c);
+      } else {
+        const int64_t a = s_row[b];
+        for (int64_t c = gt; c < cols; c += NTOT)
+          take_key(best, residual_at(in, b, r[b], a, c), entry_lin(in, b, a, c), a, c);
+      }
+      best = block_best(best, sm.s.sk, sm.s.sl, sm.s.sr, sm.s.sc);
+      if (threadIdx.x == 0) {
+        Cand *slot = in.cand + in.bond[b].cand_base + blockIdx.x;
+        *slot = best.row >= 0 ? Cand{best.key, best.lin, best.row, best.col}
+                              : Cand{0ull, LLONG_MAX, -2, -2};
+      }
+    }
+  }
+}
+
+// refinement decide: the pivot moves to a strictly larger |E| of its column
+// (step 1) or row (step 2); a round is step 1 then step 2, and the
+// refinement ends after a round that moved nothing or after max_rook rounds
+__device__ void phase_rook_decide(const RunArgs &ra, PhaseSmem &sm) {
+  for_decide_items(ra, IM_ROOK, [&](int ii, int b) {
+    const InstDev &in = inst(ra, ii);
+    Ctrl &cr = *in.ctrl;
+    const KeyBest line = merge_slots(in, cr, b, gridDim.x, sm.d);
+    if (threadIdx.x == 0) {
+      const int st = ld_cg(cr.rook_stage[b]);
+      const uint64_t cur = ld_cg(cr.best_key[b]);
+      int moved = ld_cg(cr.rook_moved[b]);
+      const int32_t r_old = ld_cg(cr.r[b]);
+      const int32_t rows = (int32_t)rows_of(in, cr.r, b), cols = (int32_t)cols_of(in, cr.r, b);
+      cr.entries += st == 1 ? rows : cols;
+      cr.entries_fresh += st == 1 ? rows : cols;
+      cr.screen_fmas += (int64_t)(st == 1 ? rows : cols) * r_old;
+      if (line.row >= 0 && line.key > cur) {
+        cr.best_key[b] = line.key;
+        cr.best_lin[b] = line.lin;
+        if (st == 1)
+          cr.best_row[b] = line.row;
+        else
+          cr.best_col[b] = line.col;
+        moved = 1;
+      }
+      if (line.key > KEY_INF) cr.best_key[b] = line.key;  // a non-finite residual ends the bond
+      if (st == 1) {
+        cr.rook_stage[b] = 2;
+        cr.rook_moved[b] = moved;
+      } else {
+        const int round = ld_cg(cr.rook_round[b]) + 1;
+        cr.rook_round[b] = round;
+        const bool again = moved && round < in.max_rook && ld_cg(cr.best_key[b]) <= KEY_INF;
+        cr.rook_stage[b] = again ? 1 : 0;
+        cr.rook_moved[b] = 0;
+      }
+    }
+    __syncthreads();
+  });
+}
+
+// sampled screen: the stop test and the pivot append of every bond, on the
+// refined pivots
+__device__ void phase_finalize(const RunArgs &ra, PhaseSmem &sm) {
+  for_decide_items(ra, IM_FINALIZE, [&](int ii, int b) {
+    const InstDev &in = inst(ra, ii);
+    finalize_bond(in, *in.ctrl, b, sm.d);
   });
 }
 
@@ -3059,6 +3318,20 @@ __global__ void __launch_bounds__(NT, 2) k_persistent(RunArgs ra) {
     phase_decide(ra, sm);
     if (!grid_barrier(ra, 4)) return;
     clk.lap(ra, T_DECIDE);
+    if (ra.sampled) {
+      // the refinement of Alg. 1: a scan and a decide per step, then the
+      // stop tests on the refined pivots
+      for (int k = 0; k < 2 * ra.max_rook && any_rook(ra); ++k) {
+        phase_rook_scan(ra, sm);
+        if (!grid_barrier(ra, 10)) return;
+        phase_rook_decide(ra, sm);
+        if (!grid_barrier(ra, 11)) return;
+      }
+      clk.lap(ra, T_SCREEN);
+      phase_finalize(ra, sm);
+      if (!grid_barrier(ra, 12)) return;
+      clk.lap(ra, T_DECIDE);
+    }
     if (ra.mixed) {
       phase_refine(ra, sm);
       if (!grid_barrier(ra, 7)) return;
@@ -3105,6 +3378,18 @@ __global__ void __launch_bounds__(NT, 2) k_refine(RunArgs ra) {
 __global__ void __launch_bounds__(NT, 2) k_decide2(RunArgs ra) {
   cache_inst0(ra);
   phase_decide2(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
+}
+__global__ void __launch_bounds__(NT, 2) k_rook_scan(RunArgs ra) {
+  cache_inst0(ra);
+  phase_rook_scan(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
+}
+__global__ void __launch_bounds__(NT, 2) k_rook_decide(RunArgs ra) {
+  cache_inst0(ra);
+  phase_rook_decide(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
+}
+__global__ void __launch_bounds__(NT, 2) k_finalize(RunArgs ra) {
+  cache_inst0(ra);
+  phase_finalize(ra, *reinterpret_cast<PhaseSmem *>(dyn_smem));
 }
 __global__ void __launch_bounds__(NT, 2) k_tables(RunArgs ra) {
   cache_inst0(ra);
@@ -3189,6 +3474,9 @@ cudaError_t launch_phase(int phase, const RunArgs &ra, int grid, cudaStream_t s)
     case PH_REFINE: f = (const void *)k_refine; break;
     case PH_DECIDE2: f = (const void *)k_decide2; break;
     case PH_TABLES: f = (const void *)k_tables; break;
+    case PH_ROOK_SCAN: f = (const void *)k_rook_scan; break;
+    case PH_ROOK_DECIDE: f = (const void *)k_rook_decide; break;
+    case PH_FINALIZE: f = (const void *)k_finalize; break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = prep(f);

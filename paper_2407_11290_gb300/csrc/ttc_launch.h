@@ -8,7 +8,8 @@ namespace ttc {
 
 enum Phase {
   PH_INIT1 = 0, PH_INIT2 = 1, PH_INIT3 = 2, PH_SCREEN = 3, PH_DECIDE = 4, PH_UPDATE = 5,
-  PH_REFINE = 6, PH_DECIDE2 = 7, PH_TABLES = 8
+  PH_REFINE = 6, PH_DECIDE2 = 7, PH_TABLES = 8, PH_ROOK_SCAN = 9, PH_ROOK_DECIDE = 10,
+  PH_FINALIZE = 11
 };
 
 size_t phase_smem_bytes();

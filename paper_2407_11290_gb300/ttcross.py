@@ -59,7 +59,10 @@ class Options(C.Structure):
                 ("host_loop", C.c_int32),
                 ("grid_ctas", C.c_int32),
                 ("wait_limit_s", C.c_double),
-                ("residual", C.c_int32)]
+                ("residual", C.c_int32),
+                ("screen_samples", C.c_int64),
+                ("screen_seed", C.c_uint64),
+                ("rook_rounds", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -153,7 +156,8 @@ class TTCross:
     def __init__(self, n, gen, max_rank: int = 64, precision="fp64", nsamples: int = 10**6,
                  seed: int = 20240715, max_refine: int = 6, topk: int = 8, host_loop: bool = False,
                  grid_ctas: int = 0, wait_limit_s: float = 2.0, bond_max_rank=None,
-                 residual="recompute"):
+                 residual="recompute", screen_samples: int = 0, screen_seed: int = 20240715,
+                 rook_rounds: int = 8):
         L = load_library()
         self._L = L
         self.n = np.ascontiguousarray(n, dtype=np.int64)
@@ -169,6 +173,9 @@ class TTCross:
         o.grid_ctas = int(grid_ctas)
         o.wait_limit_s = float(wait_limit_s)
         o.residual = RESIDUALS[residual] if isinstance(residual, str) else int(residual)
+        o.screen_samples = int(screen_samples)
+        o.screen_seed = int(screen_seed)
+        o.rook_rounds = int(rook_rounds)
         keep = []
         if bond_max_rank is not None:
             bm = _i32(bond_max_rank)

@@ -97,3 +97,25 @@ def test_noalloc_wrapper_rejects_bad_cores_before_the_call():
         with pytest.raises(ttcross.TTCError) as e:
             ttcross.sampled_error_noalloc(n, gen, cores, 100, 1, out)
         assert e.value.status == ttcross.ERR_INVALID_ARG
+
+
+def test_sampled_screen_options_checked_on_host():
+    """The Python options struct matches the C one (defaults read back), and
+    a sampled screen with the stored form or a mixed precision is refused
+    before any device call."""
+    o = ttcross.default_options()
+    assert o.screen_samples == 0 and o.screen_seed == 20240715 and o.rook_rounds == 8
+    L = ttcross.load_library()
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 3)(8, 8, 8)
+    g = ttcross.Generator()
+    g.kind = ttcross.GEN_HILBERT
+    o.screen_samples = 100
+    o.residual = ttcross.RESIDUAL_STORED
+    assert L.ttcross_create(3, n, ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)) == \
+        ttcross.ERR_INVALID_ARG
+    assert b"sampled screen" in L.ttcross_last_error_string()
+    o.residual = ttcross.RESIDUAL_RECOMPUTE
+    o.rook_rounds = 65
+    assert L.ttcross_create(3, n, ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)) == \
+        ttcross.ERR_INVALID_ARG

@@ -197,15 +197,25 @@ def replay_with_resync(g, w, eps, cap, nsamples, rel=1e-13, stored=False, max_re
             if not add[b]:
                 continue
             z = int(r[b])
+            if z >= len(gI[b][0]) and sc["best"][b] <= floor * xmax:
+                add[b] = 0  # below the noise floor the GPU stopped this bond
+                continue
             assert z < len(gI[b][0]), f"GPU stopped bond {b + 1} at rank {z}"
             a, c = _coords(o, b, gI[b][0][z], gI[b][1][z])
+            piv = o.residual(b, a, c)
+            with np.errstate(divide="ignore", over="ignore"):
+                inv = np.float64(1.0) / np.float64(piv)
+            if np.isfinite(piv) and not np.isfinite(inv):
+                add[b] = 0  # a zero pivot: the bond takes none (in both runs)
+                continue
             if (a, c) != (rows[b], cols[b]):
                 e = abs(o.stored_residual(b, a, c) if stored else o.residual(b, a, c))
                 if sc["best"][b] > floor * xmax:
                     assert e >= sc["best"][b] - rel * xmax, (b, e, sc["best"][b])
                 ties += 1
                 rows[b], cols[b] = a, c
-        assert o.apply(add, rows, cols) == 0
+        if any(add):
+            assert o.apply(add, rows, cols) == 0
     return o, ties
 
 
