@@ -62,7 +62,10 @@ typedef enum {
 typedef enum {
   TTC_GEN_HILBERT = 0,    /* X(i) = 1/(1 + i_1 + ... + i_d) (eq. HilbertTensor, 0-based) */
   TTC_GEN_TT = 1,         /* X given by TT cores (tests; exact recovery) */
-  TTC_GEN_MAXWELLIAN = 2  /* f(x,v), see ttc_generator */
+  TTC_GEN_MAXWELLIAN = 2, /* f(x,v), see ttc_generator */
+  TTC_GEN_MAXWELLIAN_XV = 3 /* the 2d2v / 3d3v distributions of Sec. 5.2
+                               (eq. 2d2vFunction), modes interleaved
+                               (x, v_x, y, v_y[, z, v_z]), see ttc_generator */
 } ttc_gen_kind;
 
 /* Entry generator.  All pointers are host pointers, read during
@@ -80,7 +83,15 @@ typedef struct {
      x_m = 2 pi i / n_m (periodic), v = vmin + (vmax - vmin) i / (n - 1);
      rho = 1 + a_rho prod_m sin x_m, u_j = a_u cos x_{(j+1) mod dx},
      T = 1 + a_T cos(sum_m x_m),
-     f = rho (2 pi T)^{-dv/2} exp(-sum_j (v_j - u_j)^2 / (2 T)). */
+     f = rho (2 pi T)^{-dv/2} exp(-sum_j (v_j - u_j)^2 / (2 T)).
+     TTC_GEN_MAXWELLIAN_XV (Sec. 5.2): dx = dv = D spatial dimensions, d = 2D,
+     mode 2q the position s_q = -1/2 + i / (n - 1) on [-1/2, 1/2], mode 2q+1
+     the velocity v_q = vmin + (vmax - vmin) i / (n - 1) (both grids include
+     their end points); rho(s) = 1 + a_rho sin(2 pi s),
+     T(s) = 1/2 + a_T sin(2 pi s) (need |a_T| < 1/2), shift a_u:
+     f = sum_q rho(s_q) / (2 sqrt(2 pi T(s_q)))
+         * (exp(-sum_q (v_q - a_u)^2 / (2 T(s_q))) + exp(-sum_q (v_q + a_u)^2 / (2 T(s_q)))).
+     The paper's values: a_rho = 0.875, a_T = 0.4, a_u = 0.75, v on [-3, 3]. */
   int32_t dx, dv;
   double a_rho, a_u, a_T, vmin, vmax;
 } ttc_generator;

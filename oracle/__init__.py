@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "libttc_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-GEN_HILBERT, GEN_TT, GEN_MAXWELLIAN = 0, 1, 2
+GEN_HILBERT, GEN_TT, GEN_MAXWELLIAN, GEN_MAXWELLIAN_XV = 0, 1, 2, 3
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_ZERO_START, ERR_NONFINITE, NOT_CONVERGED = 0, 1, 2, 3, 4, 7
 
 
@@ -139,8 +139,8 @@ class Oracle:
             self._keep += [ranks, cores]
             g.tt_ranks = _p(ranks, C.c_int32)
             g.tt_cores = _p(cores, C.c_double)
-        elif kind == "maxwellian":
-            g.kind = GEN_MAXWELLIAN
+        elif kind in ("maxwellian", "maxwellian_xv"):
+            g.kind = GEN_MAXWELLIAN if kind == "maxwellian" else GEN_MAXWELLIAN_XV
             g.dx, g.dv = int(gen["dx"]), int(gen["dv"])
             g.a_rho, g.a_u, g.a_T = float(gen["a_rho"]), float(gen["a_u"]), float(gen["a_T"])
             g.vmin, g.vmax = float(gen["vmin"]), float(gen["vmax"])

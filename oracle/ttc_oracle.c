@@ -125,10 +125,34 @@ static double maxwellian(const orc_state *s, const int32_t *idx) {
   return rho / pow(two_pi * T, 0.5 * (double)s->dv) * exp(-q / (2.0 * T));
 }
 
+/* The 2d2v / 3d3v distribution of Sec. 5.2 (eq. 2d2vFunction and its 3d3v
+   extension), modes interleaved (x, v_x, y, v_y[, z, v_z]):
+     f = sum_q rho(s_q) / (2 sqrt(2 pi T(s_q)))
+         * [exp(-sum_q b_q^-) + exp(-sum_q b_q^+)],  b_q^± = (v_q ± a_u)^2 / (2 T(s_q)),
+   rho(s) = 1 + a_rho sin(2 pi s), T(s) = 1/2 + a_T sin(2 pi s), positions
+   s = -1/2 + i / (n - 1), velocities v = vmin + (vmax - vmin) i / (n - 1). */
+static double maxwellian_xv(const orc_state *s, const int32_t *idx) {
+  const double two_pi = 6.283185307179586476925286766559;
+  double rs = 0.0, bm = 0.0, bp = 0.0;
+  for (int q = 0; q < s->dx; ++q) {
+    double sv = -0.5 + (double)idx[2 * q] / (double)(s->n[2 * q] - 1);
+    double sn = sin(two_pi * sv);
+    double rho = 1.0 + s->a_rho * sn;
+    double T = 0.5 + s->a_T * sn;
+    double v = s->vmin + (s->vmax - s->vmin) * (double)idx[2 * q + 1] / (double)(s->n[2 * q + 1] - 1);
+    double dm = v - s->a_u, dp = v + s->a_u;
+    rs = rs + rho / (2.0 * sqrt(two_pi * T));
+    bm = bm + (dm * dm) * (1.0 / (2.0 * T));
+    bp = bp + (dp * dp) * (1.0 / (2.0 * T));
+  }
+  return rs * (exp(-bm) + exp(-bp));
+}
+
 double orc_entry(const orc_state *s, const int32_t *idx) {
   switch (s->kind) {
     case ORC_GEN_HILBERT: return hilbert(s, idx);
     case ORC_GEN_TT: return tt_entry(s, idx);
+    case ORC_GEN_MAXWELLIAN_XV: return maxwellian_xv(s, idx);
     default: return maxwellian(s, idx);
   }
 }
@@ -198,6 +222,12 @@ orc_state *orc_create(int d, const int64_t *n, const orc_gen *g,
     s->a_rho = g->a_rho; s->a_u = g->a_u; s->a_T = g->a_T;
     s->vmin = g->vmin; s->vmax = g->vmax;
     if (s->dx < 1 || s->dv < 1 || s->dx + s->dv != d) { free(s); return NULL; }
+  } else if (g->kind == ORC_GEN_MAXWELLIAN_XV) {
+    s->dx = g->dx; s->dv = g->dv;
+    s->a_rho = g->a_rho; s->a_u = g->a_u; s->a_T = g->a_T;
+    s->vmin = g->vmin; s->vmax = g->vmax;
+    if (s->dx < 1 || s->dv != s->dx || 2 * s->dx != d) { free(s); return NULL; }
+    for (int m = 0; m < d; ++m) if (n[m] < 2) { free(s); return NULL; }
   } else if (g->kind != ORC_GEN_HILBERT) {
     free(s);
     return NULL;

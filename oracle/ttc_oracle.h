@@ -43,7 +43,7 @@ extern "C" {
 
 #define ORC_MAXD 16
 
-enum { ORC_GEN_HILBERT = 0, ORC_GEN_TT = 1, ORC_GEN_MAXWELLIAN = 2 };
+enum { ORC_GEN_HILBERT = 0, ORC_GEN_TT = 1, ORC_GEN_MAXWELLIAN = 2, ORC_GEN_MAXWELLIAN_XV = 3 };
 
 enum {
   ORC_OK = 0,
@@ -63,7 +63,10 @@ typedef struct {
   /* ORC_GEN_MAXWELLIAN: modes (x_0..x_{dx-1}, v_0..v_{dv-1}); x_m = 2*pi*i/n_m,
      v = vmin + (vmax-vmin)*i/(n-1).  rho = 1 + a_rho*prod sin x,
      u_j = a_u*cos x_{(j+1) mod dx}, T = 1 + a_T*cos(sum x),
-     f = rho/(2*pi*T)^{dv/2} * exp(-|v-u|^2/(2T)). */
+     f = rho/(2*pi*T)^{dv/2} * exp(-|v-u|^2/(2T)).
+     ORC_GEN_MAXWELLIAN_XV: the 2d2v / 3d3v distribution of Sec. 5.2 with
+     dx = dv = d/2 and interleaved modes, amplitudes a_rho, a_T, shift a_u
+     (see maxwellian_xv in ttc_oracle.c). */
   int32_t dx, dv;
   double a_rho, a_u, a_T, vmin, vmax;
 } orc_gen;

@@ -311,6 +311,12 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
       return fail(TTC_ERR_INVALID_ARG, "Maxwellian needs dx, dv >= 1 and dx + dv = d");
     for (int m = gen->dx; m < d; ++m)
       if (n[m] < 2) return fail(TTC_ERR_INVALID_ARG, "velocity modes need n >= 2");
+  } else if (gen->kind == TTC_GEN_MAXWELLIAN_XV) {
+    if (gen->dx < 1 || gen->dv != gen->dx || 2 * gen->dx != d)
+      return fail(TTC_ERR_INVALID_ARG, "the interleaved Maxwellian needs dx = dv = d / 2");
+    for (int m = 0; m < d; ++m)
+      if (n[m] < 2) return fail(TTC_ERR_INVALID_ARG, "its modes need n >= 2");
+    if (!(std::fabs(gen->a_T) < 0.5)) return fail(TTC_ERR_INVALID_ARG, "need |a_T| < 1/2");
   } else {
     return fail(TTC_ERR_INVALID_ARG, "unknown generator kind %d", gen->kind);
   }
@@ -385,7 +391,7 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
   I.nsamples = ns;
   I.exhaustive = exhaustive ? 1 : 0;
   I.seed = o.seed;
-  if (gen->kind == TTC_GEN_MAXWELLIAN) {
+  if (gen->kind == TTC_GEN_MAXWELLIAN || gen->kind == TTC_GEN_MAXWELLIAN_XV) {
     I.dx = gen->dx; I.dv = gen->dv;
     I.a_rho = gen->a_rho; I.a_u = gen->a_u; I.a_T = gen->a_T;
     I.vmin = gen->vmin; I.vmax = gen->vmax;
@@ -412,6 +418,17 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
       return fail(TTC_ERR_INVALID_ARG, "Maxwellian x grid too large (%lld index combinations)",
                   (long long)ncombo);
   }
+  const bool xv = gen->kind == TTC_GEN_MAXWELLIAN_XV;
+  if (xv) {
+    // one table per mode: position modes rho / (2 sqrt(2 pi T)) and
+    // 1 / (2 T), velocity modes the grid values (and zeros)
+    ncombo = 0;
+    for (int m = 0; m < d; ++m) {
+      I.mx_off[m] = ncombo;
+      ncombo += n[m];
+    }
+  }
+  const bool mxtab = gen->kind == TTC_GEN_MAXWELLIAN || xv;
   int64_t core_cap = 0;
   for (int pass = 0; pass < 2; ++pass) {
     Carver cv;
@@ -421,8 +438,8 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     InstDev *dinst = cv.take<InstDev>(1);
     InstDev **dlist = cv.take<InstDev *>(1);
     double *hilb = cv.take<double>(hlen);
-    double *mxc = cv.take<double>(gen->kind == TTC_GEN_MAXWELLIAN ? ncombo : 1);
-    double *mxn = cv.take<double>(gen->kind == TTC_GEN_MAXWELLIAN ? ncombo : 1);
+    double *mxc = cv.take<double>(mxtab ? ncombo : 1);
+    double *mxn = cv.take<double>(mxtab ? ncombo : 1);
     double *mxcos = cv.take<double>(ncos);
     float *hilb_hi = cv.take<float>(hlen);
     float *hilb_lo = cv.take<float>(hlen);
@@ -596,7 +613,7 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     return cleanup(fail(TTC_ERR_CUDA, "copy of the instance list failed"));
   ttc_status s = ensure_cands(h, nullptr);
   if (s != TTC_OK) return cleanup(s);
-  if (gen->kind == TTC_GEN_MAXWELLIAN) {
+  if (mxtab) {
     if (launch_maxwellian_tables(h->d_inst, const_cast<double *>(I.mx_coef),
                                  const_cast<double *>(I.mx_nh),
                                  const_cast<double *>(I.mx_cos)) != cudaSuccess ||

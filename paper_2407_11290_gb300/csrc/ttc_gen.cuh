@@ -70,6 +70,42 @@ __device__ __forceinline__ double gen_maxwellian_tab(const InstDev &in, const in
   return __dmul_rn(in.mx_coef[combo], exp(__dmul_rn(q, in.mx_nh[combo])));
 }
 
+// The interleaved 2d2v / 3d3v distribution of Sec. 5.2 (eq. 2d2vFunction)
+// from the create-time tables: per position mode rho / (2 sqrt(2 pi T)) and
+// 1 / (2 T), per velocity mode the grid value; two exps per entry.
+__device__ __forceinline__ double gen_maxwellian_xv(const InstDev &in, const int32_t *idx) {
+  double rs = 0.0, bm = 0.0, bp = 0.0;
+  for (int q = 0; q < in.dx; ++q) {
+    const int64_t ox = in.mx_off[2 * q] + idx[2 * q];
+    const double c = in.mx_coef[ox], h = in.mx_nh[ox];
+    const double v = in.mx_coef[in.mx_off[2 * q + 1] + idx[2 * q + 1]];
+    const double dm = __dsub_rn(v, in.a_u), dp = __dadd_rn(v, in.a_u);
+    rs = __dadd_rn(rs, c);
+    bm = __dadd_rn(bm, __dmul_rn(__dmul_rn(dm, dm), h));
+    bp = __dadd_rn(bp, __dmul_rn(__dmul_rn(dp, dp), h));
+  }
+  return __dmul_rn(rs, __dadd_rn(exp(-bm), exp(-bp)));
+}
+
+// table entry k of mode m of the interleaved distribution
+__device__ void maxwellian_xv_table_entry(const InstDev &in, int m, int64_t i, double *a,
+                                          double *b) {
+  const double two_pi = 6.283185307179586476925286766559;
+  const double t = (double)i / (double)(in.n[m] - 1);
+  if ((m & 1) == 0) {
+    const double sv = __dadd_rn(-0.5, t);
+    const double sn = sin(__dmul_rn(two_pi, sv));
+    const double rho = __dadd_rn(1.0, __dmul_rn(in.a_rho, sn));
+    const double T = __dadd_rn(0.5, __dmul_rn(in.a_T, sn));
+    *a = rho / __dmul_rn(2.0, sqrt(__dmul_rn(two_pi, T)));
+    *b = 1.0 / __dmul_rn(2.0, T);
+  } else {
+    *a = __dadd_rn(in.vmin, __dmul_rn(__dsub_rn(in.vmax, in.vmin), (double)i) /
+                                (double)(in.n[m] - 1));
+    *b = 0.0;
+  }
+}
+
 // one entry of the tables: x-index combination `combo` (column-major)
 __device__ void maxwellian_table_entry(const InstDev &in, int64_t combo, double *coef,
                                        double *nh) {
@@ -93,6 +129,7 @@ __device__ void maxwellian_table_entry(const InstDev &in, int64_t combo, double 
 // callers are many)
 __device__ __noinline__ double gen_other(const InstDev &in, const int32_t *idx) {
   if (in.gen == 1) return gen_tt(in, idx);
+  if (in.gen == 3) return gen_maxwellian_xv(in, idx);
   return gen_maxwellian_tab(in, idx);
 }
 

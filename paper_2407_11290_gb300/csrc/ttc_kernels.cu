@@ -2269,11 +2269,13 @@ __device__ void phase_rook_decide(const RunArgs &ra, PhaseSmem &sm) {
       const int st = ld_cg(cr.rook_stage[b]);
       const uint64_t cur = ld_cg(cr.best_key[b]);
       int moved = ld_cg(cr.rook_moved[b]);
+      // ranks written by other CTAs' items: read through L2, not this SM's L1
       const int32_t r_old = ld_cg(cr.r[b]);
-      const int32_t rows = (int32_t)rows_of(in, cr.r, b), cols = (int32_t)cols_of(in, cr.r, b);
+      const int64_t rows = (b == 0 ? 1 : ld_cg(cr.r[b - 1])) * in.n[b];
+      const int64_t cols = in.n[b + 1] * (b == in.nb - 1 ? 1 : ld_cg(cr.r[b + 1]));
       cr.entries += st == 1 ? rows : cols;
       cr.entries_fresh += st == 1 ? rows : cols;
-      cr.screen_fmas += (int64_t)(st == 1 ? rows : cols) * r_old;
+      cr.screen_fmas += (st == 1 ? rows : cols) * r_old;
       if (line.row >= 0 && line.key > cur) {
         cr.best_key[b] = line.key;
         cr.best_lin[b] = line.lin;
@@ -3490,6 +3492,12 @@ __global__ void k_maxwellian_tables(const InstDev *inp, double *coef, double *nh
   const InstDev &in = *inp;
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t NTOT = (int64_t)gridDim.x * blockDim.x;
+  if (in.gen == 3) {
+    for (int m = 0; m < in.d; ++m)
+      for (int64_t i = gt; i < in.n[m]; i += NTOT)
+        maxwellian_xv_table_entry(in, m, i, coef + in.mx_off[m] + i, nh + in.mx_off[m] + i);
+    return;
+  }
   int64_t ncombo = 1;
   for (int m = 0; m < in.dx; ++m) ncombo *= in.n[m];
   for (int64_t c = gt; c < ncombo; c += NTOT) maxwellian_table_entry(in, c, coef + c, nh + c);

@@ -20,7 +20,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_ZERO_START, ERR_NONFINITE, ERR_DEVICE_TIMEOUT,
     NOT_CONVERGED = range(8)
 STATUS_NAMES = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_OOM", 3: "ERR_ZERO_START",
                 4: "ERR_NONFINITE", 5: "ERR_DEVICE_TIMEOUT", 6: "ERR_CUDA", 7: "NOT_CONVERGED"}
-GEN_HILBERT, GEN_TT, GEN_MAXWELLIAN = 0, 1, 2
+GEN_HILBERT, GEN_TT, GEN_MAXWELLIAN, GEN_MAXWELLIAN_XV = 0, 1, 2, 3
 PREC_FP64, PREC_FP32, PREC_SPLIT, PREC_AUTO = 0, 1, 2, 3
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "split": PREC_SPLIT, "auto": PREC_AUTO}
 RESIDUAL_RECOMPUTE, RESIDUAL_STORED = 0, 1
@@ -193,8 +193,8 @@ class TTCross:
             keep += [ranks, cores]
             g.tt_ranks = ranks.ctypes.data_as(C.POINTER(C.c_int32))
             g.tt_cores = cores.ctypes.data_as(C.POINTER(C.c_double))
-        elif kind == "maxwellian":
-            g.kind = GEN_MAXWELLIAN
+        elif kind in ("maxwellian", "maxwellian_xv"):
+            g.kind = GEN_MAXWELLIAN if kind == "maxwellian" else GEN_MAXWELLIAN_XV
             g.dx, g.dv = int(gen["dx"]), int(gen["dv"])
             g.a_rho, g.a_u, g.a_T = float(gen["a_rho"]), float(gen["a_u"]), float(gen["a_T"])
             g.vmin, g.vmax = float(gen["vmin"]), float(gen["vmax"])
@@ -297,8 +297,8 @@ def make_generator(gen):
     g = Generator()
     if gen["kind"] == "hilbert":
         g.kind = GEN_HILBERT
-    elif gen["kind"] == "maxwellian":
-        g.kind = GEN_MAXWELLIAN
+    elif gen["kind"] in ("maxwellian", "maxwellian_xv"):
+        g.kind = GEN_MAXWELLIAN if gen["kind"] == "maxwellian" else GEN_MAXWELLIAN_XV
         g.dx, g.dv = int(gen["dx"]), int(gen["dv"])
         g.a_rho, g.a_u, g.a_T = float(gen["a_rho"]), float(gen["a_u"]), float(gen["a_T"])
         g.vmin, g.vmax = float(gen["vmin"]), float(gen["vmax"])

@@ -12,6 +12,12 @@ Workloads:
     v in [vmin, vmax]^dv (endpoints included), modes ordered (x..., v...),
     rho = 1 + a_rho prod sin x, u_j = a_u cos x_{(j+1) mod dx},
     T = 1 + a_T cos(sum x).
+  * ``maxwellian_xv``: the 2d2v / 3d3v distributions of Sec. 5.2,
+    f = sum_q rho(s_q) / (2 sqrt(2 pi T(s_q)))
+        * (exp(-sum_q (v_q - 0.75)^2 / (2 T(s_q))) + exp(-sum_q (v_q + 0.75)^2 / (2 T(s_q)))),
+    rho = 1 + 0.875 sin(2 pi s), T = 0.5 + 0.4 sin(2 pi s), positions on
+    [-1/2, 1/2], velocities on [-3, 3] (end points included), modes
+    interleaved (x, v_x, y, v_y[, z, v_z]).
   * ``tt``: a tensor given by TT cores with Gaussian entries (known ranks).
 """
 from __future__ import annotations
@@ -44,6 +50,16 @@ def maxwellian(dx: int, dv: int, n, a_rho=0.5, a_u=0.3, a_T=0.2, vmin=-8.0, vmax
     return dict(n=ns, gen={"kind": "maxwellian", "dx": dx, "dv": dv, "a_rho": float(a_rho),
                            "a_u": float(a_u), "a_T": float(a_T), "vmin": float(vmin),
                            "vmax": float(vmax)})
+
+
+def maxwellian_xv(D: int, n_pos: int, n_vel: int, a_rho=0.875, a_T=0.4, a_u=0.75, vmin=-3.0,
+                  vmax=3.0):
+    """The 2d2v (D = 2) / 3d3v (D = 3) distribution of Sec. 5.2 with modes
+    interleaved (x, v_x, y, v_y[, z, v_z]) and sizes (n_pos, n_vel, ...)."""
+    return dict(n=[int(n_pos), int(n_vel)] * D,
+                gen={"kind": "maxwellian_xv", "dx": D, "dv": D, "a_rho": float(a_rho),
+                     "a_u": float(a_u), "a_T": float(a_T), "vmin": float(vmin),
+                     "vmax": float(vmax)})
 
 
 def random_tt(n, ranks, seed: int = 1, positive_first: bool = True):
@@ -79,6 +95,22 @@ CONFIGS = {
                              grid=[4, 4, 4, 1, 1, 1], nsamples=10**6, precision="fp32"),
     "hilbert6d_n256": dict(**hilbert(6, 256), eps=1e-10, max_rank=128, grid=[4] * 6,
                            nsamples=10**6, precision="split"),
+}
+
+
+# The paper's own workloads (Sec. 5.1 and 5.2, Table 4), prescribed ranks
+# (eps = 0: every bond grows to its rank), the subtensor grids of its 64-rank
+# strong-scaling partitions (Tables 2 and 3).
+PAPER_WORKLOADS = {
+    "paper_hilbert3d_n2000": dict(**hilbert(3, 2000), eps=0.0, bond_ranks=[25, 25],
+                                  grid=[4, 4, 4], nsamples=10**6, paper_pivot_s=99.99),
+    "paper_hilbert6d_n300": dict(**hilbert(6, 300), eps=0.0, bond_ranks=[15, 17, 18, 17, 15],
+                                 grid=[1, 2, 4, 4, 2, 1], nsamples=10**6, paper_pivot_s=260.72),
+    "paper_2d2v_n1000": dict(**maxwellian_xv(2, 2000, 1000), eps=0.0, bond_ranks=[10, 5, 20],
+                             grid=[1, 8, 8, 1], nsamples=10**6, paper_pivot_s=147.34),
+    "paper_3d3v_n400": dict(**maxwellian_xv(3, 800, 400), eps=0.0,
+                            bond_ranks=[10, 5, 30, 5, 20], grid=[1, 2, 4, 4, 2, 1],
+                            nsamples=10**6, paper_pivot_s=184.16),
 }
 
 

@@ -283,3 +283,46 @@ def test_mixed_stored_batch_equals_single(tt):
         assert list(a.ranks()) == list(b.ranks())
         for k in range(1, len(a.n) + 1):
             np.testing.assert_array_equal(a.core(k), b.core(k))
+
+
+# ---------------------------------------------------------------------------
+# the paper's own workloads (Sec. 5.1, 5.2), prescribed ranks
+
+@pytest.mark.parametrize("name", ["paper_hilbert3d_n2000", "paper_hilbert6d_n300"])
+def test_paper_hilbert_prescribed_ranks_equal_oracle(tt, name):
+    w = W.PAPER_WORKLOADS[name]
+    caps = w["bond_ranks"]
+    g = tt.TTCross(w["n"], w["gen"], max_rank=max(caps), nsamples=w["nsamples"],
+                   bond_max_rank=caps, residual="stored")
+    g.run(0.0, subtensor_grid=w["grid"])
+    assert g.sync() == tt.OK
+    assert list(g.ranks()[1:-1]) == caps
+    o = oracle.Oracle(w["n"], w["gen"], caps, nthreads=NT, stored=True)
+    orc, ost = o.run(0.0, nsamples=w["nsamples"])
+    assert orc == 0
+    assert_same(g, o)
+    st = g.stats()
+    assert abs(st["err"] - ost["err"]) <= 1e-12
+    print(f"{name}: {st['device_ms']:.2f} ms on the GPU (paper, 64 CPU ranks: "
+          f"{w['paper_pivot_s']} s pivot selection), err {st['err']:.3e}")
+
+
+@pytest.mark.parametrize("name,shrink", [("paper_2d2v_n1000", 4), ("paper_3d3v_n400", 4)])
+def test_paper_maxwellian_xv_prescribed_ranks_resync(tt, name, shrink):
+    """The 2d2v / 3d3v distributions at a quarter of the paper's mode sizes,
+    the paper's ranks: pivots equal the oracle's up to logged near-ties
+    (CUDA's and glibc's sin / exp differ in the last bit)."""
+    w = dict(W.PAPER_WORKLOADS[name])
+    w["n"] = [v // shrink for v in w["n"]]
+    caps = w["bond_ranks"]
+    g = tt.TTCross(w["n"], w["gen"], max_rank=max(caps), nsamples=10**5, bond_max_rank=caps,
+                   residual="stored")
+    g.run(0.0, subtensor_grid=w["grid"])
+    assert g.sync() == tt.OK
+    assert list(g.ranks()[1:-1]) == caps
+    o, ties = replay_with_resync(g, w, 0.0, caps, 10**5, rel=1e-12, stored=True)
+    for k in range(1, o.d):
+        for a, b in zip(g.pivots(k), o.pivots(k - 1)):
+            np.testing.assert_array_equal(a, b)
+    assert abs(g.stats()["err"] - o.sampled_error(10**5)) <= 1e-12
+    print(f"{name} / {shrink}: {ties} near-tie(s), err {g.stats()['err']:.3e}")

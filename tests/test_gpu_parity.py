@@ -169,6 +169,7 @@ def replay_with_resync(g, w, eps, cap, nsamples, rel=1e-13, stored=False, max_re
     that stage are then a prefix of its lists).
     Returns (oracle, number of re-synced pivots)."""
     o = oracle.Oracle(w["n"], w["gen"], cap, nthreads=NT, stored=stored)
+    caps = list(np.broadcast_to(np.asarray(cap), (o.d - 1,)))
     rms, start = o.sample_scan(nsamples)
     gI = [g.pivots(k) for k in range(1, o.d)]
     np.testing.assert_array_equal(np.concatenate([gI[0][0][0], gI[0][1][0]]), start)
@@ -182,12 +183,12 @@ def replay_with_resync(g, w, eps, cap, nsamples, rel=1e-13, stored=False, max_re
         assert rc == 0
         r = o.ranks()
         theta = tau * rms
-        add = [int(sc["best"][b] > theta and sc["best"][b] > 0 and r[b] < cap)
+        add = [int(sc["best"][b] > theta and sc["best"][b] > 0 and r[b] < caps[b])
                for b in range(o.d - 1)]
         if not any(add):
             if first_stage or eps == 0.0 or o.sampled_error(nsamples) <= eps:
                 break
-            if all(r[b] >= cap for b in range(o.d - 1)) or refinements >= max_refine:
+            if all(r[b] >= caps[b] for b in range(o.d - 1)) or refinements >= max_refine:
                 break
             tau /= 10.0
             refinements += 1

@@ -367,3 +367,40 @@ def test_maxwellian_moments():
         assert abs(m0 - rho) < 1e-10
         assert abs(m1[0] - u[0]) < 1e-10 and abs(m1[1] - u[1]) < 1e-10
         assert abs(m2 - T) < 1e-9
+
+
+def test_maxwellian_xv_velocity_moments():
+    """The 2d2v distribution of Sec. 5.2 on a wide v-grid: for fixed
+    positions (x, y) the quadrature over (v_x, v_y) of f, of v_x^2 f and of
+    v_y^2 f returns what a sum of two Gaussians centred at -(0.75, 0.75) and
+    +(0.75, 0.75) with variances (T(x), T(y)) and weight
+    varrho(x, y) = rho(x) / (2 sqrt(2 pi T(x))) + rho(y) / (2 sqrt(2 pi T(y)))
+    integrates to: 2 varrho 2 pi sqrt(T(x) T(y)) times 1, T(x) + 0.75^2 and
+    T(y) + 0.75^2; the first moments vanish.  At s = 0 the paper's rho and T
+    are 1 and 1/2, at s = 1/4 they are 1.875 and 0.9 (sin = 1)."""
+    nv = 97
+    w = W.maxwellian_xv(2, 5, nv, vmin=-12.0, vmax=12.0)
+    o = oracle.Oracle(w["n"], w["gen"], 2)
+    v = -12.0 + 24.0 * np.arange(nv) / (nv - 1)
+    h = 24.0 / (nv - 1)
+    s_of = lambda i: -0.5 + i / 4  # noqa: E731  positions -1/2, -1/4, 0, 1/4, 1/2
+    for ix, iy in [(2, 2), (3, 2), (2, 3), (1, 3), (0, 4)]:
+        F = np.array([[o.entry((ix, a, iy, b)) for b in range(nv)] for a in range(nv)])
+        rx, tx = 1 + 0.875 * np.sin(2 * np.pi * s_of(ix)), 0.5 + 0.4 * np.sin(2 * np.pi * s_of(ix))
+        ry, ty = 1 + 0.875 * np.sin(2 * np.pi * s_of(iy)), 0.5 + 0.4 * np.sin(2 * np.pi * s_of(iy))
+        if ix == 3:
+            assert abs(rx - 1.875) < 1e-15 and abs(tx - 0.9) < 1e-15
+        if ix == 2:
+            assert abs(rx - 1.0) < 1e-15 and abs(tx - 0.5) < 1e-15
+        rho = rx / (2 * np.sqrt(2 * np.pi * tx)) + ry / (2 * np.sqrt(2 * np.pi * ty))
+        mass = 2 * rho * 2 * np.pi * np.sqrt(tx * ty)
+        m0 = F.sum() * h * h
+        assert abs(m0 - mass) < 1e-9 * mass
+        assert abs((F * v[:, None]).sum() * h * h) < 1e-9 * mass
+        assert abs((F * v[None, :]).sum() * h * h) < 1e-9 * mass
+        assert abs((F * v[:, None] ** 2).sum() * h * h / m0 - (tx + 0.75 ** 2)) < 1e-9
+        assert abs((F * v[None, :] ** 2).sum() * h * h / m0 - (ty + 0.75 ** 2)) < 1e-9
+    # interleaved order: swapping the (x, v_x) and (y, v_y) pairs of modes
+    # leaves the function unchanged
+    for idx in [(0, 3, 4, 50), (1, 96, 2, 7), (3, 40, 3, 41)]:
+        assert o.entry(idx) == o.entry((idx[2], idx[3], idx[0], idx[1]))
