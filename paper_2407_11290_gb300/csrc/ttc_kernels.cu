@@ -2273,9 +2273,11 @@ __device__ void phase_rook_decide(const RunArgs &ra, PhaseSmem &sm) {
       const int32_t r_old = ld_cg(cr.r[b]);
       const int64_t rows = (b == 0 ? 1 : ld_cg(cr.r[b - 1])) * in.n[b];
       const int64_t cols = in.n[b + 1] * (b == in.nb - 1 ? 1 : ld_cg(cr.r[b + 1]));
-      cr.entries += st == 1 ? rows : cols;
-      cr.entries_fresh += st == 1 ? rows : cols;
-      cr.screen_fmas += (st == 1 ? rows : cols) * r_old;
+      // several CTAs decide bonds of one instance at once: atomic counts
+      const unsigned long long cnt = (unsigned long long)(st == 1 ? rows : cols);
+      atomicAdd((unsigned long long *)&cr.entries, cnt);
+      atomicAdd((unsigned long long *)&cr.entries_fresh, cnt);
+      atomicAdd((unsigned long long *)&cr.screen_fmas, cnt * (unsigned long long)r_old);
       if (line.row >= 0 && line.key > cur) {
         cr.best_key[b] = line.key;
         cr.best_lin[b] = line.lin;
