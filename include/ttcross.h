@@ -63,10 +63,24 @@ typedef enum {
   TTC_GEN_HILBERT = 0,    /* X(i) = 1/(1 + i_1 + ... + i_d) (eq. HilbertTensor, 0-based) */
   TTC_GEN_TT = 1,         /* X given by TT cores (tests; exact recovery) */
   TTC_GEN_MAXWELLIAN = 2, /* f(x,v), see ttc_generator */
-  TTC_GEN_MAXWELLIAN_XV = 3 /* the 2d2v / 3d3v distributions of Sec. 5.2
+  TTC_GEN_MAXWELLIAN_XV = 3, /* the 2d2v / 3d3v distributions of Sec. 5.2
                                (eq. 2d2vFunction), modes interleaved
                                (x, v_x, y, v_y[, z, v_z]), see ttc_generator */
+  TTC_GEN_USER = 4         /* entries from the caller's batch callback (Sec. 5
+                               intro: the tensor is a function of its indices) */
 } ttc_gen_kind;
+
+/* Batch entry callback of TTC_GEN_USER.  It must set values[i] = X(i_1..i_d)
+   with the multi-index idx[i*d + m] (0-based), for 0 <= i < count.  idx
+   (int32, [count][d] row-major) and values (double, [count]) are device
+   buffers owned by the library and valid until the callback's work on
+   `stream` has run; `stream` is the run's stream (a cudaStream_t as void*).
+   The callback enqueues its work on that stream (or finishes it before it
+   returns); the library reads the values in stream order after it.  It is
+   called on the host thread that called ttcross_run, between the run's
+   kernels, never from device code.  user is the pointer of ttc_generator. */
+typedef void (*ttc_user_fn)(const int32_t *idx, int64_t count, double *values, void *user,
+                            void *stream);
 
 /* Entry generator.  All pointers are host pointers, read during
    ttcross_create only (the data is copied to the device). */
@@ -94,6 +108,16 @@ typedef struct {
      The paper's values: a_rho = 0.875, a_T = 0.4, a_u = 0.75, v on [-3, 3]. */
   int32_t dx, dv;
   double a_rho, a_u, a_T, vmin, vmax;
+  /* TTC_GEN_USER: the callback and its pointer.  The entries are evaluated
+     unfused: after every decision the library gathers the multi-indices of
+     the entries that enter a superblock (and, at the start, of the error
+     samples) into a device buffer, calls fn once for them, and scatters the
+     values into a device cache of the superblocks (8 bytes per superblock
+     entry at the rank caps, as the stored residual).  Such instances always
+     run host-stepped (the phases as separate launches) and cannot be batched
+     with run_batch. */
+  ttc_user_fn user_fn;
+  void *user;
 } ttc_generator;
 
 typedef enum {

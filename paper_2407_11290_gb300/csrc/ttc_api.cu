@@ -82,6 +82,15 @@ struct ttc_handle {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool ran = false;
   bool events_ok = false;
+  // user generator: the callback, the superblock entry cache, the staging
+  // buffers of the multi-indices and values handed to the callback
+  ttc_user_fn user_fn = nullptr;
+  void *user = nullptr;
+  void *acache = nullptr;
+  int32_t *ustage_idx = nullptr;
+  double *ustage_val = nullptr;
+  int64_t ustage_cap = 0;
+  int64_t *ucounts = nullptr;   // device [TTC_MAXD + 1]
   bool synced = false;          // h_ctrl holds the finished last run
   ttc_status sync_status = TTC_OK;
   std::string sync_msg;
@@ -171,6 +180,52 @@ Ctrl make_ctrl(const ttc_handle *h, double eps, int max_rank, const int32_t *gri
   return c;
 }
 
+// user generator: room for cnt multi-indices and values in the staging buffers
+ttc_status user_stage(ttc_handle *h, int64_t cnt, cudaStream_t s) {
+  if (cnt <= h->ustage_cap) return TTC_OK;
+  CU(cudaStreamSynchronize(s));
+  const int64_t cap = std::max<int64_t>(cnt, 2 * h->ustage_cap);
+  cudaFree(h->ustage_idx);
+  cudaFree(h->ustage_val);
+  h->ustage_idx = nullptr;
+  h->ustage_val = nullptr;
+  h->ustage_cap = 0;
+  CU(cudaMalloc(&h->ustage_idx, sizeof(int32_t) * h->d * cap));
+  CU(cudaMalloc(&h->ustage_val, sizeof(double) * cap));
+  h->ustage_cap = cap;
+  return TTC_OK;
+}
+
+// user generator: the entries that entered the superblocks in the last
+// decision (first: every entry of the rank-one superblocks) through the
+// callback into the cache, in stream order
+ttc_status user_fill(ttc_handle *h, int first, cudaStream_t s) {
+  CU(launch_user_count(h->d_inst, first, h->ucounts, s));
+  int64_t tot = 0;
+  CU(cudaMemcpyAsync(&tot, h->ucounts + h->nb, sizeof tot, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (tot == 0) return TTC_OK;
+  ttc_status st = user_stage(h, tot, s);
+  if (st) return st;
+  CU(launch_user_gather(h->d_inst, first, h->ucounts, h->ustage_idx, s));
+  h->user_fn(h->ustage_idx, tot, h->ustage_val, h->user, s);
+  CU(cudaGetLastError());
+  CU(launch_user_scatter(h->d_inst, first, h->ucounts, h->ustage_val, s));
+  return TTC_OK;
+}
+
+// user generator: X at the error samples and at the origin into xs
+ttc_status user_samples(ttc_handle *h, cudaStream_t s) {
+  const int64_t cnt = h->hi.nsamples + 1;
+  ttc_status st = user_stage(h, cnt, s);
+  if (st) return st;
+  CU(launch_user_samples(h->d_inst, h->ustage_idx, s));
+  h->user_fn(h->ustage_idx, cnt, h->ustage_val, h->user, s);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(h->hi.xs, h->ustage_val, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s));
+  return TTC_OK;
+}
+
 ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, cudaStream_t s) {
   ttc_handle *h0 = hs[0];
   RunArgs ra;
@@ -179,7 +234,8 @@ ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, 
   ra.bar = h0->d_bar;
   ra.smid = h0->d_smid;
   ra.wait_ns = (int64_t)(h0->opt.wait_limit_s * 1e9);
-  ra.persistent = h0->opt.host_loop ? 0 : 1;
+  const bool user = count == 1 && h0->user_fn;  // host-stepped with the callback
+  ra.persistent = (h0->opt.host_loop || user) ? 0 : 1;
   ra.mixed = 0;
   ra.sampled = 0;
   ra.max_rook = 0;
@@ -198,13 +254,16 @@ ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, 
   }
   ra.max_iters = (int32_t)iters;
   CU(cudaMemsetAsync(h0->d_bar, 0, sizeof(Barrier), s));
-  if (!h0->opt.host_loop) {
+  if (ra.persistent) {
     CU(launch_persistent(ra, h0->grid, s));
     return TTC_OK;
   }
   // host-stepped: the same phases as separate launches, state read per sweep
+  ttc_status us;
+  if (user && (us = user_samples(h0, s))) return us;
   CU(launch_phase(PH_INIT1, ra, h0->grid, s));
   CU(launch_phase(PH_INIT2, ra, h0->grid, s));
+  if (user && (us = user_fill(h0, 1, s))) return us;
   CU(launch_phase(PH_INIT3, ra, h0->grid, s));
   for (int64_t it = 0; it <= ra.max_iters; ++it) {
     bool done = true;
@@ -229,6 +288,7 @@ ttc_status launch_run(ttc_handle *const *hs, int count, InstDev *const *d_list, 
       CU(launch_phase(PH_REFINE, ra, h0->grid, s));
       CU(launch_phase(PH_DECIDE2, ra, h0->grid, s));
     }
+    if (user && (us = user_fill(h0, 0, s))) return us;
     CU(launch_phase(PH_TABLES, ra, h0->grid, s));
     CU(launch_phase(PH_UPDATE, ra, h0->grid, s));
   }
@@ -311,6 +371,12 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
       return fail(TTC_ERR_INVALID_ARG, "Maxwellian needs dx, dv >= 1 and dx + dv = d");
     for (int m = gen->dx; m < d; ++m)
       if (n[m] < 2) return fail(TTC_ERR_INVALID_ARG, "velocity modes need n >= 2");
+  } else if (gen->kind == TTC_GEN_USER) {
+    if (!gen->user_fn) return fail(TTC_ERR_INVALID_ARG, "user generator without a callback");
+    if (o.screen_samples > 0)
+      return fail(TTC_ERR_INVALID_ARG, "a sampled screen with the user generator is not supported");
+    if (o.precision != TTC_PREC_FP64 && o.residual != TTC_RESIDUAL_STORED)
+      return fail(TTC_ERR_INVALID_ARG, "the user generator's mixed precision needs the stored form");
   } else if (gen->kind == TTC_GEN_MAXWELLIAN_XV) {
     if (gen->dx < 1 || gen->dv != gen->dx || 2 * gen->dx != d)
       return fail(TTC_ERR_INVALID_ARG, "the interleaved Maxwellian needs dx = dv = d / 2");
@@ -444,10 +510,11 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     float *hilb_hi = cv.take<float>(hlen);
     float *hilb_lo = cv.take<float>(hlen);
     double *tt = cv.take<double>(tt_total);
-    double *xs = cv.take<double>(ns);
+    double *xs = cv.take<double>(ns + 1);  // + the origin (user generator)
     double *errp = cv.take<double>(GRID_CAP);
     Cand *spart = cv.take<Cand>(GRID_CAP);
     int32_t *smid = cv.take<int32_t>(GRID_CAP);
+    int64_t *ucnt = cv.take<int64_t>(TTC_MAXD + 1);
     int32_t *eidx = cv.take<int32_t>(TTC_MAXD);
     int64_t *elin = cv.take<int64_t>(1);
     int32_t *esum = cv.take<int32_t>(1);
@@ -520,6 +587,7 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
       h->d_ctrl = ctrl;
       h->d_bar = bar;
       h->d_smid = smid;
+      h->ucounts = ucnt;
       h->d_inst = dinst;
       h->d_list = dlist;
       I.hilb = hilb;
@@ -550,6 +618,7 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
     cudaFree(h->pool);
     if (h->cand) cudaFree(h->cand);
     if (h->estore) cudaFree(h->estore);
+    if (h->acache) cudaFree(h->acache);
     delete h;
     return s;
   };
@@ -584,6 +653,24 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
       }
     }
     I.stored = 1;
+  }
+  if (gen->kind == TTC_GEN_USER) {
+    // the entries of every superblock at the rank caps, as the stored residual
+    size_t bytes = 0;
+    for (int b = 0; b < d - 1; ++b)
+      bytes += ((size_t)(I.bond[b].ldT * I.bond[b].ldR) * 8 + 255) & ~size_t(255);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && bytes > fr)
+      return cleanup(fail(TTC_ERR_OOM, "the entry cache needs %zu bytes, %zu free", bytes, fr));
+    if (cudaMalloc(&h->acache, bytes) != cudaSuccess)
+      return cleanup(fail(TTC_ERR_OOM, "cudaMalloc(%zu) of the entry cache failed", bytes));
+    char *p = static_cast<char *>(h->acache);
+    for (int b = 0; b < d - 1; ++b) {
+      I.bond[b].A = reinterpret_cast<double *>(p);
+      p += ((size_t)(I.bond[b].ldT * I.bond[b].ldR) * 8 + 255) & ~size_t(255);
+    }
+    h->user_fn = gen->user_fn;
+    h->user = gen->user;
   }
   if (cudaMemset(h->pool, 0, h->pool_bytes) != cudaSuccess)
     return cleanup(fail(TTC_ERR_CUDA, "cudaMemset failed"));
@@ -680,6 +767,8 @@ ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps
       for (int m = 0; m < hs[i]->d; ++m)
         if (gi[m] < 1 || gi[m] > hs[i]->n[m])
           return fail(TTC_ERR_INVALID_ARG, "grids[%d][%d]=%d outside [1,n]", i, m, gi[m]);
+    if (hs[i]->user_fn && count >= 2)
+      return fail(TTC_ERR_INVALID_ARG, "instance %d: a user generator cannot be batched", i);
     // An FP32 / float-float recompute-form batch of non-Hilbert tensors ended
     // in an illegal address on the GPU twice; its cause is not found, so that
     // combination is refused here, before anything is launched.
@@ -862,6 +951,9 @@ ttc_status ttcross_destroy(ttc_handle *h) {
   }
   if (h->cand) cudaFree(h->cand);
   if (h->estore) cudaFree(h->estore);
+  if (h->acache) cudaFree(h->acache);
+  if (h->ustage_idx) cudaFree(h->ustage_idx);
+  if (h->ustage_val) cudaFree(h->ustage_val);
   if (h->pool) cudaFree(h->pool);
   delete h;
   return TTC_OK;

@@ -152,6 +152,7 @@ __device__ __noinline__ double sb_entry(const InstDev &in, int b, int64_t a, int
   if (a < 0 || c < 0 || (b > 0 && p >= in.bond[b - 1].cap) ||
       (b < in.nb - 1 && q >= in.bond[b + 1].cap))
     return __longlong_as_double(0x7FF8000000000000ll);
+  if (in.gen == 4) return in.bond[b].A[a * in.bond[b].ldR + c];  // the caller's values
   const SetDev &L = left_set(in, b);
   const SetDev &Rs = right_set(in, b);
   if (in.gen == 0) return in.hilb[L.sum[p] + (int)i + (int)j + Rs.sum[q]];

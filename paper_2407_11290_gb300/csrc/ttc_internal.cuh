@@ -46,6 +46,7 @@ struct BondDev {
   float *Thi, *Tlo, *Rhi, *Rlo;
   int32_t *prow, *pcol;  // pivot superblock coordinates, insertion order
   double *E, *ew, *erow; // stored-residual form (null otherwise)
+  double *A;             // user generator: the entries of the superblock [ldT][ldR]
   SetDev I, J;
   int64_t cand_base;     // first candidate slot of this bond
   int64_t cand_cap;      // candidate slots of this bond

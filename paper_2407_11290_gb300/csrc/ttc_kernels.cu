@@ -50,6 +50,8 @@ struct ScreenSmem {
   int64_t sl[NT / 32];
   int32_t sr[NT / 32], sc[NT / 32];
   float fred[NT / 32];
+  const double *acache;  // user generator: the tile's first entry in the cache
+  int64_t acache_ld;
 };
 
 constexpr int TOPK_MAX = 16;
@@ -436,6 +438,10 @@ __device__ void stage_meta(const InstDev &in, int b, int64_t r0, int nr, int64_t
   const int64_t nb0 = in.n[b], nb1 = in.n[b + 1];
   const bool hil = in.gen == 0;
   const int wl = b, wr = in.d - b - 2;
+  if (tid == 0 && in.gen == 4) {
+    sm.acache = in.bond[b].A + r0 * in.bond[b].ldR + c0;
+    sm.acache_ld = in.bond[b].ldR;
+  }
   for (int x = tid; x < BM; x += NT) {
     if (x < nr) {
       const uint32_t a = (uint32_t)(r0 + x), p = a / (uint32_t)nb0, i = a - p * (uint32_t)nb0;
@@ -465,6 +471,7 @@ __device__ void stage_meta(const InstDev &in, int b, int64_t r0, int nr, int64_t
 __device__ __noinline__ double tile_entry(const InstDev &in, const ScreenSmem &sm, int wl, int wr,
                                              int rr, int cc) {
   if (in.gen == 0) return in.hilb[sm.srow[rr] + sm.scol[cc]];
+  if (in.gen == 4) return sm.acache[rr * sm.acache_ld + cc];
   int32_t idx[TTC_MAXD];
   for (int m = 0; m <= wl; ++m) idx[m] = sm.ridx[rr][m];
   for (int m = 0; m <= wr; ++m) idx[wl + 1 + m] = sm.cidx[cc][m];
@@ -3030,7 +3037,8 @@ __device__ void phase_init1(const RunArgs &ra, PhaseSmem &sm) {
     for (int64_t x = first_item(base, gt, NTOT); x < base + ns; x += NTOT) {
       int32_t idx[TTC_MAXD];
       sample_index(in, x - base, idx);
-      const double v = gen_full(in, idx);
+      // user generator: the samples' values were filled by the callback
+      const double v = in.gen == 4 ? in.xs[x - base] : gen_full(in, idx);
       in.xs[x - base] = v;
       part = __fma_rn(v, v, part);
       const uint64_t k = abs_key(v);
@@ -3041,6 +3049,7 @@ __device__ void phase_init1(const RunArgs &ra, PhaseSmem &sm) {
           best.key = k;
           best.lin = l;
           best.row = 0;
+          best.col = (int32_t)(x - base);
         }
       }
     }
@@ -3055,7 +3064,7 @@ __device__ void phase_init1(const RunArgs &ra, PhaseSmem &sm) {
       in.start_part[blockIdx.x].key = best.key;
       in.start_part[blockIdx.x].lin = best.lin;
       in.start_part[blockIdx.x].row = best.row;
-      in.start_part[blockIdx.x].col = 0;
+      in.start_part[blockIdx.x].col = best.col;  // the sample's number
     }
     __syncthreads();
   }
@@ -3079,8 +3088,9 @@ __device__ void phase_init2(const RunArgs &ra, PhaseSmem &sm) {
       cr.den = den;
       cr.xrms = sqrt(den / (double)in.nsamples);
       int32_t zero[TTC_MAXD] = {0};
-      const double x0 = gen_full(in, zero);
-      KeyBest o{abs_key(x0), 0, 0, 0};
+      // user generator: the origin's value follows the samples in xs
+      const double x0 = in.gen == 4 ? in.xs[in.nsamples] : gen_full(in, zero);
+      KeyBest o{abs_key(x0), 0, 0, (int32_t)in.nsamples};
       kb_take(best, o);
       int32_t st[TTC_MAXD];
       int64_t l = best.lin;
@@ -3088,7 +3098,7 @@ __device__ void phase_init2(const RunArgs &ra, PhaseSmem &sm) {
         st[m] = (int32_t)(l % in.n[m]);
         l /= in.n[m];
       }
-      const double xs0 = gen_full(in, st);
+      const double xs0 = in.gen == 4 ? in.xs[best.col] : gen_full(in, st);
       if (!isfinite(den) || !isfinite(xs0)) {
         cr.status = 4;
         cr.state = ST_DONE;
@@ -3487,6 +3497,132 @@ cudaError_t launch_phase(int phase, const RunArgs &ra, int grid, cudaStream_t s)
   if (e != cudaSuccess) return e;
   void *args[] = {(void *)&ra};
   return cudaLaunchKernel(f, dim3(grid), dim3(NT), args, sizeof(PhaseSmem), s);
+}
+
+// ---------------------------------------------------------------------------
+// user generator: the entries that enter the superblocks after a decision.
+// For bond b with old / new ranks the superblock grows from ro x co to
+// rn x cn (rows, columns); its new entries are, in this order,
+//   rows ro..rn-1 x columns 0..cn-1, then rows 0..ro-1 x columns co..cn-1.
+// k_user_count sums them per bond (first: every entry of the rank-one
+// superblocks); k_user_gather writes their multi-indices, k_user_scatter
+// puts the callback's values into the cache at (a, c).
+
+__device__ void user_extent(const InstDev &in, const Ctrl &cr, int b, int first, int64_t &ro,
+                            int64_t &co, int64_t &rn, int64_t &cn) {
+  const int32_t *r = cr.r, *ad = cr.add;
+  const int64_t pl = b == 0 ? 1 : r[b - 1], ql = b == in.nb - 1 ? 1 : r[b + 1];
+  const int64_t pa = b == 0 ? 0 : ad[b - 1], qa = b == in.nb - 1 ? 0 : ad[b + 1];
+  rn = pl * in.n[b];
+  cn = in.n[b + 1] * ql;
+  ro = first ? 0 : (pl - pa) * in.n[b];
+  co = first ? 0 : in.n[b + 1] * (ql - qa);
+}
+
+__global__ void k_user_count(const InstDev *inp, int first, int64_t *counts) {
+  const InstDev &in = *inp;
+  const Ctrl &cr = *in.ctrl;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t tot = 0;
+  for (int b = 0; b < in.nb; ++b) {
+    counts[b] = tot;
+    int64_t ro, co, rn, cn;
+    user_extent(in, cr, b, first, ro, co, rn, cn);
+    if (cr.state != ST_DONE) tot += rn * cn - ro * co;
+  }
+  counts[in.nb] = tot;
+}
+
+// entry x of the new entries of bond b -> superblock (a, c)
+__device__ __forceinline__ void user_entry(int64_t x, int64_t ro, int64_t co, int64_t rn,
+                                           int64_t cn, int64_t &a, int64_t &c) {
+  const int64_t top = (rn - ro) * cn;
+  if (x < top) {
+    a = ro + x / cn;
+    c = x - (a - ro) * cn;
+  } else {
+    const int64_t y = x - top, w = cn - co;
+    a = y / w;
+    c = co + (y - a * w);
+  }
+}
+
+__global__ void k_user_gather(const InstDev *inp, int first, const int64_t *counts, int32_t *idx) {
+  const InstDev &in = *inp;
+  const Ctrl &cr = *in.ctrl;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t NTOT = (int64_t)gridDim.x * blockDim.x;
+  for (int b = 0; b < in.nb; ++b) {
+    int64_t ro, co, rn, cn;
+    user_extent(in, cr, b, first, ro, co, rn, cn);
+    const int64_t base = counts[b], cnt = counts[b + 1] - base;
+    const SetDev &L = left_set(in, b), &Rs = right_set(in, b);
+    const int wl = b, wr = in.d - b - 2;
+    for (int64_t x = gt; x < cnt; x += NTOT) {
+      int64_t a, c;
+      user_entry(x, ro, co, rn, cn, a, c);
+      const int64_t p = a / in.n[b], i = a - p * in.n[b];
+      const int64_t q = c / in.n[b + 1], j = c - q * in.n[b + 1];
+      int32_t *o = idx + (base + x) * in.d;
+      for (int m = 0; m < wl; ++m) o[m] = L.idx[p * wl + m];
+      o[b] = (int32_t)i;
+      o[b + 1] = (int32_t)j;
+      for (int m = 0; m < wr; ++m) o[b + 2 + m] = Rs.idx[q * wr + m];
+    }
+  }
+}
+
+__global__ void k_user_scatter(const InstDev *inp, int first, const int64_t *counts,
+                               const double *vals) {
+  const InstDev &in = *inp;
+  const Ctrl &cr = *in.ctrl;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t NTOT = (int64_t)gridDim.x * blockDim.x;
+  for (int b = 0; b < in.nb; ++b) {
+    int64_t ro, co, rn, cn;
+    user_extent(in, cr, b, first, ro, co, rn, cn);
+    const int64_t base = counts[b], cnt = counts[b + 1] - base;
+    const BondDev &B = in.bond[b];
+    for (int64_t x = gt; x < cnt; x += NTOT) {
+      int64_t a, c;
+      user_entry(x, ro, co, rn, cn, a, c);
+      B.A[a * B.ldR + c] = vals[base + x];
+    }
+  }
+}
+
+// the error samples' multi-indices, then the origin's
+__global__ void k_user_samples(const InstDev *inp, int32_t *idx) {
+  const InstDev &in = *inp;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t NTOT = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = gt; k <= in.nsamples; k += NTOT) {
+    int32_t *o = idx + k * in.d;
+    if (k == in.nsamples) {
+      for (int m = 0; m < in.d; ++m) o[m] = 0;
+    } else {
+      for (int m = 0; m < in.d; ++m) o[m] = sample_coord(in, k, m);
+    }
+  }
+}
+
+cudaError_t launch_user_count(const InstDev *d_inst, int first, int64_t *counts, cudaStream_t s) {
+  k_user_count<<<1, 32, 0, s>>>(d_inst, first, counts);
+  return cudaGetLastError();
+}
+cudaError_t launch_user_gather(const InstDev *d_inst, int first, const int64_t *counts,
+                               int32_t *idx, cudaStream_t s) {
+  k_user_gather<<<152 * 4, 256, 0, s>>>(d_inst, first, counts, idx);
+  return cudaGetLastError();
+}
+cudaError_t launch_user_scatter(const InstDev *d_inst, int first, const int64_t *counts,
+                                const double *vals, cudaStream_t s) {
+  k_user_scatter<<<152 * 4, 256, 0, s>>>(d_inst, first, counts, vals);
+  return cudaGetLastError();
+}
+cudaError_t launch_user_samples(const InstDev *d_inst, int32_t *idx, cudaStream_t s) {
+  k_user_samples<<<152 * 4, 256, 0, s>>>(d_inst, idx);
+  return cudaGetLastError();
 }
 
 // Maxwellian tables of an instance (create time)

@@ -17,6 +17,14 @@ cudaError_t persistent_occupancy(int *blocks_per_sm);
 cudaError_t launch_persistent(const RunArgs &ra, int grid, cudaStream_t s);
 cudaError_t launch_phase(int phase, const RunArgs &ra, int grid, cudaStream_t s);
 cudaError_t launch_core(const InstDev *d_inst, int m, double *dst, cudaStream_t s);
+// user generator: count / gather / scatter of the entries entering the
+// superblocks (first != 0: the rank-one superblocks), and the error samples
+cudaError_t launch_user_count(const InstDev *d_inst, int first, int64_t *counts, cudaStream_t s);
+cudaError_t launch_user_gather(const InstDev *d_inst, int first, const int64_t *counts,
+                               int32_t *idx, cudaStream_t s);
+cudaError_t launch_user_scatter(const InstDev *d_inst, int first, const int64_t *counts,
+                                const double *vals, cudaStream_t s);
+cudaError_t launch_user_samples(const InstDev *d_inst, int32_t *idx, cudaStream_t s);
 cudaError_t launch_maxwellian_tables(const InstDev *d_inst, double *coef, double *nh, double *cosx);
 
 // tile geometry used to size the candidate buffer (host mirror of tile_geo)

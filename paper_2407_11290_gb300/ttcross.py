@@ -20,7 +20,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_ZERO_START, ERR_NONFINITE, ERR_DEVICE_TIMEOUT,
     NOT_CONVERGED = range(8)
 STATUS_NAMES = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_OOM", 3: "ERR_ZERO_START",
                 4: "ERR_NONFINITE", 5: "ERR_DEVICE_TIMEOUT", 6: "ERR_CUDA", 7: "NOT_CONVERGED"}
-GEN_HILBERT, GEN_TT, GEN_MAXWELLIAN, GEN_MAXWELLIAN_XV = 0, 1, 2, 3
+GEN_HILBERT, GEN_TT, GEN_MAXWELLIAN, GEN_MAXWELLIAN_XV, GEN_USER = 0, 1, 2, 3, 4
 PREC_FP64, PREC_FP32, PREC_SPLIT, PREC_AUTO = 0, 1, 2, 3
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "split": PREC_SPLIT, "auto": PREC_AUTO}
 RESIDUAL_RECOMPUTE, RESIDUAL_STORED = 0, 1
@@ -45,7 +45,41 @@ class Generator(C.Structure):
                 ("tt_cores", C.POINTER(C.c_double)),
                 ("dx", C.c_int32), ("dv", C.c_int32),
                 ("a_rho", C.c_double), ("a_u", C.c_double), ("a_T", C.c_double),
-                ("vmin", C.c_double), ("vmax", C.c_double)]
+                ("vmin", C.c_double), ("vmax", C.c_double),
+                ("user_fn", C.c_void_p), ("user", C.c_void_p)]
+
+
+# ttc_user_fn: (idx, count, values, user, stream)
+USER_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class _DeviceView:
+    """A device buffer of the library seen by torch without a copy."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+def _user_callback(fn, d, errors):
+    """ctypes callback around fn(idx, values): idx an int32 [count, d] and
+    values a float64 [count] torch CUDA tensor over the library's buffers;
+    fn fills values on torch's current stream, which is the run's stream.
+    Exceptions are kept in ``errors`` (they cannot cross the C ABI)."""
+
+    def cb(idx_ptr, count, val_ptr, user, stream):
+        try:
+            import torch
+            st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.current_stream()
+            with torch.cuda.stream(st):
+                idx = torch.as_tensor(_DeviceView(idx_ptr, (count, d), "<i4"), device="cuda")
+                out = torch.as_tensor(_DeviceView(val_ptr, (count,), "<f8"), device="cuda")
+                fn(idx, out)
+        except BaseException as e:  # noqa: BLE001 - re-raised on the Python side
+            errors.append(e)
+
+    return USER_FN(cb)
 
 
 class Options(C.Structure):
@@ -183,8 +217,14 @@ class TTCross:
             o.bond_max_rank = bm.ctypes.data_as(C.POINTER(C.c_int32))
         g = Generator()
         kind = gen["kind"]
+        self._user_errors = []
         if kind == "hilbert":
             g.kind = GEN_HILBERT
+        elif kind == "user":
+            g.kind = GEN_USER
+            cb = _user_callback(gen["fn"], self.d, self._user_errors)
+            keep.append(cb)
+            g.user_fn = C.cast(cb, C.c_void_p)
         elif kind == "tt":
             g.kind = GEN_TT
             ranks = _i32(gen["ranks"])
@@ -204,6 +244,7 @@ class TTCross:
         _check(L.ttcross_create(self.d, self.n.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(g),
                                 C.byref(o), C.byref(h)))
         self._h = h
+        self._keep = keep  # the user callback must outlive the handle
 
     # ------------------------------------------------------------------
     def close(self):
@@ -229,9 +270,12 @@ class TTCross:
             grid = _i32(subtensor_grid)
             if grid.size != self.d:
                 raise ValueError("subtensor_grid needs d entries")
-        _check(self._L.ttcross_run(self._h, float(eps), int(max_rank),
-                                   grid.ctypes.data_as(C.POINTER(C.c_int32)) if grid is not None
-                                   else None, _stream_handle(stream)))
+        rc = self._L.ttcross_run(self._h, float(eps), int(max_rank),
+                                 grid.ctypes.data_as(C.POINTER(C.c_int32)) if grid is not None
+                                 else None, _stream_handle(stream))
+        if self._user_errors:
+            raise self._user_errors.pop(0)
+        _check(rc)
 
     def sync(self, allow=(OK, NOT_CONVERGED)) -> int:
         return _check(self._L.ttcross_sync(self._h), allow)

@@ -119,3 +119,14 @@ def test_sampled_screen_options_checked_on_host():
     o.rook_rounds = 65
     assert L.ttcross_create(3, n, ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)) == \
         ttcross.ERR_INVALID_ARG
+
+
+def test_user_generator_needs_a_callback():
+    L = ttcross.load_library()
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 3)(8, 8, 8)
+    g = ttcross.Generator()
+    g.kind = ttcross.GEN_USER
+    assert L.ttcross_create(3, n, ctypes.byref(g), None, ctypes.byref(h)) == \
+        ttcross.ERR_INVALID_ARG
+    assert b"callback" in L.ttcross_last_error_string()
