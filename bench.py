@@ -46,8 +46,10 @@ SECONDARY = "hilbert6d_n64"
 ORACLE_CAP = {"hilbert6d_n256": 32}
 # DRAM bytes (read + write) of one k_persistent launch, from one ncu capture of
 # the current kernels (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
-# (workload, residual form, precision); absent keys report null
-DRAM_TRAFFIC = {("hilbert6d_n64", "stored", "fp64"): 17181184 + 95764736}
+# (workload, residual form, precision); absent keys report null.  The n = 256
+# captures ran with rank capacity 32 (same sweeps: the ranks stay below 24).
+DRAM_TRAFFIC = {("hilbert6d_n256", "stored", "fp64"): 6190752000 + 7265992448,
+                ("hilbert6d_n256", "stored", "split"): 6190490112 + 7296124416}
 THROTTLE_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
                  0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
                  0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",

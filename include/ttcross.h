@@ -238,6 +238,27 @@ ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps
                              const int32_t *max_rank, const int32_t *const *grids,
                              void *stream);
 
+/* Schedule of the later runs of h (the paper picks its process-grid
+   partitions by trying them, Sec. 5.1 testing setup; here the tile schedule):
+   tile_edge 0 (the library's rule), 32 or 64 superblock rows / columns per
+   CTA tile (FP64 and stored forms); queue_split 0 (half) or 1..7 eighths of
+   the CTAs that start the stored screen on its queue of entries new to a
+   superblock (the others start on the carried entries).  Pivots and results
+   do not depend on it.  Errors: INVALID_ARG. */
+ttc_status ttcross_set_plan(ttc_handle *h, int32_t tile_edge, int32_t queue_split);
+
+/* Measures the candidate schedules of ttcross_set_plan on this instance (tile
+   edge 64 and 32; queue split 4, 2, 6 eighths in the stored form), each by two
+   runs of ttcross_run(eps, max_rank, subtensor_grid, stream) timed on the
+   device, keeps the fastest for later runs and returns it (any output pointer
+   may be NULL; best_ms is its device time).  Synchronous.  The caller may
+   cache the choice per shape class and apply it with ttcross_set_plan.
+   Errors: those of ttcross_run / ttcross_sync; INVALID_ARG for the user
+   generator. */
+ttc_status ttcross_autotune(ttc_handle *h, double eps, int max_rank, const int32_t *subtensor_grid,
+                            void *stream, int32_t *tile_edge, int32_t *queue_split,
+                            double *best_ms);
+
 /* Waits for the last run of h and returns its device-side status. */
 ttc_status ttcross_sync(ttc_handle *h);
 

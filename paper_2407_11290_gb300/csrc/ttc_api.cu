@@ -91,6 +91,7 @@ struct ttc_handle {
   double *ustage_val = nullptr;
   int64_t ustage_cap = 0;
   int64_t *ucounts = nullptr;   // device [TTC_MAXD + 1]
+  int32_t plan_te = 0, plan_qsplit = 0;  // ttcross_set_plan
   bool synced = false;          // h_ctrl holds the finished last run
   ttc_status sync_status = TTC_OK;
   std::string sync_msg;
@@ -177,6 +178,8 @@ Ctrl make_ctrl(const ttc_handle *h, double eps, int max_rank, const int32_t *gri
   c.tau = eps;
   c.max_refine = h->opt.max_refine;
   for (int m = 0; m < h->d; ++m) c.grid[m] = grid ? grid[m] : 0;
+  c.force_te = h->plan_te;
+  c.qsplit = h->plan_qsplit;
   return c;
 }
 
@@ -817,6 +820,61 @@ ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps
 }
 
 static ttc_status sync_run(ttc_handle *h);
+
+ttc_status ttcross_set_plan(ttc_handle *h, int32_t tile_edge, int32_t queue_split) {
+  g_err.clear();
+  ttc_status s = check_handle(h);
+  if (s) return s;
+  if (tile_edge != 0 && tile_edge != 32 && tile_edge != 64)
+    return fail(TTC_ERR_INVALID_ARG, "tile_edge %d: 0, 32 or 64", tile_edge);
+  if (queue_split < 0 || queue_split > 7)
+    return fail(TTC_ERR_INVALID_ARG, "queue_split %d outside [0,7]", queue_split);
+  h->plan_te = tile_edge;
+  h->plan_qsplit = queue_split;
+  return TTC_OK;
+}
+
+ttc_status ttcross_autotune(ttc_handle *h, double eps, int max_rank, const int32_t *subtensor_grid,
+                            void *stream, int32_t *tile_edge, int32_t *queue_split,
+                            double *best_ms) {
+  g_err.clear();
+  ttc_status s = check_handle(h);
+  if (s) return s;
+  if (h->user_fn) return fail(TTC_ERR_INVALID_ARG, "the user generator runs host-stepped: no plan");
+  if (!h->events_ok) return fail(TTC_ERR_CUDA, "no events to time the candidates");
+  // the candidates: tile edge 32 / 64, and (stored form) 2, 4 or 6 eighths of
+  // the CTAs starting the screen on the fresh queue; each is run twice and
+  // timed by the device events around its launch, the faster time counts
+  const int32_t edges[2] = {64, 32};
+  const int32_t splits_stored[3] = {4, 2, 6}, splits_other[1] = {0};
+  const int32_t *splits = h->hi.stored ? splits_stored : splits_other;
+  const int nsplit = h->hi.stored ? 3 : 1;
+  double best = 1e300;
+  int32_t be = 0, bq = 0;
+  for (int e = 0; e < 2; ++e)
+    for (int q = 0; q < nsplit; ++q) {
+      if ((s = ttcross_set_plan(h, edges[e], splits[q]))) return s;
+      double t = 1e300;
+      for (int rep = 0; rep < 2; ++rep) {
+        if ((s = ttcross_run(h, eps, max_rank, subtensor_grid, stream))) return s;
+        s = ttcross_sync(h);
+        if (s != TTC_OK && s != TTC_NOT_CONVERGED) return s;
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        t = std::min(t, (double)ms);
+      }
+      if (t < best) {
+        best = t;
+        be = edges[e];
+        bq = splits[q];
+      }
+    }
+  if ((s = ttcross_set_plan(h, be, bq))) return s;
+  if (tile_edge) *tile_edge = be;
+  if (queue_split) *queue_split = bq;
+  if (best_ms) *best_ms = best;
+  return TTC_OK;
+}
 
 ttc_status ttcross_sync(ttc_handle *h) {
   ttc_status s = check_handle(h);

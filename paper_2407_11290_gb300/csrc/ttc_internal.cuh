@@ -80,6 +80,10 @@ struct Ctrl {
   int64_t screen_fmas, error_fmas;  // algorithmic FMAs of the screens / errors
   int32_t max_refine;
   int32_t grid[TTC_MAXD];  // subtensor pieces per mode (0 = library tiles)
+  // plan of this run (ttcross_set_plan / the autotuner): tile edge (0 = the
+  // library's rule, 32, 64) and the eighths of the CTAs that start the
+  // stored screen on its fresh queue (0 = half)
+  int32_t force_te, qsplit;
   int32_t pad;
   // stored-residual form, per bond: the stored extent (superblock rows /
   // columns as of the last screen) and whether the rank-one step of the last

@@ -356,7 +356,27 @@ __device__ void write_plan_warp(const InstDev &in, Ctrl &cr, const int32_t *r, i
   const bool pieces32 = __all_sync(0xffffffffu, small) && (in.prec == P_FP64 || in.stored);
   int te = 64;
   TileGeo g = g64;
-  if (pieces32) {
+  // a tile edge set for this run (the FP64 and stored forms; the mixed
+  // recompute forms keep 64-wide tiles); 32-wide tiles when the candidate
+  // slots of every bond allow them
+  const int fte = (in.prec == P_FP64 || in.stored) ? cr.force_te : 0;
+  int fok = fte == 32 || fte == 64;
+  if (fte == 32) {
+    TileGeo g32;
+    int ok = 1;
+    if (act) {
+      g32 = tile_geo_e(in, cr, r, lane, 32);
+      ok = (int64_t)g32.nrt * g32.nct <= in.bond[lane].cand_cap;
+    }
+    fok = __all_sync(0xffffffffu, ok);
+    if (fok) {
+      te = 32;
+      g = g32;
+    }
+  }
+  if (fok) {
+    // the edge set for the run
+  } else if (pieces32) {
     te = 32;
     if (act) g = tile_geo_e(in, cr, r, lane, 32);
   } else if (!in.stored && in.prec == P_FP64 && 4 * t64 < (int64_t)grid && kmax >= 24) {
@@ -1350,7 +1370,9 @@ __device__ void screen_stored_instance(const InstDev &in, const int32_t *r, Phas
   const int32_t spt = quarters ? STORED_SLOTS : 1;  // slots per tile
   const int32_t nA = spt * nf;
   const int32_t G = gridDim.x;
-  const int32_t HA = nA == 0 ? 0 : nB == 0 ? G : (G + 1) / 2;  // CTAs starting on A
+  const int32_t qs = ld_cg(cr.qsplit);  // eighths of the CTAs that start on A (0: half)
+  const int32_t HA = nA == 0 ? 0 : nB == 0 ? G : qs > 0 ? max(1, min(G - 1, G * qs / 8))
+                                                         : (G + 1) / 2;
   const int32_t N[2] = {nA, nB}, H[2] = {HA, G - HA};
   if (blockIdx.x == 0 && threadIdx.x == 0) screen_bookkeeping(in, r, s_geo, s_sr, s_sc, s_pend, spt);
   // thread 0 keeps the queue, whether it has switched, and the next item

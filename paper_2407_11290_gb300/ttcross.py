@@ -8,6 +8,7 @@ or no GPU is present, the calls raise.  PyTorch supplies the CUDA stream
 from __future__ import annotations
 
 import ctypes as C
+import json
 import os
 import threading
 
@@ -30,7 +31,8 @@ RESIDUALS = {"recompute": RESIDUAL_RECOMPUTE, "stored": RESIDUAL_STORED}
 ABI_SYMBOLS = ("ttcross_default_options", "ttcross_create", "ttcross_run", "ttcross_run_batch",
                "ttcross_sync", "ttcross_get_ranks", "ttcross_get_cores", "ttcross_get_pivots",
                "ttcross_get_pivot_inverse", "ttcross_get_stats", "ttcross_destroy",
-               "ttcross_sampled_error_noalloc", "ttcross_last_error_string")
+               "ttcross_sampled_error_noalloc", "ttcross_last_error_string",
+               "ttcross_set_plan", "ttcross_autotune")
 
 
 class TTCError(RuntimeError):
@@ -143,6 +145,10 @@ def load_library(path: str = LIB_PATH):
                                                     C.POINTER(Generator), C.POINTER(P),
                                                     C.POINTER(C.c_int64), C.c_int64, C.c_uint64,
                                                     P, P]
+        L.ttcross_set_plan.argtypes = [P, C.c_int32, C.c_int32]
+        L.ttcross_autotune.argtypes = [P, C.c_double, C.c_int, C.POINTER(C.c_int32), P,
+                                       C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_double)]
         L.ttcross_last_error_string.restype = C.c_char_p
         for name in ABI_SYMBOLS:
             f = getattr(L, name)
@@ -276,6 +282,22 @@ class TTCross:
         if self._user_errors:
             raise self._user_errors.pop(0)
         _check(rc)
+
+    def set_plan(self, tile_edge: int = 0, queue_split: int = 0):
+        """Tile edge (0, 32, 64) and queue split (0, 1..7 eighths) of later runs."""
+        _check(self._L.ttcross_set_plan(self._h, int(tile_edge), int(queue_split)))
+
+    def autotune(self, eps: float, max_rank: int = 0, subtensor_grid=None, stream=None):
+        """Measure the candidate plans on this instance and keep the fastest.
+        Returns (tile_edge, queue_split, best_ms)."""
+        grid = _i32(subtensor_grid) if subtensor_grid is not None else None
+        te, qs, ms = C.c_int32(), C.c_int32(), C.c_double()
+        _check(self._L.ttcross_autotune(self._h, float(eps), int(max_rank),
+                                        grid.ctypes.data_as(C.POINTER(C.c_int32))
+                                        if grid is not None else None,
+                                        _stream_handle(stream), C.byref(te), C.byref(qs),
+                                        C.byref(ms)))
+        return te.value, qs.value, ms.value
 
     def sync(self, allow=(OK, NOT_CONVERGED)) -> int:
         return _check(self._L.ttcross_sync(self._h), allow)
@@ -431,3 +453,47 @@ def run_batch(crosses, eps, max_rank=None, grids=None, stream=None):
     _check(L.ttcross_run_batch(hs, cnt, e.ctypes.data_as(C.POINTER(C.c_double)),
                                mr.ctypes.data_as(C.POINTER(C.c_int32)) if mr is not None else None,
                                gp, _stream_handle(stream)))
+
+
+def plan_cache_path() -> str:
+    """The autotuner's cache of plans per shape class (TTCROSS_PLAN_CACHE, else
+    ~/.cache/ttcross_gb300/plans.json)."""
+    return os.environ.get("TTCROSS_PLAN_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "ttcross_gb300",
+                                       "plans.json"))
+
+
+def shape_class(tc, eps, max_rank, subtensor_grid, precision, residual) -> str:
+    """Key of a plan: mode sizes, the rank cap, eps, grid, precision, form."""
+    grid = None if subtensor_grid is None else [int(v) for v in subtensor_grid]
+    return json.dumps({"n": [int(v) for v in tc.n], "max_rank": int(max_rank), "eps": float(eps),
+                       "grid": grid, "precision": str(precision), "residual": str(residual)},
+                      sort_keys=True)
+
+
+def tuned_plan(tc, eps, max_rank, subtensor_grid, precision, residual, stream=None):
+    """The plan of this shape class from the cache, else measured by the
+    library's autotuner and cached.  Returns (tile_edge, queue_split, source)."""
+    path = plan_cache_path()
+    key = shape_class(tc, eps, max_rank, subtensor_grid, precision, residual)
+    cache = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if key in cache:
+        te, qs = cache[key]["tile_edge"], cache[key]["queue_split"]
+        tc.set_plan(te, qs)
+        return te, qs, "cache"
+    te, qs, ms = tc.autotune(eps, max_rank, subtensor_grid, stream)
+    cache[key] = {"tile_edge": te, "queue_split": qs, "ms": ms}
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path + ".tmp", "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(path + ".tmp", path)
+    except OSError:
+        pass
+    return te, qs, "measured"
