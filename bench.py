@@ -183,13 +183,19 @@ def _dtype(prec: str) -> str:
 
 
 def time_arm(ttcross, cfg, prec, residual, steps, warmup, stream, flush, sampler=None,
-             host_loop=False):
-    """One arm: a TTCross of the workload in the given precision, ``warmup``
+             host_loop=False, plans=None):
+    """One arm: a TTCross of the workload in the given precision, its tile
+    plan from the autotuner's cache (measured on a miss; untimed), ``warmup``
     untimed runs, then ``steps`` timed runs (L2 flushed before each, CUDA
     events on the launching stream around the run)."""
     import torch
     tc = ttcross.TTCross(cfg["n"], cfg["gen"], max_rank=cfg["max_rank"], nsamples=cfg["nsamples"],
                          precision=prec, residual=residual, host_loop=host_loop)
+    if not host_loop:
+        plan = ttcross.tuned_plan(tc, cfg["eps"], cfg["max_rank"], cfg["grid"], prec, residual,
+                                  stream)
+        if plans is not None:
+            plans[prec] = {"tile_edge": plan[0], "queue_split": plan[1], "source": plan[2]}
 
     def one_step():
         tc.run(cfg["eps"], subtensor_grid=cfg["grid"], stream=stream)
@@ -218,6 +224,7 @@ def time_arm(ttcross, cfg, prec, residual, steps, warmup, stream, flush, sampler
 
 
 def bench_gpu(args, rank, world, local):
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -232,9 +239,10 @@ def bench_gpu(args, rank, world, local):
     if world > 1:
         dist.barrier()
     sampler = ClockSampler(local)
+    plans = {}
     tc, step_ms, kern_ms, clocks, one_step = time_arm(
         ttcross, cfg, args.precision, args.residual, args.steps, args.warmup, stream, flush,
-        sampler, host_loop=args.host_loop)
+        sampler, host_loop=args.host_loop, plans=plans)
     st = tc.stats()
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
@@ -265,7 +273,7 @@ def bench_gpu(args, rank, world, local):
     if rank == 0 and not args.no_forms:
         other = "split" if args.precision == "fp64" else "fp64"
         a, sm_, km, _, _ = time_arm(ttcross, cfg, other, args.residual, max(3, args.steps // 2),
-                                    max(1, args.warmup // 2), stream, flush)
+                                    max(1, args.warmup // 2), stream, flush, plans=plans)
         ast = a.stats()
         arms[other] = {"ms": sum(sm_) / len(sm_), "median_ms": statistics.median(sm_),
                        "kernel_ms": statistics.median(km), "err": ast["err"],
@@ -304,10 +312,16 @@ def bench_gpu(args, rank, world, local):
                    "nsamples": cfg["nsamples"],
                    "precision": args.precision, "residual": args.residual,
                    "l2": "flushed between steps (512 MB write)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "plans": plans},
         "min_ms": min(step_ms), "median_ms": statistics.median(step_ms),
         "entries_screened": st["entries_screened"],
         "entries_per_s": st["entries_screened"] * world / (ms * 1e-3),
+        # the share of the tensor's entries the cross evaluated (the paper's
+        # "% of full tensor size accessed", Sec. 5.1): in the stored form every
+        # superblock entry is formed once, plus the error samples
+        "accessed_fraction": ((st["entries_fresh"] + cfg["nsamples"]) /
+                              float(np.prod([float(v) for v in cfg["n"]]))
+                              if args.residual == "stored" else None),
         "sweeps": st["sweeps"], "ranks": [int(x) for x in tc.ranks()], "err": st["err"],
         "phase_ms": st["phase_ms"],
         "status": ttcross.STATUS_NAMES.get(st["status"], st["status"]),
@@ -364,9 +378,19 @@ def bench_batch(args, rank, world, local):
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     allow = (ttcross.OK, ttcross.NOT_CONVERGED)
 
+    tuned = {}
+
     def make(prec):
-        return [ttcross.TTCross(w["n"], w["gen"], max_rank=cap, nsamples=ns, precision=prec,
-                                residual="stored") for w in ws]
+        hs = [ttcross.TTCross(w["n"], w["gen"], max_rank=cap, nsamples=ns, precision=prec,
+                              residual="stored") for w in ws]
+        # the autotuner's plan per shape class (d, n), measured on the class's
+        # first instance (cached across runs), applied to every instance
+        for w, c in zip(ws, hs):
+            key = f"{prec}/d{len(w['n'])}/n{w['n'][0]}"
+            if key not in tuned:
+                tuned[key] = ttcross.tuned_plan(c, eps, cap, None, prec, "stored", stream)[:2]
+            c.set_plan(*tuned[key])
+        return hs
 
     def timed(run):
         for _ in range(args.warmup):
@@ -426,7 +450,7 @@ def bench_batch(args, rank, world, local):
         "arms_ms": times, "fastest": best,
         "mixed_batched_vs_fp64_loop": times["loop_fp64"] / times["batched_split"],
         "fp64_batched_vs_loop": times["loop_fp64"] / times["batched_fp64"],
-        "arms": summary, "count": len(ws),
+        "arms": summary, "count": len(ws), "plans": tuned,
         "gpu_launches": 2 * len(ws),
     }
     if rank == 0:

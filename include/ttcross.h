@@ -192,6 +192,7 @@ typedef struct {
   int64_t entries_fresh;     /* screened entries formed as A - T R (all of them in the
                                 recompute form; the rest were carried in storage) */
   int64_t stored_bytes;      /* stored form: bytes of E the screens read and wrote */
+  double rebuild_ms;         /* GPU time of the last ttcross_rebuild_cores (0 if none) */
 } ttc_stats;
 
 typedef struct ttc_handle ttc_handle;
@@ -270,6 +271,19 @@ ttc_status ttcross_get_ranks(ttc_handle *h, int64_t *s);
    else host memory).  Waits for the last run. */
 ttc_status ttcross_get_cores(ttc_handle *h, int k, double *dst, int dst_is_device,
                              void *stream);
+
+/* Core construction from the pivot sets alone (Alg. 5, second loop; Sec.
+   3.2.2, eq. corereshape): after the last run, every bond's history of
+   Alg. 4 is rebuilt from the pivots (the pivot rows step by step, one CTA
+   per bond), every superblock row of T_k is replayed from it (a row per
+   warp, the rows sliced over the grid, as the paper's core-construction
+   grids), and the last core X(I_{<=d-1}, :) is formed from the entries.  T,
+   the history and the last bond's R are cleared first, so the cores read
+   afterwards come from the pivots alone; by the arithmetic contract they
+   equal the cores the sweeps kept, bit for bit.  Asynchronous on `stream`;
+   its device time is ttc_stats.rebuild_ms.  Errors: those of ttcross_sync,
+   OOM (a scratch of (d-1) * 256^2 doubles on first use), CUDA. */
+ttc_status ttcross_rebuild_cores(ttc_handle *h, void *stream);
 
 /* Pivot sets of bond k (1 <= k <= d-1) in insertion order: I_{<=k} as
    [r_k][k] and J_{>k} as [r_k][d-k] int32 host arrays (caller-owned). */

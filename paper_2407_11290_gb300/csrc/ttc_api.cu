@@ -92,6 +92,9 @@ struct ttc_handle {
   int64_t ustage_cap = 0;
   int64_t *ucounts = nullptr;   // device [TTC_MAXD + 1]
   int32_t plan_te = 0, plan_qsplit = 0;  // ttcross_set_plan
+  double *rebuild_scratch = nullptr;     // ttcross_rebuild_cores: pivot rows' T
+  cudaEvent_t ev2 = nullptr, ev3 = nullptr;  // around the last core rebuild
+  bool rebuilt = false;
   bool synced = false;          // h_ctrl holds the finished last run
   ttc_status sync_status = TTC_OK;
   std::string sync_msg;
@@ -919,6 +922,33 @@ static ttc_status synced(ttc_handle *h) {
   return TTC_OK;  // device-side failures still leave a readable state
 }
 
+ttc_status ttcross_rebuild_cores(ttc_handle *h, void *stream) {
+  ttc_status s = synced(h);
+  if (s) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!h->rebuild_scratch)
+    CU(cudaMalloc(&h->rebuild_scratch, sizeof(double) * (size_t)h->nb * RCAP * RCAP));
+  if (!h->ev2) {
+    CU(cudaEventCreate(&h->ev2));
+    CU(cudaEventCreate(&h->ev3));
+  }
+  // the factors go, so that the cores come from the pivot sets alone
+  for (int b = 0; b < h->nb; ++b) {
+    const BondDev &B = h->hi.bond[b];
+    CU(cudaMemsetAsync(B.T, 0, sizeof(double) * B.cap * B.ldT, st));
+    CU(cudaMemsetAsync(B.hc, 0, sizeof(double) * B.cap * B.cap, st));
+    CU(cudaMemsetAsync(B.hpiv, 0, sizeof(double) * B.cap * B.cap, st));
+    CU(cudaMemsetAsync(B.delta, 0, sizeof(double) * B.cap, st));
+  }
+  const BondDev &BL = h->hi.bond[h->nb - 1];
+  CU(cudaMemsetAsync(BL.R, 0, sizeof(double) * BL.cap * BL.ldR, st));
+  CU(cudaEventRecord(h->ev2, st));
+  CU(launch_rebuild_cores(h->d_inst, h->nb, h->rebuild_scratch, h->grid, st));
+  CU(cudaEventRecord(h->ev3, st));
+  h->rebuilt = true;
+  return TTC_OK;
+}
+
 ttc_status ttcross_get_ranks(ttc_handle *h, int64_t *sz) {
   ttc_status s = synced(h);
   if (s) return s;
@@ -990,6 +1020,10 @@ ttc_status ttcross_get_stats(ttc_handle *h, ttc_stats *out) {
   out->status = s;
   out->entries_fresh = c.entries_fresh;
   out->stored_bytes = c.stored_bytes;
+  if (h->rebuilt && cudaEventSynchronize(h->ev3) == cudaSuccess) {
+    float rms = 0.f;
+    if (cudaEventElapsedTime(&rms, h->ev2, h->ev3) == cudaSuccess) out->rebuild_ms = rms;
+  }
   float ms = 0.f;
   if (h->events_ok && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) out->device_ms = ms;
   Barrier bar;
@@ -1010,6 +1044,9 @@ ttc_status ttcross_destroy(ttc_handle *h) {
   if (h->cand) cudaFree(h->cand);
   if (h->estore) cudaFree(h->estore);
   if (h->acache) cudaFree(h->acache);
+  if (h->rebuild_scratch) cudaFree(h->rebuild_scratch);
+  if (h->ev2) cudaEventDestroy(h->ev2);
+  if (h->ev3) cudaEventDestroy(h->ev3);
   if (h->ustage_idx) cudaFree(h->ustage_idx);
   if (h->ustage_val) cudaFree(h->ustage_val);
   if (h->pool) cudaFree(h->pool);

@@ -3522,6 +3522,104 @@ cudaError_t launch_phase(int phase, const RunArgs &ra, int grid, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------------------
+// Core construction from the pivot sets alone (Alg. 5, second loop; Sec.
+// 3.2.2 and eq. corereshape): the history of Alg. 4 is rebuilt for every
+// bond, then every superblock row of T_k is replayed from it, sliced over the
+// grid (a row per warp), and the last bond's R is formed from the entries.
+// By the arithmetic contract every value equals the one the sweeps kept.
+
+// history of bond blockIdx.x (one CTA per bond), step by step: before step
+// t every pivot row a_z (z >= t) holds T(a_z, :t); step t takes its column
+// c_t = R(:t, c_t) = A(a_u, c_t), its snapshot T(a_t, :t) and delta_t, then
+// applies itself to the later pivot rows (a thread per row)
+__global__ void __launch_bounds__(NT) k_rebuild_history(const InstDev *inp, double *scratch) {
+  const InstDev &in = *inp;
+  const int b = blockIdx.x;
+  if (b >= in.nb) return;
+  const BondDev &B = in.bond[b];
+  const int r = in.ctrl->r[b];
+  const int64_t cap = B.cap;
+  double *Tp = scratch + (int64_t)b * RCAP * RCAP;  // [z][u]: T(a_z, u) of pivot row z
+  __shared__ double s_hc[RCAP], s_hp[RCAP];
+  __shared__ double s_delta;
+  __shared__ int s_ok;
+  for (int x = threadIdx.x; x < r * r; x += NT) Tp[x] = 0.0;
+  __syncthreads();
+  for (int t = 0; t < r; ++t) {
+    // c_t restricted to the earlier pivots, and row a_t's snapshot
+    for (int u = threadIdx.x; u < t; u += NT) {
+      const double c = sb_entry(in, b, B.prow[u], B.pcol[t]);
+      s_hc[u] = c;
+      s_hp[u] = Tp[(int64_t)t * RCAP + u];
+      B.hc[(int64_t)t * cap + u] = c;
+      B.hpiv[(int64_t)t * cap + u] = s_hp[u];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double piv = __dsub_rn(sb_entry(in, b, B.prow[t], B.pcol[t]), chain(s_hp, 1, s_hc, 1, t));
+      s_delta = 1.0 / piv;
+      s_ok = isfinite(s_delta) ? 1 : 0;
+      B.delta[t] = s_delta;
+    }
+    __syncthreads();
+    if (!s_ok) return;  // no such pivot was taken (the sweeps check the same value)
+    const double dt = s_delta;
+    // step t on the later pivot rows z > t
+    for (int z = t + 1 + threadIdx.x; z < r; z += NT) {
+      double *Tz = Tp + (int64_t)z * RCAP;
+      const double sv = __dsub_rn(chain(Tz, 1, s_hc, 1, t), sb_entry(in, b, B.prow[z], B.pcol[t]));
+      const double w = __dmul_rn(dt, sv);
+      for (int u = 0; u < t; ++u) Tz[u] = __fma_rn(w, s_hp[u], Tz[u]);
+      Tz[t] = -w;
+    }
+    __syncthreads();
+  }
+}
+
+// every superblock row of every bond replayed through its whole history
+// (Alg. 4), a row per warp, rows dealt over the grid; then R of the last
+// bond (its core) from the entries
+__global__ void __launch_bounds__(NT, 2) k_rebuild_rows(const InstDev *inp) {
+  const InstDev &in = *inp;
+  const int64_t nwarps = (int64_t)gridDim.x * (NT / 32);
+  const int64_t gw = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+  int64_t base = 0;
+  for (int b = 0; b < in.nb; ++b) {
+    const int r = in.ctrl->r[b];
+    const int64_t rows = (int64_t)(b == 0 ? 1 : in.ctrl->r[b - 1]) * in.n[b];
+    for (int64_t a = ((gw - base) % nwarps + nwarps) % nwarps; a < rows; a += nwarps) {
+      if (r <= 32)
+        replay_row_warp<1, true>(in, b, a, r, nullptr, true, 1);
+      else if (r <= 64)
+        replay_row_warp<2, true>(in, b, a, r, nullptr, true, 1);
+      else if (r <= 128)
+        replay_row_warp<4, true>(in, b, a, r, nullptr, true, 1);
+      else
+        replay_row_warp<8, false>(in, b, a, r, nullptr, true, 1);
+    }
+    base += rows;
+  }
+  const int bl = in.nb - 1;
+  const BondDev &B = in.bond[bl];
+  const int r = in.ctrl->r[bl];
+  const int64_t nn = in.n[in.d - 1];
+  const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x, NTOT = (int64_t)gridDim.x * NT;
+  for (int64_t x = gt; x < r * nn; x += NTOT) {
+    const int64_t t = x / nn, c = x - t * nn;
+    putR(in, B, t * B.ldR + c, sb_entry(in, bl, B.prow[t], c));
+  }
+}
+
+cudaError_t launch_rebuild_cores(const InstDev *d_inst, int nb, double *scratch, int grid,
+                                 cudaStream_t s) {
+  k_rebuild_history<<<nb, NT, 0, s>>>(d_inst, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_rebuild_rows<<<grid, NT, 0, s>>>(d_inst);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // user generator: the entries that enter the superblocks after a decision.
 // For bond b with old / new ranks the superblock grows from ro x co to
 // rn x cn (rows, columns); its new entries are, in this order,

@@ -17,6 +17,9 @@ cudaError_t persistent_occupancy(int *blocks_per_sm);
 cudaError_t launch_persistent(const RunArgs &ra, int grid, cudaStream_t s);
 cudaError_t launch_phase(int phase, const RunArgs &ra, int grid, cudaStream_t s);
 cudaError_t launch_core(const InstDev *d_inst, int m, double *dst, cudaStream_t s);
+// core construction from the pivot sets (scratch: nb * RCAP * RCAP doubles)
+cudaError_t launch_rebuild_cores(const InstDev *d_inst, int nb, double *scratch, int grid,
+                                 cudaStream_t s);
 // user generator: count / gather / scatter of the entries entering the
 // superblocks (first != 0: the rank-one superblocks), and the error samples
 cudaError_t launch_user_count(const InstDev *d_inst, int first, int64_t *counts, cudaStream_t s);

@@ -32,7 +32,7 @@ ABI_SYMBOLS = ("ttcross_default_options", "ttcross_create", "ttcross_run", "ttcr
                "ttcross_sync", "ttcross_get_ranks", "ttcross_get_cores", "ttcross_get_pivots",
                "ttcross_get_pivot_inverse", "ttcross_get_stats", "ttcross_destroy",
                "ttcross_sampled_error_noalloc", "ttcross_last_error_string",
-               "ttcross_set_plan", "ttcross_autotune")
+               "ttcross_set_plan", "ttcross_autotune", "ttcross_rebuild_cores")
 
 
 class TTCError(RuntimeError):
@@ -110,7 +110,8 @@ class Stats(C.Structure):
                 ("device_ms", C.c_double), ("phase_ms", C.c_double * 6),
                 ("status", C.c_int32),
                 ("device_error_where", C.c_int32),
-                ("entries_fresh", C.c_int64), ("stored_bytes", C.c_int64)]
+                ("entries_fresh", C.c_int64), ("stored_bytes", C.c_int64),
+                ("rebuild_ms", C.c_double)]
 
 
 _lock = threading.Lock()
@@ -146,6 +147,7 @@ def load_library(path: str = LIB_PATH):
                                                     C.POINTER(C.c_int64), C.c_int64, C.c_uint64,
                                                     P, P]
         L.ttcross_set_plan.argtypes = [P, C.c_int32, C.c_int32]
+        L.ttcross_rebuild_cores.argtypes = [P, P]
         L.ttcross_autotune.argtypes = [P, C.c_double, C.c_int, C.POINTER(C.c_int32), P,
                                        C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                        C.POINTER(C.c_double)]
@@ -282,6 +284,10 @@ class TTCross:
         if self._user_errors:
             raise self._user_errors.pop(0)
         _check(rc)
+
+    def rebuild_cores(self, stream=None):
+        """Rebuild T_k (and the last core) from the pivot sets alone (Alg. 5)."""
+        _check(self._L.ttcross_rebuild_cores(self._h, _stream_handle(stream)))
 
     def set_plan(self, tile_edge: int = 0, queue_split: int = 0):
         """Tile edge (0, 32, 64) and queue split (0, 1..7 eighths) of later runs."""

@@ -326,3 +326,73 @@ def test_paper_maxwellian_xv_prescribed_ranks_resync(tt, name, shrink):
             np.testing.assert_array_equal(a, b)
     assert abs(g.stats()["err"] - o.sampled_error(10**5)) <= 1e-12
     print(f"{name} / {shrink}: {ties} near-tie(s), err {g.stats()['err']:.3e}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split"])
+def test_plans_change_no_result_and_autotune_picks_one(tt, prec, tmp_path, monkeypatch):
+    """Tile edges and queue splits reorder the work, never the results: every
+    plan gives the same pivots and cores; the autotuner returns one of its
+    candidates and the binding caches it per shape class."""
+    w = W.CONFIGS["hilbert6d_n64"]
+    g = tt.TTCross(w["n"], w["gen"], max_rank=w["max_rank"], nsamples=w["nsamples"],
+                   precision=prec, residual="stored")
+    g.run(w["eps"], subtensor_grid=w["grid"])
+    assert g.sync() == tt.OK
+    ref = g.cores()
+    for te, qs in [(32, 2), (64, 6), (64, 0), (32, 7)]:
+        g.set_plan(te, qs)
+        g.run(w["eps"], subtensor_grid=w["grid"])
+        assert g.sync() == tt.OK
+        for k, (a, b) in enumerate(zip(g.cores(), ref), start=1):
+            np.testing.assert_array_equal(a, b, err_msg=f"plan {te}/{qs}, core {k}")
+    monkeypatch.setenv("TTCROSS_PLAN_CACHE", str(tmp_path / "plans.json"))
+    te, qs, src = tt.tuned_plan(g, w["eps"], w["max_rank"], w["grid"], prec, "stored")
+    assert src == "measured" and te in (32, 64) and qs in (2, 4, 6)
+    assert tt.tuned_plan(g, w["eps"], w["max_rank"], w["grid"], prec, "stored") == (te, qs, "cache")
+    g.run(w["eps"], subtensor_grid=w["grid"])
+    assert g.sync() == tt.OK
+    for a, b in zip(g.cores(), ref):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("case", ["hilbert6d_n64", "hilbert6d_n64_recompute", "tt_rank48",
+                                  "maxwellian", "split", "paper_hilbert6d_n300"])
+def test_rebuilt_cores_equal_the_sweeps_cores(tt, case):
+    """Core construction from the pivot sets alone (Alg. 5: the history of
+    Alg. 4 rebuilt from the pivots, every row replayed, the last core from the
+    entries) gives the cores the sweeps kept, bit for bit; the instance then
+    runs again as before."""
+    kw = dict(residual="stored")
+    if case.startswith("hilbert6d_n64"):
+        w = dict(W.CONFIGS["hilbert6d_n64"])
+        eps, cap, ns, grid = w["eps"], w["max_rank"], w["nsamples"], w["grid"]
+        if case.endswith("recompute"):
+            kw = dict(residual="recompute")
+    elif case == "tt_rank48":
+        w = W.random_tt([10] * 5, [1, 10, 48, 48, 10, 1], seed=21)
+        eps, cap, ns, grid = 1e-12, 56, 0, None
+    elif case == "maxwellian":
+        w = W.maxwellian(2, 3, 24, a_rho=0.3, a_u=0.2, a_T=0.25)
+        eps, cap, ns, grid = 1e-6, 48, 20000, None
+    elif case == "split":
+        w = dict(W.CONFIGS["hilbert6d_n64"])
+        eps, cap, ns, grid = w["eps"], w["max_rank"], w["nsamples"], w["grid"]
+        kw = dict(residual="stored", precision="split")
+    else:
+        w = W.PAPER_WORKLOADS["paper_hilbert6d_n300"]
+        eps, cap, ns, grid = 0.0, max(w["bond_ranks"]), 10**5, w["grid"]
+        kw = dict(residual="stored", bond_max_rank=w["bond_ranks"])
+    g = tt.TTCross(w["n"], w["gen"], max_rank=cap, nsamples=ns, **kw)
+    g.run(eps, subtensor_grid=grid)
+    rc = g.sync(allow=(tt.OK, tt.NOT_CONVERGED))
+    ref = g.cores()
+    g.rebuild_cores()
+    st = g.stats()
+    assert st["rebuild_ms"] > 0
+    for k, (a, b) in enumerate(zip(g.cores(), ref), start=1):
+        np.testing.assert_array_equal(a, b, err_msg=f"core {k}")
+    g.run(eps, subtensor_grid=grid)
+    assert g.sync(allow=(tt.OK, tt.NOT_CONVERGED)) == rc
+    for a, b in zip(g.cores(), ref):
+        np.testing.assert_array_equal(a, b)
+    print(f"{case}: cores rebuilt from the pivots in {st['rebuild_ms']:.3f} ms")
