@@ -1216,6 +1216,14 @@ __device__ __noinline__ void screen_carried_warp(const InstDev &in, int b, int64
   const int64_t sb = in.stride[b], sb1 = in.stride[b + 1];
   const int64_t lp = lane == 0 ? left_set(in, b).lin[p] : 0;
   const int64_t rq = lane == 1 ? right_set(in, b).lin[q] : 0;
+  // every row of the tile is requested into L2 before the first round's
+  // loads: the rounds then wait for L2, not for DRAM, and the tile's whole
+  // DRAM traffic is in flight at once
+  for (int rr = 0; rr < nr; ++rr)
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+      if (lane + 32 * k < nc)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(B.E + (r0 + rr) * ld + c0 + lane + 32 * k));
   VT wa[NC], er[NC];
   bool cok[NC];
 #pragma unroll
