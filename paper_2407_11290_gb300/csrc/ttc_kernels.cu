@@ -81,6 +81,10 @@ struct DecideSmem {
   int32_t rr[NT / 32], rc[NT / 32];
   double delta;
   int32_t flag;
+  // the eight warps' top candidates of the mixed stored decide
+  uint64_t wk[NT / 32 * 8];
+  int64_t wl[NT / 32 * 8];
+  int32_t wr[NT / 32 * 8], wc[NT / 32 * 8];
 };
 
 constexpr int SPREAD_MAXSM = 1024;
@@ -1216,14 +1220,6 @@ __device__ __noinline__ void screen_carried_warp(const InstDev &in, int b, int64
   const int64_t sb = in.stride[b], sb1 = in.stride[b + 1];
   const int64_t lp = lane == 0 ? left_set(in, b).lin[p] : 0;
   const int64_t rq = lane == 1 ? right_set(in, b).lin[q] : 0;
-  // every row of the tile is requested into L2 before the first round's
-  // loads: the rounds then wait for L2, not for DRAM, and the tile's whole
-  // DRAM traffic is in flight at once
-  for (int rr = 0; rr < nr; ++rr)
-#pragma unroll
-    for (int k = 0; k < NC; ++k)
-      if (lane + 32 * k < nc)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(B.E + (r0 + rr) * ld + c0 + lane + 32 * k));
   VT wa[NC], er[NC];
   bool cok[NC];
 #pragma unroll
@@ -1837,8 +1833,71 @@ __device__ void decide_bond_fp64(const InstDev &in, Ctrl &cr, int b, DecideSmem 
 // (same tie rule) is the candidate of the stop test.  One pass over the slots: every thread keeps
 // its own k best, then k block reductions over the threads' list heads.
 constexpr int RS_K = 8;  // candidates re-scored per bond in the mixed stored form
-__device__ void decide_bond_rescore(const InstDev &in, Ctrl &cr, int b, DecideSmem &sm) {
-  const int tid = threadIdx.x;
+
+// The k best (k <= RS_K) of the lanes' sorted lists loc[0..L-1]: k rounds of
+// a butterfly argmax of the list heads, the winning lane popping its head;
+// lane j < k returns the j-th (the others an empty candidate).
+template <int L>
+__device__ KeyBest warp_topk(KeyBest (&loc)[L], int k) {
+  const int lane = threadIdx.x & 31;
+  KeyBest mine{0ull, LLONG_MAX, -1, -1};
+  for (int j = 0; j < k; ++j) {
+    KeyBest w = loc[0];
+    for (int off = 16; off > 0; off >>= 1) {
+      KeyBest o;
+      o.key = __shfl_xor_sync(0xffffffffu, w.key, off);
+      o.lin = __shfl_xor_sync(0xffffffffu, w.lin, off);
+      o.row = __shfl_xor_sync(0xffffffffu, w.row, off);
+      o.col = __shfl_xor_sync(0xffffffffu, w.col, off);
+      if (o.row >= 0 && (w.row < 0 || key_better(o.key, o.lin, w.key, w.lin))) w = o;
+    }
+    if (lane == j) mine = w;
+    if (w.row >= 0 && loc[0].row == w.row && loc[0].col == w.col) {
+#pragma unroll
+      for (int q = 0; q + 1 < L; ++q) loc[q] = loc[q + 1];
+      loc[L - 1] = KeyBest{0ull, LLONG_MAX, -1, -1};
+    }
+  }
+  return mine;
+}
+
+// FP64 residual A - chain(T(a,:), R(:,c)) of entry (a, c) of bond b by one
+// warp: the lanes load the K terms at once, the chain runs in its serial
+// order from broadcasts (every lane returns the value)
+__device__ __noinline__ double residual_warp(const InstDev &in, int b, int K, int64_t a, int64_t c) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const BondDev &B = in.bond[b];
+  const int lane = threadIdx.x & 31;
+  double tv[RCAP / 32], rv[RCAP / 32];
+#pragma unroll
+  for (int m = 0; m < RCAP / 32; ++m) {
+    const int t = 32 * m + lane;
+    tv[m] = t < K ? B.T[(int64_t)t * B.ldT + a] : 0.0;
+    rv[m] = t < K ? B.R[(int64_t)t * B.ldR + c] : 0.0;
+  }
+  const double A = lane == 0 ? sb_entry(in, b, a, c) : 0.0;
+  double acc = 0.0;
+#pragma unroll
+  for (int m = 0; m < RCAP / 32; ++m) {
+    if (32 * m >= K) break;
+    const int lim = min(32, K - 32 * m);
+    for (int u = 0; u < lim; ++u)
+      acc = __fma_rn(__shfl_sync(FULL, tv[m], u), __shfl_sync(FULL, rv[m], u), acc);
+  }
+  return __dsub_rn(__shfl_sync(FULL, A, 0), acc);
+}
+
+// Mixed stored form, decide item of bond b: the tile candidates hold the
+// best stored |E| of each tile, where the entries new to the superblock were
+// formed on the FP32 pipe.  The top-k of them (by stored |E|, ties to the
+// lowest linear index; k = topk, at most RS_K) are re-scored in FP64 as
+// A - chain(T(a,:), R(:,c)) with the current factors, and the best FP64 value
+// (same tie rule) is the candidate of the stop test.  Every thread keeps its
+// own k best in one pass over the slots; each warp merges its lanes' lists,
+// one warp the warps' lists; a warp per candidate re-scores.
+__device__ __noinline__ void decide_bond_rescore(const InstDev &in, Ctrl &cr, int b,
+                                                DecideSmem &sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) sm.q_nt = ld_cg(cr.ntiles[b]);
   if (tid == 1) sm.q_r = ld_cg(cr.r[b]);
   if (tid == 2) sm.q_tau = ld_cg(cr.tau);
@@ -1861,9 +1920,16 @@ __device__ void decide_bond_rescore(const InstDev &in, Ctrl &cr, int b, DecideSm
   for (int j = 0; j < RS_K; ++j) loc[j] = KeyBest{0ull, LLONG_MAX, -1, -1};
   int bad = 0;
   for (int64_t t = tid; t < nt; t += NT) {
-    KeyBest o{cand[t].key, cand[t].lin, cand[t].row, cand[t].col};
-    bad += o.row == -1;
-    if (o.row < 0) continue;
+    const uint64_t key = cand[t].key;
+    const int64_t lin = cand[t].lin;
+    const int32_t row = cand[t].row;
+    bad += row == -1;
+    if (row < 0) continue;
+    // most slots lose to the list's last entry: one comparison
+    if (k == RS_K && loc[RS_K - 1].row >= 0 &&
+        !key_better(key, lin, loc[RS_K - 1].key, loc[RS_K - 1].lin))
+      continue;
+    KeyBest o{key, lin, row, cand[t].col};
     // insertion into the sorted list loc[0..k-1]
 #pragma unroll
     for (int j = 0; j < RS_K; ++j) {
@@ -1877,27 +1943,41 @@ __device__ void decide_bond_rescore(const InstDev &in, Ctrl &cr, int b, DecideSm
     }
   }
   if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
-  for (int j = 0; j < k; ++j) {
-    const KeyBest win = block_best(loc[0], sm.rk, sm.rl, sm.rr, sm.rc);
-    if (tid == 0) {
-      sm.skey[j] = win.key;
-      sm.slin[j] = win.lin;
-      sm.srow[j] = win.row;
-      sm.scol[j] = win.col;
-    }
-    __syncthreads();
-    if (loc[0].row >= 0 && loc[0].row == sm.srow[j] && loc[0].col == sm.scol[j]) {
+  // the warps' k best, then the CTA's k best by warp 0
+  const KeyBest wb = warp_topk<RS_K>(loc, k);
+  if (lane < RS_K) {
+    sm.wk[warp * RS_K + lane] = wb.key;
+    sm.wl[warp * RS_K + lane] = wb.lin;
+    sm.wr[warp * RS_K + lane] = wb.row;
+    sm.wc[warp * RS_K + lane] = wb.col;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    KeyBest l2[2];
 #pragma unroll
-      for (int q = 0; q + 1 < RS_K; ++q) loc[q] = loc[q + 1];
-      loc[RS_K - 1] = KeyBest{0ull, LLONG_MAX, -1, -1};
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      l2[h] = i < NT / 32 * RS_K ? KeyBest{sm.wk[i], sm.wl[i], sm.wr[i], sm.wc[i]}
+                                 : KeyBest{0ull, LLONG_MAX, -1, -1};
+    }
+    if (l2[1].row >= 0 && (l2[0].row < 0 || key_better(l2[1].key, l2[1].lin, l2[0].key, l2[0].lin))) {
+      const KeyBest tmp = l2[0];
+      l2[0] = l2[1];
+      l2[1] = tmp;
+    }
+    const KeyBest g = warp_topk<2>(l2, k);
+    if (lane < k) {
+      sm.skey[lane] = g.key;
+      sm.slin[lane] = g.lin;
+      sm.srow[lane] = g.row;
+      sm.scol[lane] = g.col;
     }
   }
-  // FP64 re-score of the k candidates, one thread each
-  const BondDev &B = in.bond[b];
-  if (tid < k && sm.srow[tid] >= 0) {
-    const int64_t a = sm.srow[tid], c = sm.scol[tid];
-    const double e = __dsub_rn(sb_entry(in, b, a, c), chain(B.T + a, B.ldT, B.R + c, B.ldR, sm.q_r));
-    sm.skey[tid] = abs_key(e);
+  __syncthreads();
+  // FP64 re-score of the k candidates, a warp each
+  if (warp < k && sm.srow[warp] >= 0) {
+    const double e = residual_warp(in, b, sm.q_r, sm.srow[warp], sm.scol[warp]);
+    if (lane == 0) sm.skey[warp] = abs_key(e);
   }
   __syncthreads();
   if (tid == 0) {
