@@ -308,13 +308,15 @@ ttc_status ttcross_destroy(ttc_handle *h);
    Hilbert or Maxwellian generator *gen (TTC_GEN_TT is rejected: it would need
    device data) and X~ the TT whose core m (0-based) is the device array
    cores[m] laid out [s_m][n_m][s_{m+1}] row-major, as ttcross_get_cores
-   writes it (s: host array of d+1 sizes, s_0 = s_d = 1, s_m <= 128).
+   writes it (s: host array of d+1 sizes, s_0 = s_d = 1, s_m <= 256).
    The result is written to *err, a caller-owned device double, in stream
    order on `stream`; the call returns after enqueueing two kernels.
    Scratch: a static 64 KiB device array per GPU holds one partial sum per
    chunk of 4096 samples, so nsamples is limited to 16,777,216 (larger
    requests return TTC_ERR_INVALID_ARG).  The first call on a device looks up
-   that array's address; make it before any stream capture.  Every call uses
+   that array's address; make it before any stream capture.  Calls outside a
+   capture look it up again, so a call after cudaDeviceReset (which reloads
+   the module) finds the array where it now is.  Every call uses
    the same array and overwrites what it reads, so calls whose kernels may
    overlap on the GPU (other streams or host threads) race and must be
    ordered by the caller.  No cudaMalloc, cudaFree or allocating library call
