@@ -224,8 +224,16 @@ __device__ __forceinline__ bool key_better(uint64_t k1, int64_t l1, uint64_t k2,
   return k1 > k2 || (k1 == k2 && l1 < l2);
 }
 
+// The bits of |e| (the order of the keys is the order of |e|), formed by an
+// integer AND on the high word.  Written as a 64-bit mask the compiler may
+// take the FP64 pipe for it (an add with an absolute-value operand); that
+// pipe runs about two FMAs per clock per SM here and is the screens' binding
+// resource, so the key stays on the integer pipe.
 __device__ __forceinline__ uint64_t abs_key(double e) {
-  return (uint64_t)__double_as_longlong(e) & 0x7FFFFFFFFFFFFFFFull;
+  uint32_t lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(e));
+  asm("and.b32 %0, %0, 0x7FFFFFFF;" : "+r"(hi));
+  return ((uint64_t)hi << 32) | lo;
 }
 // +Inf bit pattern: keys above it are NaN
 constexpr uint64_t KEY_INF = 0x7FF0000000000000ull;
