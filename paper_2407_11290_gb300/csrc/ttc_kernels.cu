@@ -557,15 +557,14 @@ __device__ __forceinline__ void tile_chain_fp64(const BondDev &B, int K, int64_t
 // screen).  SPLIT: float-float, th rh = p + pe exactly (pe by FMA), the cross
 // terms th rl + tl rh and pe join the low word, the high word is summed by
 // TwoSum and the pair renormalised every term, so the result carries about
-// 44 bits; else plain FP32 products and sums.  The pair is returned as one
-// FP64 value (hi + lo).
+// 44 bits; else plain FP32 products and sums (sl = 0).  The result is the
+// pair (sh, sl).
 template <int TE, bool SPLIT>
 __device__ __forceinline__ void tile_chain_ff(const BondDev &B, int K, int64_t r0, int nr,
-                                              int64_t c0, int nc,
-                                              double (&acc)[TE / 16][TE / 16], ScreenSmem &sm) {
+                                              int64_t c0, int nc, float (&sh)[TE / 16][TE / 16],
+                                              float (&sl)[TE / 16][TE / 16], ScreenSmem &sm) {
   constexpr int U = TE / 16;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float sh[U][U], sl[U][U];
 #pragma unroll
   for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -636,10 +635,19 @@ __device__ __forceinline__ void tile_chain_ff(const BondDev &B, int K, int64_t r
         }
     }
   }
-#pragma unroll
-  for (int u = 0; u < U; ++u)
-#pragma unroll
-    for (int v = 0; v < U; ++v) acc[u][v] = __dadd_rn((double)sh[u][v], (double)sl[u][v]);
+}
+
+// (ah + al) - (bh + bl) as a normalised float-float pair: TwoSum of the high
+// words, the low words' difference joins the rounding error, one fast
+// renormalisation (11 FP32 operations, no FP64 pipe).  The error is a few
+// units of 2^-48 (|a| + |b|), below the chain's own.
+__device__ __forceinline__ float2 ff_sub(float ah, float al, float bh, float bl) {
+  const float s = __fsub_rn(ah, bh);
+  const float v = __fsub_rn(s, ah);
+  const float e = __fsub_rn(__fsub_rn(ah, __fsub_rn(s, v)), __fadd_rn(bh, v));
+  const float t = __fadd_rn(e, __fsub_rn(al, bl));
+  const float hi = __fadd_rn(s, t);
+  return make_float2(hi, __fsub_rn(t, __fsub_rn(hi, s)));
 }
 
 template <bool HIL, int TE>
@@ -825,11 +833,14 @@ __device__ __noinline__ void screen_tile_stored_t(const InstDev &in, int b, int 
     }
     __syncthreads();  // publishes the tile metadata
   } else {
-    double acc[U][U];
-    if (MIX == 0)
+    // FP64: acc; mixed: the float-float pair (fh, fl), and E = A - T R is
+    // formed in float-float too, so the mixed path leaves the FP64 pipe alone
+    double acc[MIX == 0 ? U : 1][MIX == 0 ? U : 1];
+    float fh[MIX == 0 ? 1 : U][MIX == 0 ? 1 : U], fl[MIX == 0 ? 1 : U][MIX == 0 ? 1 : U];
+    if constexpr (MIX == 0)
       tile_chain_fp64<TE>(B, K, r0, nr, c0, nc, acc, sm);
     else
-      tile_chain_ff<TE, MIX == 2>(B, K, r0, nr, c0, nc, acc, sm);
+      tile_chain_ff<TE, MIX == 2>(B, K, r0, nr, c0, nc, fh, fl, sm);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int rr = ty + 16 * u;
@@ -848,10 +859,19 @@ __device__ __noinline__ void screen_tile_stored_t(const InstDev &in, int b, int 
         if (arow && c < sc) {
           e = V::load(B.E, a * ld + c);
           if (pend) e = V::step(wa, V::load(B.erow, c), e);
-        } else {
+        } else if constexpr (MIX == 0) {
           const double A =
               HIL ? in.hilb[sm.srow[rr] + sm.scol[cc]] : tile_entry(in, sm, wl, wr, rr, cc);
-          e = V::from(__dsub_rn(A, acc[u][v]));
+          e = __dsub_rn(A, acc[u][v]);
+        } else {
+          float ah, al;
+          if (HIL) {
+            ah = in.hilb_hi[sm.srow[rr] + sm.scol[cc]];
+            al = in.hilb_lo[sm.srow[rr] + sm.scol[cc]];
+          } else {
+            split2(tile_entry(in, sm, wl, wr, rr, cc), ah, al);
+          }
+          e = ff_sub(ah, al, fh[u][v], fl[u][v]);
         }
         V::store(B.E, a * ld + c, e);
         ev[u][v] = e;
