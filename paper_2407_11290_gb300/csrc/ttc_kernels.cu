@@ -1251,7 +1251,10 @@ __device__ __noinline__ void screen_carried_warp(const InstDev &in, int b, int64
   uint64_t bk = 0;
   int64_t bl = LLONG_MAX;
   int brr = -1, bcc = 0;
-#pragma unroll
+  // mixed forms: the rounds stay a loop; unrolled, their float-float steps
+  // make a body large enough to compete for the instruction cache with the
+  // fresh tiles of the SM's other CTA (the FP64 body is small)
+#pragma unroll(MIX == 0 ? TE / RR : 1)
   for (int r1 = 0; r1 < TE; r1 += RR) {
     VT ev[RR][NC];
 #pragma unroll
@@ -1824,9 +1827,24 @@ __device__ void decide_bond_fp64(const InstDev &in, Ctrl &cr, int b, DecideSmem 
   KeyBest best{0ull, LLONG_MAX, -1, -1};
   const Cand *cand = in.cand + in.bond[b].cand_base;
   int bad = 0;
-  for (int64_t t = tid; t < nt; t += NT) {
+  // four slots' loads in flight before their compares
+  int64_t t = tid;
+  for (; t + 3 * NT < nt; t += 4 * NT) {
+    KeyBest o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const Cand &c = cand[t + u * NT];
+      o[u] = KeyBest{c.key, c.lin, c.row, c.col};
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      bad += o[u].row == -1;  // -2 marks a slot left empty on purpose
+      kb_take(best, o[u]);
+    }
+  }
+  for (; t < nt; t += NT) {
     KeyBest o{cand[t].key, cand[t].lin, cand[t].row, cand[t].col};
-    bad += o.row == -1;  // -2 marks a slot left empty on purpose
+    bad += o.row == -1;
     kb_take(best, o);
   }
   if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
