@@ -90,7 +90,7 @@ struct DecideSmem {
 constexpr int SPREAD_MAXSM = 1024;
 struct SpreadSmem {
   int32_t cnt[SPREAD_MAXSM];  // CTAs per SM id
-  int32_t k, place, bad;
+  int32_t k, place, bad, nsm, not2;
 };
 
 // replays of up to 32 pivots (Alg. 4): the history triangles (row z at
@@ -132,6 +132,9 @@ __shared__ InstDev s_inst0;
 // items (pivot steps, replays) then do not queue for the FP64 pipe, which
 // is shared by the whole SM.  blockIdx.x until the order is known.
 __shared__ int32_t s_place;
+// S when the grid holds exactly two CTAs on each of S SMs (then places p and
+// p + S share an SM), else 0 (not known, or another layout)
+__shared__ int32_t s_sm2;
 // grid barriers this CTA has passed in the running launch
 __shared__ uint32_t s_bar_epoch;
 
@@ -139,6 +142,7 @@ __device__ void cache_inst0(const RunArgs &ra) {
   static_assert(sizeof(InstDev) % 8 == 0, "InstDev copies as 8-byte words");
   if (threadIdx.x == 0) {
     s_place = blockIdx.x;
+    s_sm2 = 0;
     s_bar_epoch = 0u;
   }
   const unsigned long long *src = reinterpret_cast<const unsigned long long *>(ra.insts[0]);
@@ -2652,6 +2656,56 @@ __device__ void stage_history(const BondDev &B, int nz, int nw, ReplaySmem &rs) 
   asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
 }
 
+// Alg. 4 replay of up to 32 rows of bond b at once, a row per lane: lane l
+// rebuilds T(a0 + l, 0..nz-1) from the pivot history (R(:, c_z) and T(a_z, :)
+// of every step z, delta_z) by the steps of update_row, the same FMAs in the
+// same order, its row in local memory.  A chain instruction then serves 32
+// rows: the FP64 unit, shared by the SM's warps at two FMAs per clock (an
+// instruction costs it 16 cycles whatever lanes are active), takes 1/32 of
+// the issue of a warp per row.  st: the history staged in shared memory;
+// nz <= LANE_NZ.
+__device__ __noinline__ void replay_rows_lane(const InstDev &in, int b, int64_t a0, int nrows,
+                                              int nz, const ReplaySmem *st) {
+  const BondDev &B = in.bond[b];
+  const int lane = threadIdx.x & 31;
+  const int64_t a = a0 + min(lane, nrows - 1);
+  const double *hcb = st->hc, *hpb = st->hp, *dlb = st->delta;
+  double tr[LANE_NZ], en[LANE_NZ];  // nz <= LANE_NZ (the staged histories)
+  // the row's entries at the pivot columns, gathered before the steps
+  if (in.gen == 0) {
+    const int64_t nb0 = in.n[b];
+    const int64_t p = a / nb0, i = a - p * nb0;
+    const int32_t rs = left_set(in, b).sum[p] + (int32_t)i;
+    for (int z = 0; z < nz; ++z) en[z] = in.hilb[rs + B.J.sum[z]];
+  } else {
+    for (int z = 0; z < nz; ++z) en[z] = sb_entry(in, b, a, B.pcol[z]);
+  }
+  for (int z = 0; z < nz; ++z) {
+    const int o = z * (z - 1) / 2;  // row z of the staged triangles
+    const double *hc = hcb + o, *hp = hpb + o;
+    const double ez = en[z];
+    const double dz = dlb[z];
+    double acc = 0.0;
+    int t = 0;
+    for (; t + 4 <= z; t += 4) {
+      double x[4], y[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        x[k] = tr[t + k];
+        y[k] = hc[t + k];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc = __fma_rn(x[k], y[k], acc);
+    }
+    for (; t < z; ++t) acc = __fma_rn(tr[t], hc[t], acc);
+    const double w = __dmul_rn(dz, __dsub_rn(acc, ez));
+    for (t = 0; t < z; ++t) tr[t] = __fma_rn(w, hp[t], tr[t]);
+    tr[z] = -w;
+  }
+  if (lane < nrows)
+    for (int t = 0; t < nz; ++t) putT(in, B, (int64_t)t * B.ldT + a, tr[t]);
+}
+
 // the replays of the n_b rows that the new prefix of bond b-1 adds to bond b:
 // chunks of W <= 8 rows, a row per warp (warps 0..W-1; W <= 4 keeps one per
 // SMSP, the smallest W that gives every row a warp is taken), chunk
@@ -3084,18 +3138,66 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
       if (nadd > 0) write_plan_warp(in, *in.ctrl, rn, gridDim.x);  // next screen's tiles
     }
     if (nadd > 0) {
-      // C first: the replays are the longest items; the thread-dealt items
-      // start on the place after the last replay chunk
-      int32_t cbase = (int32_t)((base / NT) % gridDim.x);
-      int64_t nchunks = 0, rrows = 0;
+      // the replays are the longest items.  One instance on a grid of two
+      // CTAs per SM: the replays go a row per lane to warps 0..RW-1 of the
+      // first places (distinct SMs, at most a quarter of them), whose SMs
+      // take no other item, so that their dependent FP64 chains do not
+      // queue behind other warps' FP64 work on the SM's shared unit; the
+      // thread-dealt items go to the other places.  Otherwise a row per
+      // warp, and the thread-dealt items start on the place after the last
+      // replay chunk.
+      const int32_t S = s_sm2;
+      int64_t lch = 0;
       for (int b = 1; b < in.nb; ++b)
-        if (ad[b - 1]) rrows += in.n[b];
-      const int W = (int)min((int64_t)(NT / 32), max((int64_t)1, (rrows + gridDim.x - 1) / gridDim.x));
-      for (int b = 1; b < in.nb; ++b) {
-        if (!ad[b - 1]) continue;
-        nchunks += replay_chunks(in, b, ro[b - 1], rn[b], cbase, W, sm.rp);
+        if (ad[b - 1]) lch += (in.n[b] + 31) / 32;
+      const int32_t RW = (int32_t)min((int64_t)4, (lch + (S / 4) - 1) / max(1, S / 4));
+      const int32_t nsr = RW > 0 ? (int32_t)((lch + RW - 1) / RW) : 0;  // replay SMs
+      bool small = true;  // every replayed history fits the staging (rank <= LANE_NZ)
+      for (int b = 1; b < in.nb; ++b)
+        if (ad[b - 1] && rn[b] > LANE_NZ) small = false;
+      const bool iso = ra.count == 1 && S > 0 && (int32_t)gridDim.x == 2 * S && lch > 0 &&
+                       RW == 1 && nsr <= S / 4 && 2 * nsr < (int32_t)gridDim.x && small;
+      int64_t gti = gt, NTI = NTOT;
+      bool idle = false;  // a thread of a replay SM: no thread-dealt item
+      if (iso) {
+        const int32_t pl = s_place;
+        const bool rsm = pl < nsr || (pl >= S && pl < S + nsr);
+        idle = rsm;
+        if (pl < nsr && (threadIdx.x >> 5) == 0) {
+          // replay chunk g = pl of this SM (bonds in order), by warp 0 from
+          // the history staged in shared memory
+          const int64_t g = pl;
+          int64_t first = 0;
+          for (int b = 1; b < in.nb && g >= first; ++b) {
+            if (!ad[b - 1]) continue;
+            const int64_t nc = (in.n[b] + 31) / 32;
+            if (g < first + nc) {
+              const int64_t i0 = (g - first) * 32;
+              stage_history(in.bond[b], rn[b], 1, sm.rp);
+              replay_rows_lane(in, b, (int64_t)ro[b - 1] * in.n[b] + i0,
+                               (int)min((int64_t)32, in.n[b] - i0), rn[b], &sm.rp);
+            }
+            first += nc;
+          }
+        }
+        // item threads: the places of the other SMs, renumbered from 0
+        NTI = (int64_t)(gridDim.x - 2 * nsr) * NT;
+        gti = rsm ? 0 : (int64_t)(pl < S ? pl - nsr : pl - 2 * nsr) * NT + threadIdx.x;
+      } else {
+        int32_t cbase = (int32_t)((base / NT) % gridDim.x);
+        int64_t nchunks = 0, rrows = 0;
+        for (int b = 1; b < in.nb; ++b)
+          if (ad[b - 1]) rrows += in.n[b];
+        const int W = (int)min((int64_t)(NT / 32), max((int64_t)1, (rrows + gridDim.x - 1) / gridDim.x));
+        for (int b = 1; b < in.nb; ++b) {
+          if (!ad[b - 1]) continue;
+          nchunks += replay_chunks(in, b, ro[b - 1], rn[b], cbase, W, sm.rp);
+        }
+        base += nchunks * NT;
       }
-      base += nchunks * NT;
+      auto item0 = [&](int64_t bs) -> int64_t {
+        return idle ? LLONG_MAX : first_item(bs, gti, NTI);
+      };
       for (int b = 0; b < in.nb; ++b) {
         const BondDev &B = in.bond[b];
         // a thread with no item of this bond skips it whole: no load of the
@@ -3104,7 +3206,7 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
           const int64_t rc = ad[b] ? rows_of(in, ro, b) + cols_of(in, ro, b) : 0;
           const int64_t tot = (in.stored ? 2 : 1) * rc +
                               (b < in.nb - 1 && ad[b + 1] ? (int64_t)rn[b] * in.n[b + 1] : 0);
-          if (first_item(base, gt, NTOT) >= base + tot) {
+          if (item0(base) >= base + tot) {
             base += tot;
             continue;
           }
@@ -3114,21 +3216,21 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
           // sweep-start superblock, which E still holds)
           const int64_t rows = rows_of(in, ro, b), cols = cols_of(in, ro, b);
           const int64_t ld = B.ldR, as = B.prow[ro[b]], cs = B.pcol[ro[b]];
-          for (int64_t x = first_item(base, gt, NTOT); x < base + rows; x += NTOT)
+          for (int64_t x = item0(base); x < base + rows; x += NTI)
             sv_put(in, B.ew, x - base,
                    -(sv_get(in, B.E, (x - base) * ld + cs) / sv_get(in, B.E, as * ld + cs)));
           base += rows;
-          for (int64_t x = first_item(base, gt, NTOT); x < base + cols; x += NTOT)
+          for (int64_t x = item0(base); x < base + cols; x += NTI)
             B.erow[x - base] = B.E[as * ld + (x - base)];  // the same 8 bytes in either form
           base += cols;
         }
         if (ad[b]) {
           const int z = ro[b];
           const int64_t rows = rows_of(in, ro, b), cols = cols_of(in, ro, b);
-          for (int64_t x = first_item(base, gt, NTOT); x < base + rows; x += NTOT)
+          for (int64_t x = item0(base); x < base + rows; x += NTI)
             update_row(in, b, x - base, z);
           base += rows;
-          for (int64_t x = first_item(base, gt, NTOT); x < base + cols; x += NTOT)
+          for (int64_t x = item0(base); x < base + cols; x += NTI)
             putR(in, B, (int64_t)z * B.ldR + (x - base), sb_entry(in, b, B.prow[z], x - base));
           base += cols;
         }
@@ -3136,7 +3238,7 @@ __device__ void phase_update(const RunArgs &ra, PhaseSmem &sm) {
           const int64_t nb1 = in.n[b + 1];
           const int64_t q = ro[b + 1];
           const int64_t nit = (int64_t)rn[b] * nb1;
-          for (int64_t x = first_item(base, gt, NTOT); x < base + nit; x += NTOT) {
+          for (int64_t x = item0(base); x < base + nit; x += NTI) {
             const int64_t l = x - base, t = l / nb1, jj = l - t * nb1;
             const int64_t c = q * nb1 + jj;
             putR(in, B, t * B.ldR + c, sb_entry(in, b, B.prow[t], c));
@@ -3429,6 +3531,8 @@ __device__ void spread_order(const RunArgs &ra, PhaseSmem &sm) {
     sp.k = 0;
     sp.place = 0;
     sp.bad = me >= SPREAD_MAXSM;
+    sp.nsm = 0;
+    sp.not2 = 0;
   }
   __syncthreads();
   int k = 0;
@@ -3443,14 +3547,21 @@ __device__ void spread_order(const RunArgs &ra, PhaseSmem &sm) {
   if (k) atomicAdd(&sp.k, k);
   __syncthreads();
   const int kk = sp.k;
-  int part = 0;
+  int part = 0, used = 0, odd = 0;
   for (int s = threadIdx.x; s < SPREAD_MAXSM; s += NT) {
     const int c = sp.cnt[s];
     part += min(c, kk) + (s < me && c > kk);
+    used += c > 0;
+    odd += c != 0 && c != 2;
   }
   if (part) atomicAdd(&sp.place, part);
+  if (used) atomicAdd(&sp.nsm, used);
+  if (odd) atomicAdd(&sp.not2, odd);
   __syncthreads();
-  if (threadIdx.x == 0) s_place = sp.bad ? (int32_t)blockIdx.x : sp.place;
+  if (threadIdx.x == 0) {
+    s_place = sp.bad ? (int32_t)blockIdx.x : sp.place;
+    s_sm2 = (sp.bad || sp.not2) ? 0 : sp.nsm;
+  }
   __syncthreads();
 }
 
