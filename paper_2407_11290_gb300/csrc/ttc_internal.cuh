@@ -100,6 +100,9 @@ struct Ctrl {
   // running round moved the pivot
   int32_t rook_stage[TTC_MAXD], rook_round[TTC_MAXD], rook_moved[TTC_MAXD];
   int64_t screen_t;          // sampled screen: screens run (the sample counter)
+  int32_t dcount[TTC_MAXD];  // stored forms: parts of bond b's decide that have
+                             // merged their share of the tile slots (the last
+                             // one finishes the bond and clears it)
   int32_t dkind;             // work of the coming decide phases, fixed by the
                              // screen phase: DK_BONDS, DK_VERIFY or DK_NONE
   int32_t pad_dkind;

@@ -85,6 +85,10 @@ struct DecideSmem {
   uint64_t wk[NT / 32 * 8];
   int64_t wl[NT / 32 * 8];
   int32_t wr[NT / 32 * 8], wc[NT / 32 * 8];
+  // keys and indices of up to 2 NT slots ranked at once (stored decide)
+  uint64_t tk[2 * NT];
+  int64_t tl[2 * NT];
+  int32_t last;  // this CTA finishes the bond's decide
 };
 
 constexpr int SPREAD_MAXSM = 1024;
@@ -1867,13 +1871,6 @@ __device__ void decide_bond_fp64(const InstDev &in, Ctrl &cr, int b, DecideSmem 
                   sm.q_maxr);
 }
 
-// Mixed stored form, decide item of bond b: the tile candidates hold the
-// best stored |E| of each tile, where the entries new to the superblock were
-// formed on the FP32 pipe.  The top-k of them (by stored |E|, ties to the
-// lowest linear index; k = topk, at most RS_K) are re-scored in FP64 as
-// A - chain(T(a,:), R(:,c)) with the current factors, and the best FP64 value
-// (same tie rule) is the candidate of the stop test.  One pass over the slots: every thread keeps
-// its own k best, then k block reductions over the threads' list heads.
 constexpr int RS_K = 8;  // candidates re-scored per bond in the mixed stored form
 
 // The k best (k <= RS_K) of the lanes' sorted lists loc[0..L-1]: k rounds of
@@ -1903,75 +1900,66 @@ __device__ KeyBest warp_topk(KeyBest (&loc)[L], int k) {
   return mine;
 }
 
-// FP64 residual A - chain(T(a,:), R(:,c)) of entry (a, c) of bond b by one
-// warp: the lanes load the K terms at once, the chain runs in its serial
-// order from broadcasts (every lane returns the value)
-__device__ __noinline__ double residual_warp(const InstDev &in, int b, int K, int64_t a, int64_t c) {
-  constexpr unsigned FULL = 0xffffffffu;
-  const BondDev &B = in.bond[b];
-  const int lane = threadIdx.x & 31;
-  double tv[RCAP / 32], rv[RCAP / 32];
-#pragma unroll
-  for (int m = 0; m < RCAP / 32; ++m) {
-    const int t = 32 * m + lane;
-    tv[m] = t < K ? B.T[(int64_t)t * B.ldT + a] : 0.0;
-    rv[m] = t < K ? B.R[(int64_t)t * B.ldR + c] : 0.0;
-  }
-  const double A = lane == 0 ? sb_entry(in, b, a, c) : 0.0;
-  double acc = 0.0;
-#pragma unroll
-  for (int m = 0; m < RCAP / 32; ++m) {
-    if (32 * m >= K) break;
-    const int lim = min(32, K - 32 * m);
-    for (int u = 0; u < lim; ++u)
-      acc = __fma_rn(__shfl_sync(FULL, tv[m], u), __shfl_sync(FULL, rv[m], u), acc);
-  }
-  return __dsub_rn(__shfl_sync(FULL, A, 0), acc);
+// a candidate slot read through L2 (other SMs wrote it in this launch)
+__device__ __forceinline__ Cand ld_cand(const Cand *p) {
+  Cand c;
+  c.key = __ldcg(&p->key);
+  c.lin = __ldcg(&p->lin);
+  const int2 rc = __ldcg(reinterpret_cast<const int2 *>(&p->row));
+  c.row = rc.x;
+  c.col = rc.y;
+  return c;
 }
 
-// Mixed stored form, decide item of bond b: the tile candidates hold the
-// best stored |E| of each tile, where the entries new to the superblock were
-// formed on the FP32 pipe.  The top-k of them (by stored |E|, ties to the
-// lowest linear index; k = topk, at most RS_K) are re-scored in FP64 as
-// A - chain(T(a,:), R(:,c)) with the current factors, and the best FP64 value
-// (same tie rule) is the candidate of the stop test.  Every thread keeps its
-// own k best in one pass over the slots; each warp merges its lanes' lists,
-// one warp the warps' lists; a warp per candidate re-scores.
-__device__ __noinline__ void decide_bond_rescore(const InstDev &in, Ctrl &cr, int b,
-                                                DecideSmem &sm) {
+// The k best (k <= RS_K; key, then lowest linear index) of slots [t0, t1)
+// into sm.skey / slin / srow / scol [0, k), missing ones with row -1;
+// block-wide.  Up to 2 NT slots: every slot's rank is the number of better
+// slots (the slots are distinct entries).  More: every thread keeps its own
+// k best in one pass, each warp merges its lanes' lists, one warp the warps'.
+__device__ void topk_of_slots(const Cand *src, int64_t t0, int64_t t1, int k, DecideSmem &sm,
+                              int &bad) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) sm.q_nt = ld_cg(cr.ntiles[b]);
-  if (tid == 1) sm.q_r = ld_cg(cr.r[b]);
-  if (tid == 2) sm.q_tau = ld_cg(cr.tau);
-  if (tid == 3) sm.q_xrms = ld_cg(cr.xrms);
-  if (tid == 4) sm.q_maxr = ld_cg(cr.maxr[b]);
-  if (tid == 5) sm.q_prow = ld_cg(cr.plan_rows[b]);
-  if (tid == 6) sm.q_pcol = ld_cg(cr.plan_cols[b]);
-  __syncthreads();
-  if (tid == 0) {
-    cr.st_rows[b] = sm.q_prow;
-    cr.st_cols[b] = sm.q_pcol;
-    cr.e_pend[b] = 0;
-    if (b == 0) cr.steal = cr.steal2 = 0;
+  const int64_t m = t1 - t0;
+  if (tid < RS_K) sm.srow[tid] = -1;
+  if (m <= 2 * NT) {
+    Cand c[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t i = tid + u * NT;
+      c[u] = i < m ? ld_cand(src + t0 + i) : Cand{0ull, LLONG_MAX, -2, -2};
+      bad += c[u].row == -1;
+      const bool v = c[u].row >= 0;
+      sm.tk[i] = v ? c[u].key : 0ull;
+      sm.tl[i] = v ? c[u].lin : LLONG_MAX;  // never better than a real slot
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (c[u].row < 0) continue;
+      int rank = 0;
+      for (int j = 0; j < (int)m; ++j) rank += key_better(sm.tk[j], sm.tl[j], c[u].key, c[u].lin);
+      if (rank < k) {
+        sm.skey[rank] = c[u].key;
+        sm.slin[rank] = c[u].lin;
+        sm.srow[rank] = c[u].row;
+        sm.scol[rank] = c[u].col;
+      }
+    }
+    __syncthreads();
+    return;
   }
-  const int64_t nt = sm.q_nt;
-  const int k = (int)min((int64_t)min(in.topk, RS_K), nt);
-  const Cand *cand = in.cand + in.bond[b].cand_base;
   KeyBest loc[RS_K];
 #pragma unroll
   for (int j = 0; j < RS_K; ++j) loc[j] = KeyBest{0ull, LLONG_MAX, -1, -1};
-  int bad = 0;
-  for (int64_t t = tid; t < nt; t += NT) {
-    const uint64_t key = cand[t].key;
-    const int64_t lin = cand[t].lin;
-    const int32_t row = cand[t].row;
-    bad += row == -1;
-    if (row < 0) continue;
+  for (int64_t t = t0 + tid; t < t1; t += NT) {
+    const Cand c = ld_cand(src + t);
+    bad += c.row == -1;
+    if (c.row < 0) continue;
     // most slots lose to the list's last entry: one comparison
     if (k == RS_K && loc[RS_K - 1].row >= 0 &&
-        !key_better(key, lin, loc[RS_K - 1].key, loc[RS_K - 1].lin))
+        !key_better(c.key, c.lin, loc[RS_K - 1].key, loc[RS_K - 1].lin))
       continue;
-    KeyBest o{key, lin, row, cand[t].col};
+    KeyBest o{c.key, c.lin, c.row, c.col};
     // insertion into the sorted list loc[0..k-1]
 #pragma unroll
     for (int j = 0; j < RS_K; ++j) {
@@ -1984,9 +1972,8 @@ __device__ __noinline__ void decide_bond_rescore(const InstDev &in, Ctrl &cr, in
       }
     }
   }
-  if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
-  // the warps' k best, then the CTA's k best by warp 0
   const KeyBest wb = warp_topk<RS_K>(loc, k);
+  __syncthreads();  // the srow marks above are written before warp 0's results
   if (lane < RS_K) {
     sm.wk[warp * RS_K + lane] = wb.key;
     sm.wl[warp * RS_K + lane] = wb.lin;
@@ -2016,11 +2003,68 @@ __device__ __noinline__ void decide_bond_rescore(const InstDev &in, Ctrl &cr, in
     }
   }
   __syncthreads();
-  // FP64 re-score of the k candidates, a warp each
-  if (warp < k && sm.srow[warp] >= 0) {
-    const double e = residual_warp(in, b, sm.q_r, sm.srow[warp], sm.scol[warp]);
-    if (lane == 0) sm.skey[warp] = abs_key(e);
+}
+
+// Mixed stored form, decide item (bond b, part of P): the part takes the k
+// best of its share of the tile slots by stored |E| (k = topk, at most RS_K;
+// entries new to the superblock formed on the FP32 pipe) into the bond's
+// partial results, the Allgather of Alg. 3.  The last part to finish takes
+// the k best of the partials, re-scores them in FP64 as A - chain(T(a,:),
+// R(:,c)) with the current factors, and takes the best FP64 value (same tie
+// rule) to the stop test and the pivot step.
+__device__ __noinline__ void decide_bond_rescore(const InstDev &in, Ctrl &cr, int b, int part,
+                                                 int P, DecideSmem &sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = max(1, min(in.topk, RS_K));
+  if (tid == 0) sm.q_nt = ld_cg(cr.ntiles[b]);
+  if (tid == 1) sm.q_r = ld_cg(cr.r[b]);
+  if (tid == 2) sm.q_tau = ld_cg(cr.tau);
+  if (tid == 3) sm.q_xrms = ld_cg(cr.xrms);
+  if (tid == 4) sm.q_maxr = ld_cg(cr.maxr[b]);
+  if (tid == 5) sm.q_prow = ld_cg(cr.plan_rows[b]);
+  if (tid == 6) sm.q_pcol = ld_cg(cr.plan_cols[b]);
+  __syncthreads();
+  const int64_t nt = sm.q_nt, L = (nt + P - 1) / P;
+  const int64_t t0 = min(nt, (int64_t)part * L), t1 = min(nt, t0 + L);
+  const Cand *cand = in.cand + in.bond[b].cand_base;
+  Cand *pb = in.refine_cand + in.bond[b].cand_base;  // the parts' results, [P][k]
+  int bad = 0;
+  topk_of_slots(cand, t0, t1, k, sm, bad);
+  if (P > 1) {
+    if (tid < k)
+      pb[part * k + tid] = sm.srow[tid] >= 0
+                               ? Cand{sm.skey[tid], sm.slin[tid], sm.srow[tid], sm.scol[tid]}
+                               : Cand{0ull, LLONG_MAX, -2, -2};
+    // the last of the P parts to arrive finishes the bond
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();  // the part's results before its arrival
+      sm.last = atomicAdd(&cr.dcount[b], 1) == P - 1;
+      if (sm.last) {
+        cr.dcount[b] = 0;
+        __threadfence();  // the other parts' results after theirs
+      }
+    }
+    __syncthreads();
+    if (!sm.last) {
+      if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
+      return;
+    }
+    topk_of_slots(pb, 0, (int64_t)P * k, k, sm, bad);
   }
+  if (tid == 0) {
+    // the screen just stored every entry of the superblock and applied the
+    // pending rank-one step
+    cr.st_rows[b] = sm.q_prow;
+    cr.st_cols[b] = sm.q_pcol;
+    cr.e_pend[b] = 0;
+    if (b == 0) cr.steal = cr.steal2 = 0;  // item counters of the next screen
+  }
+  if (bad) atomicAdd((unsigned long long *)&cr.unscreened, (unsigned long long)bad);
+  // FP64 re-score of the k candidates, a lane each of warp 0 (the chains run
+  // side by side instead of queueing warps on the SM's FP64 units)
+  if (warp == 0 && lane < k && sm.srow[lane] >= 0)
+    sm.skey[lane] = abs_key(residual_at(in, b, sm.q_r, sm.srow[lane], sm.scol[lane]));
   __syncthreads();
   if (tid == 0) {
     KeyBest best{0ull, LLONG_MAX, -1, -1};
@@ -2032,7 +2076,7 @@ __device__ __noinline__ void decide_bond_rescore(const InstDev &in, Ctrl &cr, in
     cr.best_lin[b] = best.lin;
     cr.best_row[b] = best.row;
     cr.best_col[b] = best.col;
-    atomicAdd((unsigned long long *)&cr.tiles_refined, (unsigned long long)k);
+    atomicAdd((unsigned long long *)&cr.tiles_refined, (unsigned long long)min((int64_t)k, nt));
     sm.rk[0] = best.key;
     sm.rr[0] = best.row;
     sm.rc[0] = best.col;
@@ -2227,6 +2271,17 @@ __device__ void verify_instance(const InstDev &in, Ctrl &cr, DecideSmem &sm) {
 // item kinds of for_decide_items
 enum ItemMode { IM_DECIDE = 0, IM_PENDING = 1, IM_ROOK = 2, IM_FINALIZE = 3 };
 
+// CTAs that share one bond's decide: the mixed stored form of a single
+// instance merges its tile slots' k best in DPARTS parts (the last part to
+// finish re-scores, takes the stop test and the pivot step); everything else
+// in one part (the FP64 best of the slots is one short pass)
+constexpr int DPARTS = 32;
+__device__ __forceinline__ int decide_parts(const RunArgs &ra, const InstDev &in, int mode) {
+  return (mode == IM_DECIDE && ra.count == 1 && in.stored && in.nl == 0 && in.prec != P_FP64)
+             ? DPARTS
+             : 1;
+}
+
 template <class F>
 __device__ void for_decide_items(const RunArgs &ra, int mode, F &&f) {
   __shared__ int s_take;
@@ -2235,9 +2290,11 @@ __device__ void for_decide_items(const RunArgs &ra, int mode, F &&f) {
   for (int ii = 0; ii < ra.count; ++ii) {
     const InstDev &in = inst(ra, ii);
     const Ctrl &cr = *in.ctrl;
-    const int64_t end = first + in.nb + 1;
+    const int P = decide_parts(ra, in, mode);
+    const int64_t end = first + (int64_t)in.nb * P + 1;
     for (int64_t x = first + ((s_place - first) % G + G) % G; x < end; x += G) {
-      const int slot = (int)(x - first) - 1;
+      const int slot = x == first ? -1 : (int)((x - first - 1) / P);
+      const int part = x == first ? 0 : (int)((x - first - 1) % P);
       // one thread decides and the CTA follows: the words it reads can be
       // rewritten by other CTAs' items during the phase (a failing bond ends
       // the instance), and every thread of the CTA must take the same branch
@@ -2256,14 +2313,14 @@ __device__ void for_decide_items(const RunArgs &ra, int mode, F &&f) {
         s_take = take ? 1 : 0;
       }
       __syncthreads();
-      if (s_take) f(ii, slot);
+      if (s_take) f(ii, slot, part, P);
     }
     first = end;
   }
 }
 
 __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
-  for_decide_items(ra, IM_DECIDE, [&](int ii, int b) {
+  for_decide_items(ra, IM_DECIDE, [&](int ii, int b, int part, int P) {
     const InstDev &in = inst(ra, ii);
     Ctrl &cr = *in.ctrl;
     if (b < 0) {
@@ -2273,7 +2330,7 @@ __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
     } else if (in.prec == P_FP64) {
       decide_bond_fp64(in, cr, b, sm.d);
     } else if (in.stored) {
-      decide_bond_rescore(in, cr, b, sm.d);
+      decide_bond_rescore(in, cr, b, part, P, sm.d);
     } else {
       merge_bond_mixed(in, cr, b, sm.d);
     }
@@ -2283,7 +2340,7 @@ __device__ void phase_decide(const RunArgs &ra, PhaseSmem &sm) {
 // mixed forms, part 2: the FP64 results of the refined tiles join the
 // re-scored candidates; the best is the FP64 argmax of the screen.
 __device__ void phase_decide2(const RunArgs &ra, PhaseSmem &sm) {
-  for_decide_items(ra, IM_PENDING, [&](int ii, int b) {
+  for_decide_items(ra, IM_PENDING, [&](int ii, int b, int, int) {
     const InstDev &in = inst(ra, ii);
     Ctrl &cr = *in.ctrl;
     DecideSmem &d = sm.d;
@@ -2420,7 +2477,7 @@ __device__ void phase_rook_scan(const RunArgs &ra, PhaseSmem &sm) {
 // (step 1) or row (step 2); a round is step 1 then step 2, and the
 // refinement ends after a round that moved nothing or after max_rook rounds
 __device__ void phase_rook_decide(const RunArgs &ra, PhaseSmem &sm) {
-  for_decide_items(ra, IM_ROOK, [&](int ii, int b) {
+  for_decide_items(ra, IM_ROOK, [&](int ii, int b, int, int) {
     const InstDev &in = inst(ra, ii);
     Ctrl &cr = *in.ctrl;
     const KeyBest line = merge_slots(in, cr, b, gridDim.x, sm.d);
@@ -2465,7 +2522,7 @@ __device__ void phase_rook_decide(const RunArgs &ra, PhaseSmem &sm) {
 // sampled screen: the stop test and the pivot append of every bond, on the
 // refined pivots
 __device__ void phase_finalize(const RunArgs &ra, PhaseSmem &sm) {
-  for_decide_items(ra, IM_FINALIZE, [&](int ii, int b) {
+  for_decide_items(ra, IM_FINALIZE, [&](int ii, int b, int, int) {
     const InstDev &in = inst(ra, ii);
     finalize_bond(in, *in.ctrl, b, sm.d);
   });
