@@ -22,6 +22,19 @@ extern "C" {
 int ttcross_probe_fma_peak(int fp64, int blocks_per_sm, int64_t iters, double *fma_per_s,
                            double *ms);
 
+/* Latency of a dependent binary64 FMA chain on one SM of the current device,
+   the quantity that bounds the serial parts of the cross (the pivot steps,
+   Alg. 4 replays, the FP64 re-scores).  One CTA: warps 0..chain_warps-1 run
+   `iters` dependent FMAs on their lanes 0..active_lanes-1 (the other lanes
+   idle); warps chain_warps..chain_warps+busy_warps-1 run four independent
+   chains each on all lanes, a throughput load on the same SM.  Writes the
+   clock cycles per dependent FMA of warp 0 to *cycles.  Limits:
+   1 <= chain_warps, 0 <= busy_warps, chain_warps + busy_warps <= 32,
+   1 <= active_lanes <= 32, 1 <= iters <= 2^30; else TTC_ERR_INVALID_ARG (1).
+   Returns 0 or a ttc_status code (6: CUDA).  Synchronizes the device. */
+int ttcross_probe_fp64_chain(int chain_warps, int active_lanes, int busy_warps, int64_t iters,
+                             double *cycles);
+
 #ifdef __cplusplus
 }
 #endif

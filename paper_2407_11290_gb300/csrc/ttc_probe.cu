@@ -18,7 +18,53 @@ __global__ void k_fma_loop(T *out, int64_t iters, T a, T b) {
   if (s == (T)-1.2345) out[blockIdx.x] = s;  // keeps the loop alive
 }
 
+// dependent FMA chains of warps < nchain on lanes < active; warps >= nchain
+// load the SM's FP64 units with independent chains; thread t writes out[t]
+__global__ void k_fp64_chain(double *out, long long *cyc, int64_t iters, int nchain, int active) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double a = 1.0000001 + 1e-9 * threadIdx.x, b = 1e-9;
+  double acc = 0.5;
+  __syncthreads();
+  const long long t0 = clock64();
+  if (warp < nchain) {
+    if (lane < active)
+      for (int64_t i = 0; i < iters; ++i) acc = fma(acc, a, b);
+  } else {
+    double x0 = acc, x1 = acc + 1.0, x2 = acc + 2.0, x3 = acc + 3.0;
+    for (int64_t i = 0; i < iters; ++i) {
+      x0 = fma(x0, a, b);
+      x1 = fma(x1, a, b);
+      x2 = fma(x2, a, b);
+      x3 = fma(x3, a, b);
+    }
+    acc = (x0 + x1) + (x2 + x3);
+  }
+  const long long t1 = clock64();
+  out[threadIdx.x] = acc;
+  if (threadIdx.x == 0) *cyc = t1 - t0;
+}
+
 }  // namespace
+
+extern "C" int ttcross_probe_fp64_chain(int chain_warps, int active_lanes, int busy_warps,
+                                        int64_t iters, double *cycles) {
+  if (chain_warps < 1 || busy_warps < 0 || chain_warps + busy_warps > 32 || active_lanes < 1 ||
+      active_lanes > 32 || iters < 1 || iters > ((int64_t)1 << 30) || !cycles)
+    return 1;
+  const int threads = 32 * (chain_warps + busy_warps);
+  void *buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * threads + sizeof(long long)) != cudaSuccess) return 6;
+  double *out = (double *)buf;
+  long long *cyc = (long long *)(out + threads);
+  long long h = 0;
+  for (int rep = 0; rep < 2; ++rep)  // warm-up, then the measured launch
+    k_fp64_chain<<<1, threads>>>(out, cyc, iters, chain_warps, active_lanes);
+  cudaError_t e = cudaMemcpy(&h, cyc, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return 6;
+  *cycles = (double)h / (double)iters;
+  return 0;
+}
 
 extern "C" int ttcross_probe_fma_peak(int fp64, int blocks_per_sm, int64_t iters,
                                       double *fma_per_s, double *ms) {

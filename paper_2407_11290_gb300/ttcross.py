@@ -432,6 +432,19 @@ def probe_fma_peak(fp64: bool = True, blocks_per_sm: int = 4, iters: int = 1 << 
     return rate.value, ms.value
 
 
+def probe_fp64_chain(chain_warps: int = 1, active_lanes: int = 32, busy_warps: int = 0,
+                     iters: int = 1 << 14) -> float:
+    """Clock cycles per dependent FP64 FMA of one warp on one SM, with
+    ``chain_warps`` such warps and ``busy_warps`` warps of independent FMAs."""
+    L = load_library()
+    f = L.ttcross_probe_fp64_chain
+    f.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, C.POINTER(C.c_double)]
+    f.restype = C.c_int
+    cyc = C.c_double()
+    _check(f(int(chain_warps), int(active_lanes), int(busy_warps), int(iters), C.byref(cyc)))
+    return cyc.value
+
+
 def run_batch(crosses, eps, max_rank=None, grids=None, stream=None):
     """Run several instances in one persistent launch (asynchronous).
     ``grids``: None, or one subtensor grid (or None) per instance."""

@@ -18,6 +18,16 @@ def declared_functions():
     return sorted(set(re.findall(r"\b(ttcross_\w+)\s*\(", text)))
 
 
+def test_library_exports_the_probe_symbols():
+    text = open(os.path.join(B.INCLUDE, "ttcross_probe.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = sorted(set(re.findall(r"\b(ttcross_\w+)\s*\(", text)))
+    assert names == ["ttcross_probe_fma_peak", "ttcross_probe_fp64_chain"]
+    L = ctypes.CDLL(B.build())
+    for name in names:
+        assert hasattr(L, name), name
+
+
 def test_library_builds_and_exports_header_symbols():
     lib = B.build()
     L = ctypes.CDLL(lib)
