@@ -1238,7 +1238,7 @@ __device__ __noinline__ void screen_carried_warp(const InstDev &in, int b, int64
   using VT = typename V::T;
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int NC = TE / 32;                // columns per lane
-  constexpr int RR = TE == 32 ? 32 : 8;      // rows per round
+  constexpr int RR = TE == 32 ? 32 : (MIX == 0 ? 8 : 16);  // rows per round
   const BondDev &B = in.bond[b];
   const int lane = threadIdx.x & 31;
   const int64_t ld = B.ldR;
