@@ -140,3 +140,13 @@ def test_user_generator_needs_a_callback():
     assert L.ttcross_create(3, n, ctypes.byref(g), None, ctypes.byref(h)) == \
         ttcross.ERR_INVALID_ARG
     assert b"callback" in L.ttcross_last_error_string()
+
+
+def test_fp64_chain_probe_rejects_bad_arguments_on_the_host():
+    """The latency probe checks its arguments before any device call, so the
+    refusals need no GPU."""
+    for args in [(0, 32, 0), (1, 0, 0), (1, 33, 0), (1, 32, -1), (20, 32, 13)]:
+        with pytest.raises(ttcross.TTCError):
+            ttcross.probe_fp64_chain(*args)
+    with pytest.raises(ttcross.TTCError):
+        ttcross.probe_fp64_chain(1, 32, 0, iters=0)
