@@ -220,7 +220,15 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen,
    Sec. 3.2.1).  NULL lets the library choose the tiles.
    Asynchronous on `stream` unless opt->host_loop: it returns after the launch;
    ttcross_sync / the getters wait for it.  Errors detected on the host are
-   returned at once; errors found on the device are reported by ttcross_sync. */
+   returned at once; errors found on the device are reported by ttcross_sync.
+   CUDA graphs: while `stream` is capturing, the call adds its work (a control
+   block kernel, a memset and the persistent kernel) to the graph, so that
+   replays rerun the whole cross.  It needs a persistent run (no host_loop, no
+   user generator) and an earlier ordinary run with the same subtensor grid
+   (a captured call allocates nothing; otherwise INVALID_ARG).  After a
+   replay, wait for the replay's stream before ttcross_sync, which then reads
+   the device on every call for this handle; device_ms keeps the last
+   ordinary run's time. */
 ttc_status ttcross_run(ttc_handle *h, double eps, int max_rank,
                        const int32_t *subtensor_grid, void *stream);
 
@@ -234,7 +242,12 @@ ttc_status ttcross_run(ttc_handle *h, double eps, int max_rank,
    (checked on the host before anything is launched; this includes a batch
    of two or more instances where an FP32 / float-float instance of the
    recompute form has a non-Hilbert generator, a combination that is not
-   supported), CUDA, OOM. */
+   supported), CUDA, OOM.  The instance list lives with hs[0] (grown by
+   ordinary calls).  CUDA graphs as for ttcross_run: a captured batch needs an
+   earlier ordinary batch of at least count instances led by hs[0] and an
+   earlier run of every instance with its grid; the list's pointers are
+   captured by value, so a replay reruns these instances even after hs[0]
+   led other batches. */
 ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps,
                              const int32_t *max_rank, const int32_t *const *grids,
                              void *stream);

@@ -65,6 +65,10 @@ struct ttc_handle {
   InstDev hi{};                 // host copy of the device descriptor
   InstDev *d_inst = nullptr;
   InstDev **d_list = nullptr;   // [1] = d_inst, for single runs
+  InstDev **blist = nullptr;    // the instance list of batches led by this handle
+  int64_t blist_cap = 0;
+  bool captured = false;        // a run of this handle was captured in a CUDA graph:
+                                // every sync reads the device (replays bypass the host)
   Ctrl *d_ctrl = nullptr;
   Barrier *d_bar = nullptr;
   int32_t *d_smid = nullptr;
@@ -106,11 +110,40 @@ namespace {
 
 __global__ void k_set_ctrl(Ctrl *dst, Ctrl v) { *dst = v; }
 
+// a chunk of the instance list, passed by value as a kernel parameter (so
+// that a captured launch keeps the pointers it was given)
+constexpr int BATCH_CHUNK = 256;
+struct BatchList {
+  InstDev *p[BATCH_CHUNK];
+};
+
 int64_t cand_need(const ttc_handle *h, int b, const int32_t *grid) {
   const int64_t capL = b == 0 ? 1 : h->bond_cap[b - 1];
   const int64_t capR = b == h->nb - 1 ? 1 : h->bond_cap[b + 1];
   const int32_t pr = grid ? grid[b] : 0, pc = grid ? grid[b + 1] : 0;
   return host_tiles(h->n[b], h->n[b + 1], capL, capR, pr, pc);
+}
+
+// the candidate slots of a run with this grid fit the current allocation
+bool cands_fit(const ttc_handle *h, const int32_t *grid) {
+  if (!h->cand) return false;
+  for (int b = 0; b < h->nb; ++b) {
+    int64_t need = std::max<int64_t>(cand_need(h, b, grid), 8192);
+    if (h->hi.stored) need *= 4;
+    if (need > h->bond_cand_cap[b]) return false;
+  }
+  return true;
+}
+
+// the stream is capturing into a CUDA graph (errors read as not capturing)
+bool stream_capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+__global__ void k_set_list(InstDev **dst, BatchList src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src.p[i];
 }
 
 ttc_status ensure_cands(ttc_handle *h, const int32_t *grid) {
@@ -741,20 +774,33 @@ ttc_status ttcross_run(ttc_handle *h, double eps, int max_rank, const int32_t *s
   int dev = -1;
   CU(cudaGetDevice(&dev));
   if (dev != h->device) return fail(TTC_ERR_INVALID_ARG, "handle lives on device %d", h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool cap = stream_capturing(st);
+  if (cap) {
+    // a captured run issues stream work only: the persistent kernel, and
+    // buffers already sized by an earlier run with this grid
+    if (h->opt.host_loop || h->user_fn)
+      return fail(TTC_ERR_INVALID_ARG, "a host-stepped run cannot be captured in a graph");
+    if (!cands_fit(h, subtensor_grid))
+      return fail(TTC_ERR_INVALID_ARG,
+                  "run once with this subtensor grid before capturing (buffers would grow)");
+  }
   s = ensure_cands(h, subtensor_grid);
   if (s) return s;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   Ctrl c = make_ctrl(h, eps, max_rank, subtensor_grid);
   k_set_ctrl<<<1, 1, 0, st>>>(h->d_ctrl, c);
   CU(cudaGetLastError());
-  if (h->events_ok) CU(cudaEventRecord(h->ev0, st));
+  // (a captured run records no timing events: device_ms keeps the last
+  // ordinary run's time)
+  if (h->events_ok && !cap) CU(cudaEventRecord(h->ev0, st));
   ttc_handle *hs[1] = {h};
   s = launch_run(hs, 1, h->d_list, st);
   if (s) return s;
-  if (h->events_ok) CU(cudaEventRecord(h->ev1, st));
+  if (h->events_ok && !cap) CU(cudaEventRecord(h->ev1, st));
   h->stream = st;
   h->ran = true;
   h->synced = false;
+  if (cap) h->captured = true;
   return TTC_OK;
 }
 
@@ -785,6 +831,26 @@ ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps
                   "generator only (use the stored residual form or FP64)", i);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ttc_handle *h0 = hs[0];
+  const bool cap = stream_capturing(st);
+  if (cap) {
+    if (h0->blist_cap < count)
+      return fail(TTC_ERR_INVALID_ARG,
+                  "run a batch of this size led by this handle once before capturing");
+    for (int i = 0; i < count; ++i)
+      if (!cands_fit(hs[i], grids ? grids[i] : nullptr))
+        return fail(TTC_ERR_INVALID_ARG, "instance %d: run it with this grid before capturing", i);
+  }
+  if (h0->blist_cap < count) {
+    if (h0->blist) {
+      CU(cudaDeviceSynchronize());
+      CU(cudaFree(h0->blist));
+      h0->blist = nullptr;
+      h0->blist_cap = 0;
+    }
+    CU(cudaMalloc((void **)&h0->blist, sizeof(InstDev *) * count));
+    h0->blist_cap = count;
+  }
   for (int i = 0; i < count; ++i) {
     const int32_t *gi = grids ? grids[i] : nullptr;
     ttc_status s = ensure_cands(hs[i], gi);
@@ -793,15 +859,17 @@ ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps
     k_set_ctrl<<<1, 1, 0, st>>>(hs[i]->d_ctrl, c);
     CU(cudaGetLastError());
   }
-  std::vector<InstDev *> lst(count);
-  for (int i = 0; i < count; ++i) lst[i] = hs[i]->d_inst;
-  InstDev **d_list = nullptr;
-  CU(cudaMallocAsync((void **)&d_list, sizeof(InstDev *) * count, st));
-  CU(cudaMemcpyAsync(d_list, lst.data(), sizeof(InstDev *) * count, cudaMemcpyHostToDevice, st));
-  CU(cudaStreamSynchronize(st));  // the host vector dies at return
-  ttc_handle *h0 = hs[0];
+  // the instance list, written by kernels whose parameters carry the pointers
+  for (int i0 = 0; i0 < count; i0 += BATCH_CHUNK) {
+    BatchList bl{};
+    const int nc = std::min(BATCH_CHUNK, count - i0);
+    for (int i = 0; i < nc; ++i) bl.p[i] = hs[i0 + i]->d_inst;
+    k_set_list<<<1, 256, 0, st>>>(h0->blist + i0, bl, nc);
+    CU(cudaGetLastError());
+  }
+  InstDev **d_list = h0->blist;
   for (int i = 0; i < count; ++i)
-    if (hs[i]->events_ok) CU(cudaEventRecord(hs[i]->ev0, st));
+    if (hs[i]->events_ok && !cap) CU(cudaEventRecord(hs[i]->ev0, st));
   ttc_status s = launch_run(hs, count, d_list, st);
   // every instance keeps its own copy of the launch's barrier words (abort
   // flag, phase times) and its own events, so that it can be synchronised,
@@ -811,13 +879,13 @@ ttc_status ttcross_run_batch(ttc_handle *const *hs, int count, const double *eps
         cudaSuccess)
       s = fail(TTC_ERR_CUDA, "copy of the barrier words failed");
   for (int i = 0; i < count; ++i)
-    if (hs[i]->events_ok) cudaEventRecord(hs[i]->ev1, st);
-  cudaFreeAsync(d_list, st);
+    if (hs[i]->events_ok && !cap) cudaEventRecord(hs[i]->ev1, st);
   if (s) return s;
   for (int i = 0; i < count; ++i) {
     hs[i]->stream = st;
     hs[i]->ran = true;
     hs[i]->synced = false;
+    if (cap) hs[i]->captured = true;
   }
   return TTC_OK;
 }
@@ -884,8 +952,10 @@ ttc_status ttcross_sync(ttc_handle *h) {
   if (s) return s;
   if (!h->ran) return fail(TTC_ERR_INVALID_ARG, "no run to wait for");
   // the first wait after a run reads its control block; later calls (every
-  // getter waits) return what it found without touching the device
-  if (h->synced) {
+  // getter waits) return what it found without touching the device.  A
+  // handle whose run was captured in a CUDA graph reads it every time: the
+  // graph's replays do not pass through here.
+  if (h->synced && !h->captured) {
     if (h->sync_status != TTC_OK && h->sync_status != TTC_NOT_CONVERGED)
       return fail(h->sync_status, "%s", h->sync_msg.c_str());
     return h->sync_status;
@@ -1045,6 +1115,7 @@ ttc_status ttcross_destroy(ttc_handle *h) {
   if (h->estore) cudaFree(h->estore);
   if (h->acache) cudaFree(h->acache);
   if (h->rebuild_scratch) cudaFree(h->rebuild_scratch);
+  if (h->blist) cudaFree(h->blist);
   if (h->ev2) cudaEventDestroy(h->ev2);
   if (h->ev3) cudaEventDestroy(h->ev3);
   if (h->ustage_idx) cudaFree(h->ustage_idx);
