@@ -35,6 +35,13 @@ int ttcross_probe_fma_peak(int fp64, int blocks_per_sm, int64_t iters, double *f
 int ttcross_probe_fp64_chain(int chain_warps, int active_lanes, int busy_warps, int64_t iters,
                              double *cycles);
 
+/* Issue rate of one warp's independent binary64 FMAs: one CTA of `warps`
+   warps (1..32), each lane running `chains` (1, 2, 4 or 8) independent FMA
+   chains for `iters` iterations; writes the clock cycles per FMA instruction
+   of warp 0 to *cycles.  Returns 0, 1 (INVALID_ARG) or 6 (CUDA).
+   Synchronizes the device. */
+int ttcross_probe_fp64_ilp(int warps, int chains, int64_t iters, double *cycles);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,7 +44,51 @@ __global__ void k_fp64_chain(double *out, long long *cyc, int64_t iters, int nch
   if (threadIdx.x == 0) *cyc = t1 - t0;
 }
 
+// K independent FMA chains per lane; thread t writes out[t]
+template <int K>
+__global__ void k_fp64_ilp(double *out, long long *cyc, int64_t iters) {
+  const double a = 1.0000001 + 1e-9 * threadIdx.x, b = 1e-9;
+  double x[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) x[k] = 0.5 + k;
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) x[k] = fma(x[k], a, b);
+  }
+  const long long t1 = clock64();
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) s += x[k];
+  out[threadIdx.x] = s;
+  if (threadIdx.x == 0) *cyc = t1 - t0;
+}
+
 }  // namespace
+
+extern "C" int ttcross_probe_fp64_ilp(int warps, int chains, int64_t iters, double *cycles) {
+  if (warps < 1 || warps > 32 || !(chains == 1 || chains == 2 || chains == 4 || chains == 8) ||
+      iters < 1 || iters > ((int64_t)1 << 30) || !cycles)
+    return 1;
+  const int threads = 32 * warps;
+  void *buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * threads + sizeof(long long)) != cudaSuccess) return 6;
+  double *out = (double *)buf;
+  long long *cyc = (long long *)(out + threads);
+  for (int rep = 0; rep < 2; ++rep) {  // warm-up, then the measured launch
+    if (chains == 1) k_fp64_ilp<1><<<1, threads>>>(out, cyc, iters);
+    if (chains == 2) k_fp64_ilp<2><<<1, threads>>>(out, cyc, iters);
+    if (chains == 4) k_fp64_ilp<4><<<1, threads>>>(out, cyc, iters);
+    if (chains == 8) k_fp64_ilp<8><<<1, threads>>>(out, cyc, iters);
+  }
+  long long h = 0;
+  cudaError_t e = cudaMemcpy(&h, cyc, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return 6;
+  *cycles = (double)h / ((double)iters * chains);
+  return 0;
+}
 
 extern "C" int ttcross_probe_fp64_chain(int chain_warps, int active_lanes, int busy_warps,
                                         int64_t iters, double *cycles) {

@@ -445,6 +445,18 @@ def probe_fp64_chain(chain_warps: int = 1, active_lanes: int = 32, busy_warps: i
     return cyc.value
 
 
+def probe_fp64_ilp(warps: int = 1, chains: int = 4, iters: int = 1 << 12) -> float:
+    """Clock cycles per FP64 FMA instruction of one warp running ``chains``
+    independent chains, with ``warps`` such warps on one SM."""
+    L = load_library()
+    f = L.ttcross_probe_fp64_ilp
+    f.argtypes = [C.c_int, C.c_int, C.c_int64, C.POINTER(C.c_double)]
+    f.restype = C.c_int
+    cyc = C.c_double()
+    _check(f(int(warps), int(chains), int(iters), C.byref(cyc)))
+    return cyc.value
+
+
 def run_batch(crosses, eps, max_rank=None, grids=None, stream=None):
     """Run several instances in one persistent launch (asynchronous).
     ``grids``: None, or one subtensor grid (or None) per instance."""

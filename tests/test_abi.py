@@ -22,7 +22,8 @@ def test_library_exports_the_probe_symbols():
     text = open(os.path.join(B.INCLUDE, "ttcross_probe.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = sorted(set(re.findall(r"\b(ttcross_\w+)\s*\(", text)))
-    assert names == ["ttcross_probe_fma_peak", "ttcross_probe_fp64_chain"]
+    assert names == ["ttcross_probe_fma_peak", "ttcross_probe_fp64_chain",
+                     "ttcross_probe_fp64_ilp"]
     L = ctypes.CDLL(B.build())
     for name in names:
         assert hasattr(L, name), name
@@ -150,3 +151,6 @@ def test_fp64_chain_probe_rejects_bad_arguments_on_the_host():
             ttcross.probe_fp64_chain(*args)
     with pytest.raises(ttcross.TTCError):
         ttcross.probe_fp64_chain(1, 32, 0, iters=0)
+    for args in [(0, 4), (33, 4), (1, 3), (1, 16)]:
+        with pytest.raises(ttcross.TTCError):
+            ttcross.probe_fp64_ilp(*args)
