@@ -30,11 +30,13 @@ def _same(c, ref):
         np.testing.assert_array_equal(c.core(k + 1), cores[k])
 
 
-def test_run_captured_in_a_cuda_graph(tt):
+@pytest.mark.parametrize("precision,residual", [("fp64", "stored"), ("split", "stored"),
+                                                ("fp64", "recompute")])
+def test_run_captured_in_a_cuda_graph(tt, precision, residual):
     import torch
     w = W.CONFIGS["hilbert6d_n64"]
     g = tt.TTCross(w["n"], w["gen"], max_rank=w["max_rank"], nsamples=w["nsamples"],
-                   residual="stored")
+                   precision=precision, residual=residual)
     g.run(w["eps"], subtensor_grid=w["grid"])
     assert g.sync() == tt.OK
     ref = _state(g)
