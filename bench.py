@@ -116,6 +116,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
+HBM_FALLBACK_GBS = 6800.0
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -268,7 +271,8 @@ def bench_gpu(args, rank, world, local):
                              "kernel_ms": statistics.median(kern_ms), "err": st["err"],
                              "status": ttcross.STATUS_NAMES.get(st["status"], st["status"]),
                              "ranks": [int(x) for x in tc.ranks()], "sweeps": st["sweeps"],
-                             "phase_ms": st["phase_ms"], "rescored": st["tiles_refined"]}}
+                             "phase_ms": st["phase_ms"], "rescored": st["tiles_refined"],
+                             "stored_gbs": _stored_gbs(st, kern_ms)}}
     secondary = {}
     if rank == 0 and not args.no_forms:
         other = "split" if args.precision == "fp64" else "fp64"
@@ -279,7 +283,8 @@ def bench_gpu(args, rank, world, local):
                        "kernel_ms": statistics.median(km), "err": ast["err"],
                        "status": ttcross.STATUS_NAMES.get(ast["status"], ast["status"]),
                        "ranks": [int(x) for x in a.ranks()], "sweeps": ast["sweeps"],
-                       "phase_ms": ast["phase_ms"], "rescored": ast["tiles_refined"]}
+                       "phase_ms": ast["phase_ms"], "rescored": ast["tiles_refined"],
+                       "stored_gbs": _stored_gbs(ast, km)}
         a.close()
         if args.workload != SECONDARY:
             wc = workloads.CONFIGS[SECONDARY]
@@ -301,7 +306,15 @@ def bench_gpu(args, rank, world, local):
     peak = 2.0 * fma64 / 1e12
     peaks = measured_peaks() or {}
     hbm = peaks.get("hbm_gbs")
+    hbm_source = "measured copy bandwidth on this GPU pool"
+    if not hbm:
+        # no measured copy bandwidth on this machine: one earlier GB300 copy
+        # measurement stands in, labelled as such
+        hbm, hbm_source = HBM_FALLBACK_GBS, "fallback (earlier GB300 copy measurement)"
     stored_gbs = st["stored_bytes"] / (kms * 1e-3) / 1e9
+    # each arm's stored-residual bytes against the same HBM peak
+    for arm in arms.values():
+        arm["hbm_frac"] = arm["stored_gbs"] / hbm if hbm and arm["stored_gbs"] else None
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -336,7 +349,7 @@ def bench_gpu(args, rank, world, local):
                      "algorithmic_fma": algo_fma,
                      "stored_bytes": st["stored_bytes"], "stored_gbs": stored_gbs,
                      "hbm_frac": stored_gbs / hbm if hbm else None,
-                     "hbm_peak_gbs": hbm},
+                     "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_source},
         "clocks": clocks,
         "arms": arms,
         "secondary": {"workload": SECONDARY, **secondary} if secondary else None,
@@ -357,6 +370,15 @@ def bench_gpu(args, rank, world, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     tc.close()
+
+
+def _stored_gbs(st, kern_ms):
+    """The bytes of the stored residual E that the arm's screens read and
+    wrote, over its median kernel time, in GB/s; None in the recompute form,
+    which stores nothing."""
+    if not st["stored_bytes"]:
+        return None
+    return st["stored_bytes"] / (statistics.median(kern_ms) * 1e-3) / 1e9
 
 
 def bench_batch(args, rank, world, local):
