@@ -48,8 +48,8 @@ ORACLE_CAP = {"hilbert6d_n256": 32}
 # the current kernels (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # (workload, residual form, precision); absent keys report null.  The n = 256
 # captures ran with rank capacity 32 (same sweeps: the ranks stay below 24).
-DRAM_TRAFFIC = {("hilbert6d_n256", "stored", "fp64"): 6215667200 + 7255294208,
-                ("hilbert6d_n256", "stored", "split"): 6188207616 + 7328576512}
+DRAM_TRAFFIC = {("hilbert6d_n256", "stored", "fp64"): 6215910144 + 7267844096,
+                ("hilbert6d_n256", "stored", "split"): 6212543488 + 7494847744}
 THROTTLE_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
                  0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
                  0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
