@@ -369,6 +369,45 @@ def test_maxwellian_moments():
         assert abs(m2 - T) < 1e-9
 
 
+def test_maxwellian_3d3v_velocity_moments():
+    """The 6D Maxwellian (d_x = 3, d_v = 3) of the single-tensor workload:
+    rho = 1 + a_rho sin x1 sin x2 sin x3, u = a_u (cos x2, cos x3, cos x1),
+    T = 1 + a_T cos(x1 + x2 + x3) on the periodic grid x = 2 pi i / n.  On a
+    wide v-grid the quadrature over the three velocities returns rho, u and
+    T (the uniform-grid sum of a Gaussian is exact far below 1e-10 at these
+    spacings), and at x = 0 the distribution is the standard Gaussian up to
+    the shift u = (a_u, a_u, a_u) and T = 1 + a_T."""
+    nv = 32
+    w = W.maxwellian(3, 3, [5, 6, 7, nv, nv, nv], a_rho=0.45, a_u=0.3, a_T=0.2,
+                     vmin=-9.0, vmax=9.0)
+    o = oracle.Oracle(w["n"], w["gen"], 2)
+    g = w["gen"]
+    v = g["vmin"] + (g["vmax"] - g["vmin"]) * np.arange(nv) / (nv - 1)
+    h = (g["vmax"] - g["vmin"]) / (nv - 1)
+    V = np.meshgrid(v, v, v, indexing="ij")
+    for ix in [(0, 0, 0), (1, 2, 3), (4, 5, 6), (2, 1, 5)]:
+        x = [2 * np.pi * ix[m] / w["n"][m] for m in range(3)]
+        F = np.empty((nv, nv, nv))
+        for a in range(nv):
+            for b in range(nv):
+                for c in range(nv):
+                    F[a, b, c] = o.entry(ix + (a, b, c))
+        rho = 1 + g["a_rho"] * np.sin(x[0]) * np.sin(x[1]) * np.sin(x[2])
+        u = [g["a_u"] * np.cos(x[1]), g["a_u"] * np.cos(x[2]), g["a_u"] * np.cos(x[0])]
+        T = 1 + g["a_T"] * np.cos(x[0] + x[1] + x[2])
+        m0 = F.sum() * h ** 3
+        m1 = [(F * V[j]).sum() * h ** 3 / m0 for j in range(3)]
+        m2 = sum((F * (V[j] - m1[j]) ** 2).sum() for j in range(3)) * h ** 3 / m0 / 3
+        assert abs(m0 - rho) < 1e-10
+        assert max(abs(m1[j] - u[j]) for j in range(3)) < 1e-10
+        assert abs(m2 - T) < 1e-9
+        if ix == (0, 0, 0):
+            t = 1 + g["a_T"]
+            q = sum((V[j] - g["a_u"]) ** 2 for j in range(3))
+            np.testing.assert_allclose(F, np.exp(-q / (2 * t)) / (2 * np.pi * t) ** 1.5,
+                                       rtol=1e-13, atol=1e-300)
+
+
 def test_maxwellian_xv_velocity_moments():
     """The 2d2v distribution of Sec. 5.2 on a wide v-grid: for fixed
     positions (x, y) the quadrature over (v_x, v_y) of f, of v_x^2 f and of
