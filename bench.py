@@ -56,6 +56,17 @@ THROTTLE_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_p
                  0x100: "display_clock_setting"}
 
 
+def max_over_ranks(value: float, device: str) -> float:
+    """The largest of the ranks' values (the replicas' step time is the
+    slowest replica's), reduced on ``device`` (a CUDA device under NCCL, the
+    CPU under gloo)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -250,9 +261,7 @@ def bench_gpu(args, rank, world, local):
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
         dist.barrier()
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, "cuda")
 
     # end to end through the C ABI with host buffers: run + cores to host memory
     e2e = []
@@ -392,6 +401,7 @@ def bench_batch(args, rank, world, local):
     The FP32 / float-float recompute-form batch of these tensors is refused by
     the library, so it is not an arm."""
     import torch
+    import torch.distributed as dist
 
     from paper_2407_11290_gb300 import ttcross, workloads
 
@@ -417,8 +427,13 @@ def bench_batch(args, rank, world, local):
         return hs
 
     def timed(run):
+        # replicas: a barrier on both sides of the timed steps, and the
+        # slowest replica's time
         for _ in range(args.warmup):
             run()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         out = []
         for _ in range(args.steps):
             torch.cuda.synchronize()
@@ -427,6 +442,9 @@ def bench_batch(args, rank, world, local):
             ev[1].record(stream)
             torch.cuda.synchronize()
             out.append(ev[0].elapsed_time(ev[1]))
+        if world > 1:
+            dist.barrier()
+            return max_over_ranks(sum(out) / len(out), "cuda")
         return sum(out) / len(out)
 
     def graphed(hs):
