@@ -311,6 +311,25 @@ ttc_status ttcross_get_stats(ttc_handle *h, ttc_stats *st);
 /* Frees the instance (waits for its last run).  NULL is accepted. */
 ttc_status ttcross_destroy(ttc_handle *h);
 
+/* Host-side check of the screens' tile arithmetic (Alg. 3's subtensors as
+   CTA tiles, Sec. 3.2; no GPU and no handle needed).  For a d-mode tensor of
+   mode sizes n[0..d-1] at bond ranks r[0..d-2] (bond k = r[k-1]), subtensor
+   grid grid[0..d-1] (pieces per mode; NULL: library tiles) and tile edge
+   tile_edge (32 or 64), it runs the kernels' own tile geometry on the host
+   and counts in *violations the tiles that are empty, wider than the edge,
+   outside their superblock or across a piece of the grid, plus every
+   superblock row or column the tiles do not cover exactly once.  tiles[b]
+   (may be NULL) receives bond b+1's tile count; cand_cap[b] (may be NULL)
+   the candidate slots a run with rank caps caps[0..d-2] gives bond b+1
+   (stored != 0: the stored form), which every tile count at ranks up to the
+   caps must not exceed.  All arrays are caller-owned host memory.
+   Errors: INVALID_ARG (d outside [2, TTC_MAXD], n[m] outside [1, 2^20],
+   caps outside [1, 256], r[b] outside [1, caps[b]], a grid entry outside
+   [0, n[m]], a superblock above 2^24 rows or columns, a null array). */
+ttc_status ttcross_check_tiles(int d, const int64_t *n, const int32_t *r, const int32_t *caps,
+                               const int32_t *grid, int tile_edge, int stored, int64_t *tiles,
+                               int64_t *cand_cap, int64_t *violations);
+
 /* Sampled relative error of a TT, computed without allocating memory.
    The paper has no counterpart: this is for callers that cannot call
    cudaMalloc (a custom allocator or memory-pool callback, a process whose

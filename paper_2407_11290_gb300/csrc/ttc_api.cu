@@ -117,21 +117,28 @@ struct BatchList {
   InstDev *p[BATCH_CHUNK];
 };
 
+// candidate slots of bond b for rank caps capL / capR of its neighbours:
+// one per 64 x 64 tile at the caps, at least 8192 (room for the 32 x 32 tiles
+// the kernels switch to when a sweep has fewer than two waves of tiles), and
+// four per tile in the stored form
+int64_t cand_slots(int64_t n_b, int64_t n_b1, int64_t capL, int64_t capR, int32_t pr, int32_t pc,
+                   bool stored) {
+  const int64_t need = std::max<int64_t>(host_tiles(n_b, n_b1, capL, capR, pr, pc), 8192);
+  return stored ? 4 * need : need;
+}
+
 int64_t cand_need(const ttc_handle *h, int b, const int32_t *grid) {
   const int64_t capL = b == 0 ? 1 : h->bond_cap[b - 1];
   const int64_t capR = b == h->nb - 1 ? 1 : h->bond_cap[b + 1];
   const int32_t pr = grid ? grid[b] : 0, pc = grid ? grid[b + 1] : 0;
-  return host_tiles(h->n[b], h->n[b + 1], capL, capR, pr, pc);
+  return cand_slots(h->n[b], h->n[b + 1], capL, capR, pr, pc, h->hi.stored != 0);
 }
 
 // the candidate slots of a run with this grid fit the current allocation
 bool cands_fit(const ttc_handle *h, const int32_t *grid) {
   if (!h->cand) return false;
-  for (int b = 0; b < h->nb; ++b) {
-    int64_t need = std::max<int64_t>(cand_need(h, b, grid), 8192);
-    if (h->hi.stored) need *= 4;
-    if (need > h->bond_cand_cap[b]) return false;
-  }
+  for (int b = 0; b < h->nb; ++b)
+    if (cand_need(h, b, grid) > h->bond_cand_cap[b]) return false;
   return true;
 }
 
@@ -150,10 +157,7 @@ ttc_status ensure_cands(ttc_handle *h, const int32_t *grid) {
   int64_t need[TTC_MAXB], total = 0;
   bool grow = false;
   for (int b = 0; b < h->nb; ++b) {
-    // 64 x 64 tiles at the rank caps, and room for the 32 x 32 tiles the
-    // kernels switch to when a sweep has fewer than two waves of tiles
-    need[b] = std::max<int64_t>(cand_need(h, b, grid), 8192);
-    if (h->hi.stored) need[b] *= 4;  // candidate slots per tile in the stored form
+    need[b] = cand_need(h, b, grid);
     if (need[b] > h->bond_cand_cap[b]) grow = true;
   }
   if (!grow && h->cand) return TTC_OK;
@@ -1100,6 +1104,40 @@ ttc_status ttcross_get_stats(ttc_handle *h, ttc_stats *out) {
   if (cudaMemcpy(&bar, h->d_bar, sizeof bar, cudaMemcpyDeviceToHost) == cudaSuccess) {
     out->device_error_where = bar.where;
     for (int i = 0; i < 6; ++i) out->phase_ms[i] = bar.phase_ns[i] * 1e-6;
+  }
+  return TTC_OK;
+}
+
+ttc_status ttcross_check_tiles(int d, const int64_t *n, const int32_t *r, const int32_t *caps,
+                               const int32_t *grid, int tile_edge, int stored, int64_t *tiles,
+                               int64_t *cand_cap, int64_t *violations) {
+  if (d < 2 || d > TTC_MAXD) return fail(TTC_ERR_INVALID_ARG, "d=%d outside [2,%d]", d, TTC_MAXD);
+  if (!n || !r || !caps || !violations) return fail(TTC_ERR_INVALID_ARG, "null array");
+  if (tile_edge != 32 && tile_edge != 64) return fail(TTC_ERR_INVALID_ARG, "tile_edge not 32/64");
+  for (int m = 0; m < d; ++m) {
+    if (n[m] < 1 || n[m] > (1 << 20)) return fail(TTC_ERR_INVALID_ARG, "n[%d] outside [1,2^20]", m);
+    if (grid && (grid[m] < 0 || grid[m] > n[m]))
+      return fail(TTC_ERR_INVALID_ARG, "grid[%d] outside [0,n]", m);
+  }
+  for (int b = 0; b < d - 1; ++b) {
+    if (caps[b] < 1 || caps[b] > RCAP) return fail(TTC_ERR_INVALID_ARG, "caps[%d] outside [1,%d]", b, RCAP);
+    if (r[b] < 1 || r[b] > caps[b]) return fail(TTC_ERR_INVALID_ARG, "r[%d] outside [1,cap]", b);
+  }
+  for (int b = 0; b < d - 1; ++b) {
+    const int64_t rl = b == 0 ? 1 : r[b - 1], rr = b == d - 2 ? 1 : r[b + 1];
+    if (rl * n[b] > (1 << 24) || rr * n[b + 1] > (1 << 24))
+      return fail(TTC_ERR_INVALID_ARG, "superblock of bond %d above 2^24 rows or columns", b + 1);
+  }
+  *violations = 0;
+  for (int b = 0; b < d - 1; ++b) {
+    int64_t nt = 0;
+    *violations += host_check_bond_tiles(d, n, r, grid, b, tile_edge, &nt);
+    if (tiles) tiles[b] = nt;
+    if (cand_cap) {
+      const int64_t capL = b == 0 ? 1 : caps[b - 1], capR = b == d - 2 ? 1 : caps[b + 1];
+      cand_cap[b] = cand_slots(n[b], n[b + 1], capL, capR, grid ? grid[b] : 0,
+                               grid ? grid[b + 1] : 0, stored != 0);
+    }
   }
   return TTC_OK;
 }

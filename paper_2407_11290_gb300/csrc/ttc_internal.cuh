@@ -270,10 +270,10 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
   return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ int64_t rows_of(const InstDev &in, const int32_t *r, int b) {
+__host__ __device__ __forceinline__ int64_t rows_of(const InstDev &in, const int32_t *r, int b) {
   return (int64_t)(b == 0 ? 1 : r[b - 1]) * in.n[b];
 }
-__device__ __forceinline__ int64_t cols_of(const InstDev &in, const int32_t *r, int b) {
+__host__ __device__ __forceinline__ int64_t cols_of(const InstDev &in, const int32_t *r, int b) {
   return in.n[b + 1] * (int64_t)(b == in.nb - 1 ? 1 : r[b + 1]);
 }
 __device__ __forceinline__ const SetDev &left_set(const InstDev &in, int b) {

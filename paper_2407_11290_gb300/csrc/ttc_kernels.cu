@@ -17,8 +17,11 @@
 //            error of Sec. 5.
 // The phases run either in one persistent cooperative launch separated by
 // grid barriers (every wait bounded in time) or as separate launches.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
+#include <memory>
+#include <vector>
 
 #include "ttc_gen.cuh"
 #include "ttc_internal.cuh"
@@ -270,7 +273,7 @@ struct Pieces {
   int32_t q, rem, tq1, tq0, tpb;  // tiles per piece of size q+1 / q, tiles per block
 };
 
-__device__ __forceinline__ Pieces make_pieces(int32_t n, int32_t C, int32_t te) {
+__host__ __device__ __forceinline__ Pieces make_pieces(int32_t n, int32_t C, int32_t te) {
   Pieces P;
   P.q = n / C;
   P.rem = n - P.q * C;
@@ -281,8 +284,8 @@ __device__ __forceinline__ Pieces make_pieces(int32_t n, int32_t C, int32_t te) 
 }
 
 // tile t of one block: start within the block and length
-__device__ __forceinline__ void piece_tile(const Pieces &P, int32_t t, int32_t te, int32_t &start,
-                                           int32_t &len) {
+__host__ __device__ __forceinline__ void piece_tile(const Pieces &P, int32_t t, int32_t te,
+                                                    int32_t &start, int32_t &len) {
   int32_t k, tin, size;
   if (t < P.rem * P.tq1) {
     k = t / P.tq1;
@@ -309,7 +312,8 @@ struct TileGeo {
   Pieces P, Q;             // row / column pieces
 };
 
-__device__ TileGeo tile_geo_e(const InstDev &in, const Ctrl &cr, const int32_t *r, int b, int te) {
+__host__ __device__ TileGeo tile_geo_e(const InstDev &in, const Ctrl &cr, const int32_t *r, int b,
+                                       int te) {
   TileGeo g;
   g.te = te;
   g.rows = (int32_t)rows_of(in, r, b);
@@ -428,8 +432,8 @@ __device__ __forceinline__ TileGeo planned_geo(const InstDev &in, const Ctrl &cr
   return g;
 }
 
-__device__ __forceinline__ void tile_rows(const InstDev &in, const TileGeo &g, int b, int32_t t,
-                                          int64_t &r0, int &nr) {
+__host__ __device__ __forceinline__ void tile_rows(const InstDev &in, const TileGeo &g, int b,
+                                                   int32_t t, int64_t &r0, int &nr) {
   if (g.pr > 0) {
     const int32_t p = t / g.P.tpb;
     int32_t st, len;
@@ -442,8 +446,8 @@ __device__ __forceinline__ void tile_rows(const InstDev &in, const TileGeo &g, i
   }
 }
 
-__device__ __forceinline__ void tile_cols(const InstDev &in, const TileGeo &g, int b, int32_t t,
-                                          int64_t &c0, int &nc) {
+__host__ __device__ __forceinline__ void tile_cols(const InstDev &in, const TileGeo &g, int b,
+                                                   int32_t t, int64_t &c0, int &nc) {
   if (g.pc > 0) {
     const int32_t q = t / g.Q.tpb;
     int32_t st, len;
@@ -3771,6 +3775,54 @@ int64_t host_tiles(int64_t n_b, int64_t n_b1, int64_t rl, int64_t rr, int32_t pr
   const int64_t nrt = pr > 0 ? rl * host_piece_tiles(n_b, pr, BM) : (rl * n_b + BM - 1) / BM;
   const int64_t nct = pc > 0 ? rr * host_piece_tiles(n_b1, pc, BN) : (n_b1 * rr + BN - 1) / BN;
   return nrt * nct;
+}
+
+// Host replay of the screens' tile arithmetic for bond b at ranks r: the
+// kernels' own tile_geo_e / tile_rows / tile_cols, run on the host.  Counts
+// the violations: a tile that is empty, wider than te or outside the
+// superblock; a tile that crosses a piece of the subtensor grid (the pieces
+// recomputed here from the balanced split); a superblock row or column that
+// the tiles cover other than exactly once.
+int64_t host_check_bond_tiles(int d, const int64_t *n, const int32_t *r, const int32_t *grid,
+                              int b, int te, int64_t *ntiles) {
+  std::unique_ptr<InstDev> in(new InstDev());
+  std::unique_ptr<Ctrl> cr(new Ctrl());
+  in->d = d;
+  in->nb = d - 1;
+  for (int m = 0; m < d; ++m) {
+    in->n[m] = n[m];
+    cr->grid[m] = grid ? grid[m] : 0;
+  }
+  const TileGeo g = tile_geo_e(*in, *cr, r, b, te);
+  int64_t bad = 0;
+  auto side = [&](int64_t len, int64_t nm, int32_t pieces, int32_t count, bool rows) {
+    std::vector<int32_t> cov((size_t)len, 0);
+    for (int32_t t = 0; t < count; ++t) {
+      int64_t s0;
+      int nl;
+      if (rows)
+        tile_rows(*in, g, b, t, s0, nl);
+      else
+        tile_cols(*in, g, b, t, s0, nl);
+      if (nl < 1 || nl > te || s0 < 0 || s0 + nl > len) {
+        ++bad;
+        continue;
+      }
+      if (pieces > 0) {
+        const int64_t i0 = s0 % nm, q = nm / pieces, rem = nm % pieces;
+        int64_t k = 0;
+        while (k + 1 < pieces && (k + 1) * q + std::min<int64_t>(k + 1, rem) <= i0) ++k;
+        const int64_t st = k * q + std::min<int64_t>(k, rem), sz = q + (k < rem ? 1 : 0);
+        if ((s0 + nl - 1) / nm != s0 / nm || i0 + nl > st + sz) ++bad;
+      }
+      for (int64_t x = s0; x < s0 + nl; ++x) ++cov[(size_t)x];
+    }
+    for (int64_t x = 0; x < len; ++x) bad += cov[(size_t)x] != 1;
+  };
+  side(g.rows, n[b], g.pr, g.nrt, true);
+  side(g.cols, n[b + 1], g.pc, g.nct, false);
+  if (ntiles) *ntiles = (int64_t)g.nrt * g.nct;
+  return bad;
 }
 
 cudaError_t persistent_occupancy(int *blocks_per_sm) {

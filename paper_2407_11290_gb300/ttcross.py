@@ -32,7 +32,8 @@ ABI_SYMBOLS = ("ttcross_default_options", "ttcross_create", "ttcross_run", "ttcr
                "ttcross_sync", "ttcross_get_ranks", "ttcross_get_cores", "ttcross_get_pivots",
                "ttcross_get_pivot_inverse", "ttcross_get_stats", "ttcross_destroy",
                "ttcross_sampled_error_noalloc", "ttcross_last_error_string",
-               "ttcross_set_plan", "ttcross_autotune", "ttcross_rebuild_cores")
+               "ttcross_set_plan", "ttcross_autotune", "ttcross_rebuild_cores",
+               "ttcross_check_tiles")
 
 
 class TTCError(RuntimeError):
@@ -151,6 +152,10 @@ def load_library(path: str = LIB_PATH):
         L.ttcross_autotune.argtypes = [P, C.c_double, C.c_int, C.POINTER(C.c_int32), P,
                                        C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                        C.POINTER(C.c_double)]
+        L.ttcross_check_tiles.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int,
+                                          C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_int64)]
         L.ttcross_last_error_string.restype = C.c_char_p
         for name in ABI_SYMBOLS:
             f = getattr(L, name)
@@ -455,6 +460,29 @@ def probe_fp64_ilp(warps: int = 1, chains: int = 4, iters: int = 1 << 12) -> flo
     cyc = C.c_double()
     _check(f(int(warps), int(chains), int(iters), C.byref(cyc)))
     return cyc.value
+
+
+def check_tiles(n, ranks, caps, grid=None, tile_edge: int = 64, stored: bool = False):
+    """ttcross_check_tiles: the kernels' tile arithmetic replayed on the host
+    for bond ranks ``ranks`` (bond k = ranks[k-1]).  Returns (tiles per bond,
+    candidate slots per bond at the rank caps ``caps``, violations).  Needs no
+    GPU."""
+    L = load_library()
+    d = len(n)
+    nn = np.ascontiguousarray(n, dtype=np.int64)
+    rr, cc = _i32(ranks), _i32(caps)
+    g = _i32(grid) if grid is not None else None
+    tiles = np.zeros(d - 1, dtype=np.int64)
+    cap = np.zeros(d - 1, dtype=np.int64)
+    bad = C.c_int64(0)
+    p64 = C.POINTER(C.c_int64)
+    p32 = C.POINTER(C.c_int32)
+    _check(L.ttcross_check_tiles(d, nn.ctypes.data_as(p64), rr.ctypes.data_as(p32),
+                                 cc.ctypes.data_as(p32), g.ctypes.data_as(p32) if g is not None
+                                 else None, int(tile_edge), int(bool(stored)),
+                                 tiles.ctypes.data_as(p64), cap.ctypes.data_as(p64),
+                                 C.byref(bad)))
+    return tiles, cap, int(bad.value)
 
 
 def run_batch(crosses, eps, max_rank=None, grids=None, stream=None):
