@@ -133,10 +133,16 @@ typedef enum {
                                  carried through each pivot's rank-one step
                                  E <- E - E(:,j*) E(i*,:) / E(i*,j*); only entries
                                  that enter a superblock are formed as A - T R.
-                                 FP64 only.  Needs 8 * rows_cap * cols_cap bytes per
-                                 bond (rows_cap = cap_{k-1} n_k, cols_cap = n_{k+1}
+                                 Needs 8 * rows_cap * cols_cap bytes per bond
+                                 (rows_cap = cap_{k-1} n_k, cols_cap = n_{k+1}
                                  cap_{k+1}); pivots follow the stored values, so they
-                                 may differ from the recompute form's at near-ties. */
+                                 may differ from the recompute form's at near-ties.
+                                 With TTC_PREC_FP32 / SPLIT / AUTO the entries are
+                                 formed and carried on the FP32 pipe as float-float
+                                 pairs (the same 8 bytes), each bond's top-k
+                                 candidates are re-scored in FP64, and T, R, P^-1 and
+                                 the error stay FP64; where FP64 residuals tie, the
+                                 pivot may be another of the tied entries. */
 } ttc_residual;
 
 typedef struct {
