@@ -324,17 +324,22 @@ ttc_status ttcross_destroy(ttc_handle *h);
    tile_edge (32 or 64), it runs the kernels' own tile geometry on the host
    and counts in *violations the tiles that are empty, wider than the edge,
    outside their superblock or across a piece of the grid, plus every
-   superblock row or column the tiles do not cover exactly once.  tiles[b]
+   superblock row or column the tiles do not cover exactly once; with
+   r_stored (nullable, d-1 ranks with 1 <= r_stored[b] <= r[b]: the ranks the
+   stored residual was last written at) also every tile of the stored
+   screen's carried rectangle that reaches outside the stored extent.  tiles[b]
    (may be NULL) receives bond b+1's tile count; cand_cap[b] (may be NULL)
    the candidate slots a run with rank caps caps[0..d-2] gives bond b+1
    (stored != 0: the stored form), which every tile count at ranks up to the
    caps must not exceed.  All arrays are caller-owned host memory.
    Errors: INVALID_ARG (d outside [2, TTC_MAXD], n[m] outside [1, 2^20],
-   caps outside [1, 256], r[b] outside [1, caps[b]], a grid entry outside
-   [0, n[m]], a superblock above 2^24 rows or columns, a null array). */
+   caps outside [1, 256], r[b] outside [1, caps[b]], r_stored[b] outside
+   [1, r[b]], a grid entry outside [0, n[m]], a superblock above 2^24 rows or
+   columns, a null array). */
 ttc_status ttcross_check_tiles(int d, const int64_t *n, const int32_t *r, const int32_t *caps,
-                               const int32_t *grid, int tile_edge, int stored, int64_t *tiles,
-                               int64_t *cand_cap, int64_t *violations);
+                               const int32_t *r_stored, const int32_t *grid, int tile_edge,
+                               int stored, int64_t *tiles, int64_t *cand_cap,
+                               int64_t *violations);
 
 /* Sampled relative error of a TT, computed without allocating memory.
    The paper has no counterpart: this is for callers that cannot call

@@ -1109,8 +1109,9 @@ ttc_status ttcross_get_stats(ttc_handle *h, ttc_stats *out) {
 }
 
 ttc_status ttcross_check_tiles(int d, const int64_t *n, const int32_t *r, const int32_t *caps,
-                               const int32_t *grid, int tile_edge, int stored, int64_t *tiles,
-                               int64_t *cand_cap, int64_t *violations) {
+                               const int32_t *r_stored, const int32_t *grid, int tile_edge,
+                               int stored, int64_t *tiles, int64_t *cand_cap,
+                               int64_t *violations) {
   if (d < 2 || d > TTC_MAXD) return fail(TTC_ERR_INVALID_ARG, "d=%d outside [2,%d]", d, TTC_MAXD);
   if (!n || !r || !caps || !violations) return fail(TTC_ERR_INVALID_ARG, "null array");
   if (tile_edge != 32 && tile_edge != 64) return fail(TTC_ERR_INVALID_ARG, "tile_edge not 32/64");
@@ -1122,6 +1123,8 @@ ttc_status ttcross_check_tiles(int d, const int64_t *n, const int32_t *r, const 
   for (int b = 0; b < d - 1; ++b) {
     if (caps[b] < 1 || caps[b] > RCAP) return fail(TTC_ERR_INVALID_ARG, "caps[%d] outside [1,%d]", b, RCAP);
     if (r[b] < 1 || r[b] > caps[b]) return fail(TTC_ERR_INVALID_ARG, "r[%d] outside [1,cap]", b);
+    if (r_stored && (r_stored[b] < 1 || r_stored[b] > r[b]))
+      return fail(TTC_ERR_INVALID_ARG, "r_stored[%d] outside [1,r]", b);
   }
   for (int b = 0; b < d - 1; ++b) {
     const int64_t rl = b == 0 ? 1 : r[b - 1], rr = b == d - 2 ? 1 : r[b + 1];
@@ -1131,7 +1134,7 @@ ttc_status ttcross_check_tiles(int d, const int64_t *n, const int32_t *r, const 
   *violations = 0;
   for (int b = 0; b < d - 1; ++b) {
     int64_t nt = 0;
-    *violations += host_check_bond_tiles(d, n, r, grid, b, tile_edge, &nt);
+    *violations += host_check_bond_tiles(d, n, r, r_stored, grid, b, tile_edge, &nt);
     if (tiles) tiles[b] = nt;
     if (cand_cap) {
       const int64_t capL = b == 0 ? 1 : caps[b - 1], capR = b == d - 2 ? 1 : caps[b + 1];

@@ -1187,9 +1187,9 @@ __device__ void snap_ctrl(const Ctrl &cr, int nb, CtrlSnap &out) {
 
 // carried region of bond b: row tiles < tr0 and column tiles < tc0 lie in
 // the stored extent (its rows / columns are whole prefix / suffix blocks)
-__device__ __forceinline__ void carried_tiles(const InstDev &in, const TileGeo &g, int b,
-                                              int32_t sr, int32_t sc, int32_t &tr0,
-                                              int32_t &tc0) {
+__host__ __device__ __forceinline__ void carried_tiles(const InstDev &in, const TileGeo &g, int b,
+                                                       int32_t sr, int32_t sc, int32_t &tr0,
+                                                       int32_t &tc0) {
   tr0 = g.pr > 0 ? (sr / (int32_t)in.n[b]) * g.P.tpb : sr / g.te;
   tc0 = g.pc > 0 ? (sc / (int32_t)in.n[b + 1]) * g.Q.tpb : sc / g.te;
 }
@@ -3778,13 +3778,15 @@ int64_t host_tiles(int64_t n_b, int64_t n_b1, int64_t rl, int64_t rr, int32_t pr
 }
 
 // Host replay of the screens' tile arithmetic for bond b at ranks r: the
-// kernels' own tile_geo_e / tile_rows / tile_cols, run on the host.  Counts
-// the violations: a tile that is empty, wider than te or outside the
-// superblock; a tile that crosses a piece of the subtensor grid (the pieces
-// recomputed here from the balanced split); a superblock row or column that
-// the tiles cover other than exactly once.
-int64_t host_check_bond_tiles(int d, const int64_t *n, const int32_t *r, const int32_t *grid,
-                              int b, int te, int64_t *ntiles) {
+// kernels' own tile_geo_e / tile_rows / tile_cols / carried_tiles, run on
+// the host.  Counts the violations: a tile that is empty, wider than te or
+// outside the superblock; a tile that crosses a piece of the subtensor grid
+// (the pieces recomputed here from the balanced split); a superblock row or
+// column that the tiles cover other than exactly once; with r_stored (the
+// ranks the stored residual was written at), a carried tile outside the
+// stored extent.
+int64_t host_check_bond_tiles(int d, const int64_t *n, const int32_t *r, const int32_t *r_stored,
+                              const int32_t *grid, int b, int te, int64_t *ntiles) {
   std::unique_ptr<InstDev> in(new InstDev());
   std::unique_ptr<Ctrl> cr(new Ctrl());
   in->d = d;
@@ -3821,6 +3823,27 @@ int64_t host_check_bond_tiles(int d, const int64_t *n, const int32_t *r, const i
   };
   side(g.rows, n[b], g.pr, g.nrt, true);
   side(g.cols, n[b + 1], g.pc, g.nct, false);
+  if (r_stored) {
+    // stored form: the carried rectangle (row tiles < tr0, column tiles <
+    // tc0) lies inside the stored extent at the ranks the residual was last
+    // written with, so the carried warp tiles read only carried entries
+    const int32_t sr = (int32_t)rows_of(*in, r_stored, b), sc = (int32_t)cols_of(*in, r_stored, b);
+    int32_t tr0, tc0;
+    carried_tiles(*in, g, b, sr, sc, tr0, tc0);
+    if (tr0 < 0 || tr0 > g.nrt || tc0 < 0 || tc0 > g.nct) ++bad;
+    for (int32_t t = 0; t < std::min(tr0, g.nrt); ++t) {
+      int64_t s0;
+      int nl;
+      tile_rows(*in, g, b, t, s0, nl);
+      if (s0 + nl > sr) ++bad;
+    }
+    for (int32_t t = 0; t < std::min(tc0, g.nct); ++t) {
+      int64_t s0;
+      int nl;
+      tile_cols(*in, g, b, t, s0, nl);
+      if (s0 + nl > sc) ++bad;
+    }
+  }
   if (ntiles) *ntiles = (int64_t)g.nrt * g.nct;
   return bad;
 }

@@ -33,7 +33,7 @@ cudaError_t launch_maxwellian_tables(const InstDev *d_inst, double *coef, double
 // tile geometry used to size the candidate buffer (host mirror of tile_geo)
 int64_t host_tiles(int64_t n_b, int64_t n_b1, int64_t rl, int64_t rr, int32_t pr, int32_t pc);
 // host replay of the kernels' tile arithmetic for one bond: violations found
-int64_t host_check_bond_tiles(int d, const int64_t *n, const int32_t *r, const int32_t *grid,
-                              int b, int te, int64_t *ntiles);
+int64_t host_check_bond_tiles(int d, const int64_t *n, const int32_t *r, const int32_t *r_stored,
+                              const int32_t *grid, int b, int te, int64_t *ntiles);
 
 }  // namespace ttc

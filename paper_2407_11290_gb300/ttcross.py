@@ -153,8 +153,9 @@ def load_library(path: str = LIB_PATH):
                                        C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                        C.POINTER(C.c_double)]
         L.ttcross_check_tiles.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
-                                          C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int,
-                                          C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_int32), C.c_int, C.c_int,
+                                          C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                           C.POINTER(C.c_int64)]
         L.ttcross_last_error_string.restype = C.c_char_p
         for name in ABI_SYMBOLS:
@@ -462,15 +463,18 @@ def probe_fp64_ilp(warps: int = 1, chains: int = 4, iters: int = 1 << 12) -> flo
     return cyc.value
 
 
-def check_tiles(n, ranks, caps, grid=None, tile_edge: int = 64, stored: bool = False):
+def check_tiles(n, ranks, caps, grid=None, tile_edge: int = 64, stored: bool = False,
+                stored_ranks=None):
     """ttcross_check_tiles: the kernels' tile arithmetic replayed on the host
-    for bond ranks ``ranks`` (bond k = ranks[k-1]).  Returns (tiles per bond,
-    candidate slots per bond at the rank caps ``caps``, violations).  Needs no
-    GPU."""
+    for bond ranks ``ranks`` (bond k = ranks[k-1]); ``stored_ranks`` (the
+    ranks the stored residual was written at) adds the carried-tile check.
+    Returns (tiles per bond, candidate slots per bond at the rank caps
+    ``caps``, violations).  Needs no GPU."""
     L = load_library()
     d = len(n)
     nn = np.ascontiguousarray(n, dtype=np.int64)
     rr, cc = _i32(ranks), _i32(caps)
+    rs = _i32(stored_ranks) if stored_ranks is not None else None
     g = _i32(grid) if grid is not None else None
     tiles = np.zeros(d - 1, dtype=np.int64)
     cap = np.zeros(d - 1, dtype=np.int64)
@@ -478,8 +482,10 @@ def check_tiles(n, ranks, caps, grid=None, tile_edge: int = 64, stored: bool = F
     p64 = C.POINTER(C.c_int64)
     p32 = C.POINTER(C.c_int32)
     _check(L.ttcross_check_tiles(d, nn.ctypes.data_as(p64), rr.ctypes.data_as(p32),
-                                 cc.ctypes.data_as(p32), g.ctypes.data_as(p32) if g is not None
-                                 else None, int(tile_edge), int(bool(stored)),
+                                 cc.ctypes.data_as(p32),
+                                 rs.ctypes.data_as(p32) if rs is not None else None,
+                                 g.ctypes.data_as(p32) if g is not None else None,
+                                 int(tile_edge), int(bool(stored)),
                                  tiles.ctypes.data_as(p64), cap.ctypes.data_as(p64),
                                  C.byref(bad)))
     return tiles, cap, int(bad.value)

@@ -18,9 +18,10 @@ import pytest
 from paper_2407_11290_gb300 import ttcross, workloads
 
 
-def _check(n, ranks, caps, grid, te, stored):
-    tiles, cap, bad = ttcross.check_tiles(n, ranks, caps, grid=grid, tile_edge=te, stored=stored)
-    assert bad == 0, (n, ranks, grid, te)
+def _check(n, ranks, caps, grid, te, stored, stored_ranks=None):
+    tiles, cap, bad = ttcross.check_tiles(n, ranks, caps, grid=grid, tile_edge=te, stored=stored,
+                                          stored_ranks=stored_ranks)
+    assert bad == 0, (n, ranks, stored_ranks, grid, te)
     return tiles, cap
 
 
@@ -55,7 +56,11 @@ def test_batch_recipe_tiles_cover_and_fit_the_slots():
             for ranks in rank_sets:
                 for te in (32, 64):
                     tiles, cap = _check(n, ranks, caps, grid, te, False)
-                    _, cap_st = _check(n, ranks, caps, grid, te, True)
+                    # the stored form, its residual written one pivot (and
+                    # all the way) back
+                    back = [max(1, int(x) - 1) for x in ranks]
+                    _, cap_st = _check(n, ranks, caps, grid, te, True, back)
+                    _check(n, ranks, caps, grid, te, True, [1] * (d - 1))
                     if te == 64:
                         # the slots are sized for 64-wide tiles at the caps
                         assert np.all(tiles <= cap) and np.all(4 * tiles <= cap_st)
@@ -76,6 +81,17 @@ def test_ragged_shapes_and_pieces(seed):
                 tiles, cap = _check(n, [r0, r1], caps, grid, te, False)
                 if te == 64:
                     assert np.all(tiles <= cap)
+                _check(n, [r0, r1], caps, grid, te, True,
+                       [int(rng.integers(1, r0 + 1)), int(rng.integers(1, r1 + 1))])
+
+
+def test_carried_rectangle_counts():
+    """Stored form, no grid, n = (100, 100, 100), ranks (5, 7) written at
+    (3, 7): bond 1's carried rows are the 100 rows of I_<1 (one 64-row tile
+    lies inside), its carried columns 100 * 7 (ten 64-column tiles); the
+    check passes and the tile counts are those of the plain cut."""
+    tiles, _ = _check([100, 100, 100], [5, 7], [8, 8], None, 64, True, [3, 7])
+    assert list(tiles) == [2 * 11, 8 * 2]
 
 
 def test_arguments_checked():
@@ -85,3 +101,5 @@ def test_arguments_checked():
         ttcross.check_tiles([10, 10], [1], [1], tile_edge=48)
     with pytest.raises(ttcross.TTCError):
         ttcross.check_tiles([10, 10], [1], [1], grid=[11, 1])
+    with pytest.raises(ttcross.TTCError):
+        ttcross.check_tiles([10, 10, 10], [2, 2], [4, 4], stored_ranks=[3, 1])  # above r
