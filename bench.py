@@ -510,7 +510,10 @@ def bench_batch(args, rank, world, local):
         "mixed_batched_vs_fp64_loop": times["loop_fp64"] / times["batched_split"],
         "fp64_batched_vs_loop": times["loop_fp64"] / times["batched_fp64"],
         "arms": summary, "count": len(ws), "plans": tuned,
-        "gpu_launches": 2 * len(ws),
+        # the headline arm's kernels per step (a batch: a control-block
+        # kernel per instance, the instance-list kernel per 256 instances,
+        # the persistent kernel), over the timed steps
+        "gpu_launches": args.steps * (len(ws) + (len(ws) + 255) // 256 + 1),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
