@@ -315,7 +315,7 @@ def bench_gpu(args, rank, world, local):
     peak = 2.0 * fma64 / 1e12
     peaks = measured_peaks() or {}
     hbm = peaks.get("hbm_gbs")
-    hbm_source = "measured copy bandwidth on this GPU pool"
+    hbm_source = "measured copy bandwidth (MEASURED_PEAKS.json)"
     if not hbm:
         # no measured copy bandwidth on this machine: one earlier GB300 copy
         # measurement stands in, labelled as such
