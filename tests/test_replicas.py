@@ -67,5 +67,15 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank0():
     assert line["err"] <= 1e-10
 
 
+def test_bench_host_helpers():
+    """The bench line's host arithmetic: stored-residual GB/s over the median
+    kernel time (none in the recompute form), and the dtype names."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench._stored_gbs({"stored_bytes": 0}, [1.0]) is None
+    assert bench._stored_gbs({"stored_bytes": 2 * 10**9}, [3.0, 1.0, 2.0]) == 1000.0
+    assert bench._dtype("fp64") == "f64" and bench._dtype("split") == "f32x2+f64"
+
+
 if __name__ == "__main__":
     sys.exit(pytest.main([__file__, "-q"]))
