@@ -1,4 +1,5 @@
-"""The multi-process path of bench.py on the CPU (gloo, world size 2).
+"""The multi-process path of bench.py on the CPU (gloo, world size 2), and
+the bench line's host arithmetic.
 
 A run does not shard: ``bench.py --gpus N`` runs N independent replicas, one
 process per GPU.  What the replicas share is host logic: the barrier around
