@@ -29,31 +29,8 @@ __device__ __noinline__ double gen_tt(const InstDev &in, const int32_t *idx) {
 }
 
 // Maxwellian f(x,v) = rho(x) (2 pi T(x))^{-dv/2} exp(-|v - u(x)|^2 / (2 T(x)))
-__device__ __noinline__ double gen_maxwellian(const InstDev &in, const int32_t *idx) {
-  const double two_pi = 6.283185307179586476925286766559;
-  double x[TTC_MAXD];
-  double prod_sin = 1.0, sum_x = 0.0;
-  for (int m = 0; m < in.dx; ++m) {
-    x[m] = __dmul_rn(two_pi, (double)idx[m]) / (double)in.n[m];
-    prod_sin = __dmul_rn(prod_sin, sin(x[m]));
-    sum_x = __dadd_rn(sum_x, x[m]);
-  }
-  const double rho = __dadd_rn(1.0, __dmul_rn(in.a_rho, prod_sin));
-  const double T = __dadd_rn(1.0, __dmul_rn(in.a_T, cos(sum_x)));
-  double q = 0.0;
-  for (int j = 0; j < in.dv; ++j) {
-    const int m = in.dx + j;
-    const double v = __dadd_rn(in.vmin, __dmul_rn(__dsub_rn(in.vmax, in.vmin), (double)idx[m]) /
-                                            (double)(in.n[m] - 1));
-    const double u = __dmul_rn(in.a_u, cos(x[(j + 1) % in.dx]));
-    const double dvu = __dsub_rn(v, u);
-    q = __dadd_rn(q, __dmul_rn(dvu, dvu));
-  }
-  return __dmul_rn(rho / pow(__dmul_rn(two_pi, T), 0.5 * (double)in.dv),
-                   exp(-q / __dmul_rn(2.0, T)));
-}
-
-// The same function from the create-time tables: one exp per entry.
+// from the create-time tables (rho (2 pi T)^{-dv/2} and -1 / (2 T) per
+// combination of the x indices, cos x_m per x mode): one exp per entry.
 __device__ __forceinline__ double gen_maxwellian_tab(const InstDev &in, const int32_t *idx) {
   int64_t combo = 0;
   for (int m = 0; m < in.dx; ++m) combo += (int64_t)idx[m] * in.mx_stride[m];
