@@ -376,6 +376,10 @@ def bench_gpu(args, rank, world, local):
                                           f"{args.residual} form (oracle rank cap {cap}; its "
                                           f"ranks {ost['ranks']} stay below it)",
                                 "err": ost["err"]}
+        # the same oracle on one thread (one full run), beside the all-core figure
+        t1, _ = cpu_oracle_time(cfg, 1, reps=1, residual=args.residual, workload=args.workload)
+        line["cpu_baseline"]["single_thread"] = {"value": t1[0], "unit": "ms", "cores": 1,
+                                                 "sample": "1 full run of the workload"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     tc.close()
