@@ -46,6 +46,16 @@ def test_default_options_without_gpu():
     assert o.residual == ttcross.RESIDUAL_RECOMPUTE
 
 
+def test_missing_library_raises(tmp_path):
+    """No CPU fallback: without the built library the binding raises."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("ttcross_copy", ttcross.__file__)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with pytest.raises(RuntimeError, match="not built"):
+        mod.load_library(str(tmp_path / "libttcross.so"))
+
+
 def test_create_fails_loudly_without_device():
     import torch
     if torch.cuda.is_available():
