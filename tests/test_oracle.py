@@ -345,6 +345,60 @@ def test_table5_weak_range():
     assert st["err"] <= 10 * ttaca_err[250]
 
 
+def _spike_tt(n, a, delta):
+    """Rank-2 TT on four modes: a smooth rank-1 term s(i) = 1 / (1 + i / 10)
+    in every mode plus a * v(i1) v(i2) v(i3) v(i4), v = delta at index 0 and
+    1 elsewhere.  Near the start pivot (the origin) the second term is
+    scaled down by delta^2 or more, so the rank-1 screens see only a small
+    trace of it while most entries carry all of it."""
+    i = np.arange(n)
+    s = 1.0 / (1.0 + 0.1 * i)
+    v = np.where(i == 0, delta, 1.0)
+    c1 = np.zeros((1, n, 2)); c1[0, :, 0] = s; c1[0, :, 1] = v
+    mid = np.zeros((2, n, 2)); mid[0, :, 0] = s; mid[1, :, 1] = v
+    c4 = np.zeros((2, n, 1)); c4[0, :, 0] = s; c4[1, :, 0] = a * v
+    cores = [c1, mid, mid.copy(), c4]
+    return dict(n=[n] * 4, gen={"kind": "tt", "ranks": [1, 2, 2, 2, 1], "cores": cores})
+
+
+@pytest.mark.parametrize("a,delta", [(1e-4, 0.01), (1e-4, 0.03), (1e-3, 0.01)])
+def test_tau_refinement_follows_the_stop_rule(a, delta):
+    """The stop rule with tau refinement (a bond adds a pivot while its best
+    |E| > tau rms(X); tau starts at eps and drops tenfold while the verified
+    error is above eps), checked from numpy on the full tensor: the number
+    of refinements is the smallest j with max |E| > eps 10^-j rms over the
+    rank-1 superblocks at the start pivot; one refinement fewer leaves the
+    rank-1 cross, NOT_CONVERGED, with the error of its interpolant."""
+    eps, n = 1e-6, 10
+    w = _spike_tt(n, a, delta)
+    X = np.einsum("aib,bjc,ckd,dle->ijkl", *w["gen"]["cores"])
+    p = np.unravel_index(int(np.argmax(np.abs(X.reshape(-1, order="F")))), X.shape, order="F")
+    rms = np.sqrt(np.mean(X ** 2))
+    M = 0.0
+    for k in range(3):
+        B = X[tuple(slice(None) if m in (k, k + 1) else p[m] for m in range(4))]
+        E = B - np.outer(B[:, p[k + 1]], B[p[k], :]) / B[p[k], p[k + 1]]
+        M = max(M, np.abs(E).max())
+    j = 0
+    while not M > eps * 10.0 ** (-j) * rms:
+        j += 1
+    assert 1 <= j <= 4
+    o = oracle.Oracle(w["n"], w["gen"], 8)
+    rc, st = o.run(eps, nsamples=0, max_refine=6)
+    assert rc == 0 and st["refinements"] == j
+    assert abs(st["tau"] - eps * 10.0 ** (-j)) <= 1e-12 * eps
+    assert [int(r) for r in o.ranks()] == [2, 2, 2] and st["err"] <= 1e-10
+    # one refinement fewer: the rank-1 cross through p
+    o = oracle.Oracle(w["n"], w["gen"], 8)
+    rc, st = o.run(eps, nsamples=0, max_refine=j - 1)
+    assert rc == 7 and [int(r) for r in o.ranks()] == [1, 1, 1]
+    i1, i2, i3, i4 = np.meshgrid(*[np.arange(n)] * 4, indexing="ij")
+    Xt = (X[i1, p[1], p[2], p[3]] * X[p[0], i2, p[2], p[3]] * X[p[0], p[1], i3, p[3]] *
+          X[p[0], p[1], p[2], i4]) / X[p] ** 3
+    exact = np.linalg.norm(X - Xt) / np.linalg.norm(X)
+    assert exact > eps and abs(st["err"] - exact) <= 1e-9 * exact
+
+
 def test_maxwellian_moments():
     """Velocity moments of the Maxwellian (Sec. 5.2 family): on a wide v-grid
     the quadrature of f over v returns rho(x), rho u(x) and dv rho T(x)."""
