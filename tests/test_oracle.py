@@ -423,7 +423,7 @@ def test_maxwellian_moments():
         assert abs(m2 - T) < 1e-9
 
 
-def test_maxwellian_3d3v_velocity_moments():
+def test_maxwellian_dx3_velocity_moments():
     """The 6D Maxwellian (d_x = 3, d_v = 3) of the single-tensor workload:
     rho = 1 + a_rho sin x1 sin x2 sin x3, u = a_u (cos x2, cos x3, cos x1),
     T = 1 + a_T cos(x1 + x2 + x3) on the periodic grid x = 2 pi i / n.  On a
@@ -460,6 +460,39 @@ def test_maxwellian_3d3v_velocity_moments():
             q = sum((V[j] - g["a_u"]) ** 2 for j in range(3))
             np.testing.assert_allclose(F, np.exp(-q / (2 * t)) / (2 * np.pi * t) ** 1.5,
                                        rtol=1e-13, atol=1e-300)
+
+
+def test_maxwellian_xv_3d3v_velocity_moments():
+    """The 3d3v distribution of Sec. 5.2 (modes x, v_x, y, v_y, z, v_z): for
+    fixed positions the quadrature over the three velocities of f is
+    2 varrho (2 pi)^(3/2) sqrt(T_x T_y T_z), with varrho the sum over the
+    three positions of rho / (2 sqrt(2 pi T)); the second moment in v_q is
+    T_q + a_u^2 and the first moments vanish.  Positions s = -1/2, 0, 1/4,
+    1/2 (T = 1/2, 1/2, 0.9, 1/2)."""
+    nv = 49
+    w = W.maxwellian_xv(3, 5, nv, vmin=-8.0, vmax=8.0)
+    o = oracle.Oracle(w["n"], w["gen"], 2)
+    g = w["gen"]
+    v = -8.0 + 16.0 * np.arange(nv) / (nv - 1)
+    h = 16.0 / (nv - 1)
+    V = np.meshgrid(v, v, v, indexing="ij")
+    for pos in [(2, 3, 0), (3, 4, 2)]:
+        F = np.empty((nv, nv, nv))
+        for a in range(nv):
+            for b in range(nv):
+                for c in range(nv):
+                    F[a, b, c] = o.entry((pos[0], a, pos[1], b, pos[2], c))
+        s = [-0.5 + i / 4 for i in pos]
+        rho = [1 + g["a_rho"] * np.sin(2 * np.pi * t) for t in s]
+        T = [0.5 + g["a_T"] * np.sin(2 * np.pi * t) for t in s]
+        varrho = sum(r / (2 * np.sqrt(2 * np.pi * t)) for r, t in zip(rho, T))
+        mass = 2 * varrho * (2 * np.pi) ** 1.5 * np.sqrt(T[0] * T[1] * T[2])
+        m0 = F.sum() * h ** 3
+        assert abs(m0 - mass) < 1e-9 * mass
+        for q in range(3):
+            assert abs((F * V[q]).sum() * h ** 3) < 1e-9 * mass
+            m2 = (F * V[q] ** 2).sum() * h ** 3 / m0
+            assert abs(m2 - (T[q] + g["a_u"] ** 2)) < 1e-9
 
 
 def test_maxwellian_xv_velocity_moments():
