@@ -39,6 +39,43 @@ def test_library_builds_and_exports_header_symbols():
     assert sorted(ttcross.ABI_SYMBOLS) == names
 
 
+C_CLIENT = r"""
+#include <stdio.h>
+#include "ttcross.h"
+#include "ttcross_probe.h"
+int main(void) {
+  ttc_options o;
+  if (ttcross_default_options(&o) != TTC_OK || o.max_rank != 64) return 1;
+  const int64_t n[3] = {100, 100, 100};
+  const int32_t r[2] = {5, 7}, caps[2] = {8, 8};
+  int64_t tiles[2], cap[2], bad = -1;
+  if (ttcross_check_tiles(3, n, r, caps, NULL, NULL, 64, 0, tiles, cap, &bad) != TTC_OK) return 2;
+  printf("%lld %lld %lld\n", (long long)tiles[0], (long long)tiles[1], (long long)bad);
+  return 0;
+}
+"""
+
+
+def test_plain_c_client(tmp_path):
+    """The boundary is plain C: a C99 program (-pedantic -Werror) includes
+    both headers, links the library and calls its host-side entry points."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lib = B.build()
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", B.INCLUDE,
+                    str(src), "-o", str(exe), os.path.abspath(lib),
+                    "-Wl,-rpath," + os.path.dirname(os.path.abspath(lib))], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.split() == ["22", "16", "0"]
+
+
 def test_default_options_without_gpu():
     o = ttcross.default_options()
     assert o.max_rank == 64 and o.nsamples == 10**6 and o.seed == 20240715
