@@ -78,5 +78,34 @@ def test_bench_host_helpers():
     assert bench._dtype("fp64") == "f64" and bench._dtype("split") == "f32x2+f64"
 
 
+def test_clock_samples_decoded():
+    """nvidia-smi lines (SM clock, max clock, power, event-reason mask) become
+    the line's clocks: median SM clock under load, the max clock, and the
+    named reasons seen (idle left out)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class FakeProc:
+        stdout = ["2070, 2070, 900.1, 0x0000000000000000\n",
+                  "1980, 2070, 1390.5, 0x0000000000000004\n",
+                  "2070, 2070, 1100.0, 0x0000000000000001\n",
+                  "garbage line\n",
+                  "2055, 2070, 1200.0, 0x0000000000000020\n"]
+
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c = bench.ClockSampler(0)
+    c.proc = FakeProc()
+    c._read()
+    out = c.stop()
+    assert out["samples"] == 4 and out["sm_max_mhz"] == 2070.0
+    assert out["sm_mhz"] == 2062.5
+    assert out["reasons"] == ["sw_power_cap", "sw_thermal_slowdown"]
+
+
 if __name__ == "__main__":
     sys.exit(pytest.main([__file__, "-q"]))
