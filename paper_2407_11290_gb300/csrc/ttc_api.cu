@@ -523,9 +523,11 @@ ttc_status ttcross_create(int d, const int64_t *n, const ttc_generator *gen, con
       ncombo *= n[m];
       ncos += n[m];
     }
-    if (ncombo > ((int64_t)1 << 27))
+    if (ncombo > ((int64_t)1 << 27)) {
+      delete h;
       return fail(TTC_ERR_INVALID_ARG, "Maxwellian x grid too large (%lld index combinations)",
                   (long long)ncombo);
+    }
   }
   const bool xv = gen->kind == TTC_GEN_MAXWELLIAN_XV;
   if (xv) {
